@@ -1,0 +1,869 @@
+/*
+ * hisq_oracle.c -- plain, slow, FP64 CPU oracle for the HISQ staggered stencil,
+ * the reduced-bit storage formats and the Krylov solvers of
+ * M. A. Clark, D. Howarth, J. Tu, M. Wagner, E. Weinberg,
+ * "Maximizing the Bang Per Bit" (Lattice 2022).
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this library.  It shares no code, header, table or
+ * helper with the CUDA path; the two meet only through the seeded inputs.
+ *
+ * Conventions (the readings of points the paper leaves open are listed with
+ * the design notes; each function below names the passage it follows):
+ *   dims L = {Lx, Ly, Lz, Lt}, all even.
+ *   lex = ((t*Lz + z)*Ly + y)*Lx + x,  parity = (x+y+z+t) mod 2,  cb = lex/2.
+ *   gauge  : double [mu][lex][row][col][re,im]     (4*V links, 18 reals each)
+ *   spinor : double [cb][color][re,im] on one parity (Vh = V/2 sites);
+ *            full lattice = [parity][cb][color][re,im], even first.
+ *
+ * The stencil (the HISQ operator, named in Sec. 1 and Sec. 4.2 but never
+ * written out) is read as
+ *   (D psi)(x) = sum_mu [ F_mu(x) psi(x+mu) - F_mu(x-mu)^+ psi(x-mu)
+ *                       + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^+ psi(x-3mu) ]
+ * with links that already carry the staggered phases, M = 2m + D on the full
+ * lattice and M_ee = 4m^2 - D_eo D_oe on the even sites.
+ *
+ * Parity unpinned: none of the functions in this file; every one is checked
+ * against closed forms, invariants, hand-derived bit patterns or a dense
+ * direct solve by the tests.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double _Complex cplx;
+
+/* ------------------------------------------------------------------------ */
+/* threads                                                                   */
+/* ------------------------------------------------------------------------ */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* O1 geometry                                                               */
+/* ------------------------------------------------------------------------ */
+static int64_t vol_of(const int *L) { return (int64_t)L[0] * L[1] * L[2] * L[3]; }
+
+static void coords_of(const int *L, int64_t lex, int c[4])
+{
+    for (int d = 0; d < 4; d++) {
+        c[d] = (int)(lex % L[d]);
+        lex /= L[d];
+    }
+}
+
+static int64_t lex_of(const int *L, const int c[4])
+{
+    return (((int64_t)c[3] * L[2] + c[2]) * L[1] + c[1]) * L[0] + c[0];
+}
+
+static int parity_of(const int c[4]) { return (c[0] + c[1] + c[2] + c[3]) & 1; }
+
+/* Site of the given parity with checkerboard index cb: lex 2cb and 2cb+1 share
+ * y, z, t and differ by one step in x, so exactly one of them has the parity. */
+static int64_t lex_from_cb(const int *L, int parity, int64_t cb)
+{
+    int c[4];
+    int64_t lex = 2 * cb;
+    coords_of(L, lex, c);
+    return parity_of(c) == parity ? lex : lex + 1;
+}
+
+/* lex of x + k * mu-hat with periodic wrap. */
+static int64_t hop(const int *L, const int c[4], int mu, int k)
+{
+    int d[4] = {c[0], c[1], c[2], c[3]};
+    d[mu] = ((d[mu] + k) % L[mu] + L[mu]) % L[mu];
+    return lex_of(L, d);
+}
+
+/* Staggered phase eta_mu(x) times the antiperiodic-t sign of a fat (k=1) or
+ * long (k=3) link: the sign that multiplies an SU(3) matrix in the synthetic
+ * fields, used only to rebuild the third row of a compressed long link. */
+static double link_sign(const int *L, const int c[4], int mu, int k, int antiperiodic_t)
+{
+    int s = 0;
+    for (int nu = 0; nu < mu; nu++) s += c[nu];
+    double eta = (s & 1) ? -1.0 : 1.0;
+    if (antiperiodic_t && mu == 3 && c[3] + k >= L[3]) eta = -eta;
+    return eta;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O3 the stencil                                                            */
+/* ------------------------------------------------------------------------ */
+static const cplx *link_at(const cplx *g, int64_t V, int mu, int64_t lex)
+{
+    return g + ((int64_t)mu * V + lex) * 9;
+}
+
+/* acc += sgn * U s */
+static void mv_add(cplx acc[3], const cplx *U, const cplx *s, double sgn)
+{
+    for (int i = 0; i < 3; i++) {
+        cplx t = 0;
+        for (int j = 0; j < 3; j++) t += U[i * 3 + j] * s[j];
+        acc[i] += sgn * t;
+    }
+}
+
+/* acc += sgn * U^+ s */
+static void mv_adj_add(cplx acc[3], const cplx *U, const cplx *s, double sgn)
+{
+    for (int i = 0; i < 3; i++) {
+        cplx t = 0;
+        for (int j = 0; j < 3; j++) t += conj(U[j * 3 + i]) * s[j];
+        acc[i] += sgn * t;
+    }
+}
+
+/* (D psi)(x) at one site x; psi is the half-lattice field of the other parity.
+ * Terms are added per direction in the order +1, -1, +3, -3. */
+static void dslash_site(const int *L, const cplx *fat, const cplx *lng, const cplx *in,
+                        int64_t lex, cplx out[3])
+{
+    const int64_t V = vol_of(L);
+    int c[4];
+    coords_of(L, lex, c);
+    cplx acc[3] = {0, 0, 0};
+    for (int mu = 0; mu < 4; mu++) {
+        int64_t p1 = hop(L, c, mu, +1), m1 = hop(L, c, mu, -1);
+        int64_t p3 = hop(L, c, mu, +3), m3 = hop(L, c, mu, -3);
+        mv_add(acc, link_at(fat, V, mu, lex), in + (p1 / 2) * 3, +1.0);
+        mv_adj_add(acc, link_at(fat, V, mu, m1), in + (m1 / 2) * 3, -1.0);
+        mv_add(acc, link_at(lng, V, mu, lex), in + (p3 / 2) * 3, +1.0);
+        mv_adj_add(acc, link_at(lng, V, mu, m3), in + (m3 / 2) * 3, -1.0);
+    }
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+}
+
+/* out[cb] = (D in)(x) for every site x of parity out_parity; in lives on the
+ * other parity.  D_eo is out_parity 0, D_oe is out_parity 1. */
+void or_dslash(const int *L, const double *fat, const double *lng, int out_parity,
+               const double *in, double *out)
+{
+    const int64_t Vh = vol_of(L) / 2;
+    const cplx *F = (const cplx *)fat, *G = (const cplx *)lng, *s = (const cplx *)in;
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(static)
+    for (int64_t cb = 0; cb < Vh; cb++)
+        dslash_site(L, F, G, s, lex_from_cb(L, out_parity, cb), o + cb * 3);
+}
+
+/* The stencil at a list of output sites only (checkerboard indices cbs[i]). */
+void or_dslash_sites(const int *L, const double *fat, const double *lng, int out_parity,
+                     const double *in, int64_t n, const int64_t *cbs, double *out)
+{
+    const cplx *F = (const cplx *)fat, *G = (const cplx *)lng, *s = (const cplx *)in;
+    cplx *o = (cplx *)out;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++)
+        dslash_site(L, F, G, s, lex_from_cb(L, out_parity, cbs[i]), o + i * 3);
+}
+
+/* y = (4 m^2 + sigma) x - D_eo D_oe x on the even sites. */
+void or_mee(const int *L, const double *fat, const double *lng, double m, double sigma,
+            const double *x, double *y)
+{
+    const int64_t n = vol_of(L) / 2 * 3;
+    cplx *tmp = malloc(sizeof(cplx) * n);
+    cplx *dd = malloc(sizeof(cplx) * n);
+    or_dslash(L, fat, lng, 1, x, (double *)tmp);
+    or_dslash(L, fat, lng, 0, (double *)tmp, (double *)dd);
+    const cplx *xc = (const cplx *)x;
+    cplx *yc = (cplx *)y;
+    const double d = 4.0 * m * m + sigma;
+    for (int64_t i = 0; i < n; i++) yc[i] = d * xc[i] - dd[i];
+    free(tmp);
+    free(dd);
+}
+
+/* y = 2 m x + D x on the full lattice ([parity][cb][color]). */
+void or_mfull(const int *L, const double *fat, const double *lng, double m,
+              const double *x, double *y)
+{
+    const int64_t n = vol_of(L) / 2 * 3;
+    const cplx *xe = (const cplx *)x, *xo = xe + n;
+    cplx *ye = (cplx *)y, *yo = ye + n;
+    or_dslash(L, fat, lng, 0, (const double *)xo, (double *)ye);
+    or_dslash(L, fat, lng, 1, (const double *)xe, (double *)yo);
+    for (int64_t i = 0; i < n; i++) {
+        ye[i] += 2.0 * m * xe[i];
+        yo[i] += 2.0 * m * xo[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* O5 storage formats                                                        */
+/* ------------------------------------------------------------------------ */
+static uint32_t f2u(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+static float u2f(uint32_t u)
+{
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* 16-bit fixed point with a site-local FP32 norm (Sec. 2, Listing 1): record
+ * of 16 bytes = int16 v[6] followed by float max.  The largest |component| of
+ * the site sets the scale; components are rounded to nearest-even integers in
+ * [-32767, 32767].  Decoding multiplies by max * fl(1/32767).
+ * Returns the number of sites with a non-finite component. */
+int64_t or_half_pack(int64_t n, const float *v, unsigned char *rec)
+{
+    int64_t bad = 0;
+    for (int64_t s = 0; s < n; s++) {
+        const float *x = v + 6 * s;
+        float mx = 0.0f;
+        int finite = 1;
+        for (int i = 0; i < 6; i++) {
+            if (!isfinite(x[i])) finite = 0;
+            mx = fmaxf(mx, fabsf(x[i]));
+        }
+        int16_t q[6] = {0, 0, 0, 0, 0, 0};
+        if (!finite) {
+            bad++;
+            mx = 0.0f;
+        } else if (mx > 0.0f) {
+            const float inv = 32767.0f / mx;
+            for (int i = 0; i < 6; i++) {
+                long r = lrintf(x[i] * inv);
+                if (r > 32767) r = 32767;
+                if (r < -32767) r = -32767;
+                q[i] = (int16_t)r;
+            }
+        }
+        memcpy(rec + 16 * s, q, 12);
+        memcpy(rec + 16 * s + 12, &mx, 4);
+    }
+    return bad;
+}
+
+void or_half_unpack(int64_t n, const unsigned char *rec, float *v)
+{
+    const float inv32767 = 1.0f / 32767.0f;
+    for (int64_t s = 0; s < n; s++) {
+        int16_t q[6];
+        float mx;
+        memcpy(q, rec + 16 * s, 12);
+        memcpy(&mx, rec + 16 * s + 12, 4);
+        const float scale = mx * inv32767;
+        for (int i = 0; i < 6; i++) v[6 * s + i] = (float)q[i] * scale;
+    }
+}
+
+/* 20-bit shared-exponent format (Sec. 3, Listing 2; the codec of Appendix A,
+ * Listing 4).  Per site: six 20-bit two's-complement integers and an 8-bit
+ * exponent in four 32-bit words.  Steps of the appendix:
+ *   max  = largest |component| (FP32; the garbled vector initialisation of
+ *          the listing is read as a scalar max over all six components);
+ *   t    = max / (2^19 - 1) in FP32;
+ *   E    = (biased exponent field of t) + 1, mantissa dropped, so 2^(E-127)
+ *          is the power of two just above t;
+ *   q_i  = round-to-nearest-even(v_i * 2^-(E-127))  (|q_i| <= 2^19 - 1);
+ * and the bitfields are laid out least-significant first within each word:
+ *   w0 = re0[0:20] | im0 bits 8..19 at [20:32]
+ *   w1 = im0 bits 0..7 at [0:8] | re1 at [8:28] | im1 bits 16..19 at [28:32]
+ *   w2 = im1 bits 0..15 at [0:16] | re2 bits 4..19 at [16:32]
+ *   w3 = re2 bits 0..3 at [0:4] | im2 at [4:24] | E at [24:32]
+ * Decoding sign-extends each 20-bit value and multiplies by 2^(E-127).
+ * Returns the number of sites with a non-finite component (their record is
+ * written as zero with E = 1). */
+int64_t or_int20_pack(int64_t n, const float *v, uint32_t *w)
+{
+    int64_t bad = 0;
+    for (int64_t s = 0; s < n; s++) {
+        const float *x = v + 6 * s;
+        float mx = 0.0f;
+        int finite = 1;
+        for (int i = 0; i < 6; i++) {
+            if (!isfinite(x[i])) finite = 0;
+            mx = fmaxf(mx, fabsf(x[i]));
+        }
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t E = 1;
+        if (!finite) {
+            bad++;
+        } else {
+            const float t = mx / 524287.0f;
+            E = ((f2u(t) >> 23) & 0xffu) + 1u;
+            const float down = u2f((254u - E) << 23); /* 2^-(E-127) */
+            for (int i = 0; i < 6; i++) {
+                long q = lrintf(x[i] * down);
+                u[i] = (uint32_t)(int32_t)q;
+            }
+        }
+        uint32_t *o = w + 4 * s;
+        o[0] = (u[0] & 0xfffffu) | (((u[1] >> 8) & 0xfffu) << 20);
+        o[1] = (u[1] & 0xffu) | ((u[2] & 0xfffffu) << 8) | (((u[3] >> 16) & 0xfu) << 28);
+        o[2] = (u[3] & 0xffffu) | (((u[4] >> 4) & 0xffffu) << 16);
+        o[3] = (u[4] & 0xfu) | ((u[5] & 0xfffffu) << 4) | (E << 24);
+    }
+    return bad;
+}
+
+static int32_t sext(uint32_t u, int bits)
+{
+    const uint32_t m = 1u << (bits - 1);
+    u &= (bits == 32) ? 0xffffffffu : ((1u << bits) - 1u);
+    return (int32_t)((u ^ m) - m);
+}
+
+void or_int20_unpack(int64_t n, const uint32_t *w, float *v)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const uint32_t *o = w + 4 * s;
+        uint32_t u[6];
+        u[0] = o[0] & 0xfffffu;
+        u[1] = ((o[0] >> 20) << 8) | (o[1] & 0xffu);
+        u[2] = (o[1] >> 8) & 0xfffffu;
+        u[3] = ((o[1] >> 28) << 16) | (o[2] & 0xffffu);
+        u[4] = ((o[2] >> 16) << 4) | (o[3] & 0xfu);
+        u[5] = (o[3] >> 4) & 0xfffffu;
+        const uint32_t E = o[3] >> 24;
+        const float up = u2f(E << 23); /* 2^(E-127) */
+        for (int i = 0; i < 6; i++) v[6 * s + i] = (float)sext(u[i], 20) * up;
+    }
+}
+
+/* 30-bit shared-exponent format (Sec. 3, Listing 3; no layout is given, so
+ * this is our reading): six 32-bit words; bits 0..29 of word k hold the 30-bit
+ * two's-complement integer q_k; bits 30..31 of words 0..3 hold bits 2k..2k+1
+ * of the 8-bit exponent E; the top bits of words 4, 5 are zero.  The exponent
+ * rule is the 20-bit one applied in FP64 with scale 2^29 - 1:
+ * t = max / (2^29-1), 2^(E-127) the power of two just above t (E clamped to
+ * [1, 254]), q_k = rint(v_k * 2^-(E-127)).  Decoding is exact in FP64.
+ * Returns the number of sites that could not be encoded (non-finite, or too
+ * large for the 8-bit exponent); they are written as zero with E = 1. */
+int64_t or_int30_pack(int64_t n, const double *v, uint32_t *w)
+{
+    int64_t bad = 0;
+    for (int64_t s = 0; s < n; s++) {
+        const double *x = v + 6 * s;
+        double mx = 0.0;
+        int ok = 1;
+        for (int i = 0; i < 6; i++) {
+            if (!isfinite(x[i])) ok = 0;
+            mx = fmax(mx, fabs(x[i]));
+        }
+        uint32_t E = 1;
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        if (ok) {
+            const double t = mx / 536870911.0;
+            int ex = 0;
+            if (t > 0.0) frexp(t, &ex); /* t = f 2^ex, f in [0.5, 1) */
+            int e = (t > 0.0) ? ex + 127 : 1;
+            if (e < 1) e = 1;
+            if (e > 254) ok = 0;
+            if (ok) {
+                E = (uint32_t)e;
+                for (int i = 0; i < 6; i++) {
+                    long long q = llrint(ldexp(x[i], -(e - 127)));
+                    u[i] = (uint32_t)(int32_t)q;
+                }
+            }
+        }
+        if (!ok) bad++;
+        uint32_t *o = w + 6 * s;
+        for (int k = 0; k < 6; k++) {
+            o[k] = u[k] & 0x3fffffffu;
+            if (k < 4) o[k] |= ((E >> (2 * k)) & 3u) << 30;
+        }
+    }
+    return bad;
+}
+
+void or_int30_unpack(int64_t n, const uint32_t *w, double *v)
+{
+    for (int64_t s = 0; s < n; s++) {
+        const uint32_t *o = w + 6 * s;
+        uint32_t E = 0;
+        for (int k = 0; k < 4; k++) E |= (o[k] >> 30) << (2 * k);
+        for (int k = 0; k < 6; k++) v[6 * s + k] = ldexp((double)sext(o[k], 30), (int)E - 127);
+    }
+}
+
+/* Fixed-point gauge (Sec. 2 and its footnote on smeared fields; Sec. 3 for the
+ * 32-bit variant): one scale per field set by the global max |element|;
+ * q = rint(x * (qmax / gmax)) in FP64, clamped to [-qmax, qmax],
+ * qmax = 2^15-1 (16-bit) or 2^31-1 (32-bit). */
+double or_absmax(int64_t n, const double *g)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; i++) m = fmax(m, fabs(g[i]));
+    return m;
+}
+
+static double qmax_of(int bits) { return bits == 16 ? 32767.0 : 2147483647.0; }
+
+void or_fix_pack(int64_t n, const double *g, double gmax, int bits, int32_t *q)
+{
+    const double qm = qmax_of(bits);
+    const double inv = gmax > 0.0 ? qm / gmax : 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double r = rint(g[i] * inv);
+        if (r > qm) r = qm;
+        if (r < -qm) r = -qm;
+        q[i] = (int32_t)r;
+    }
+}
+
+/* Decoded value as the computation sees it: FP64 q * (gmax/qmax), or, for FP32
+ * compute, fl32(q) * fl32(gmax/qmax) rounded to FP32. */
+void or_fix_unpack(int64_t n, const int32_t *q, double gmax, int bits, int compute_f32, double *out)
+{
+    const double s = gmax / qmax_of(bits);
+    const float sf = (float)s;
+    for (int64_t i = 0; i < n; i++) {
+        if (compute_f32)
+            out[i] = (double)((float)q[i] * sf);
+        else
+            out[i] = (double)q[i] * s;
+    }
+}
+
+/* Row 2 of a compressed link from rows 0 and 1 (Sec. 1, link compression 18 ->
+ * 12): for U = sign * W with W in SU(3), row2(U) = sign * conj(row0 x row1). */
+static void rebuild_row2(cplx *U, double sign)
+{
+    U[6] = sign * conj(U[1] * U[5] - U[2] * U[4]);
+    U[7] = sign * conj(U[2] * U[3] - U[0] * U[5]);
+    U[8] = sign * conj(U[0] * U[4] - U[1] * U[3]);
+}
+
+/* Format emulation (O4): a link field as the computation sees it after storage
+ * in format gfmt (0 FP64, 1 FP32, 2 fixed-16, 3 fixed-32) with recon 18 or 12;
+ * r12 rebuilds row 2 in FP64 from the decoded rows 0, 1 and the link's sign
+ * (long links: k = 3, fat links: k = 1).  gmax is the field's scale. */
+void or_gauge_emulate(const int *L, const double *g, int gfmt, int recon, int k,
+                      int antiperiodic_t, int compute_f32, double gmax, double *out)
+{
+    const int64_t V = vol_of(L);
+    const int64_t n = 4 * V * 18;
+    if (gfmt == 0) {
+        memcpy(out, g, sizeof(double) * n);
+    } else if (gfmt == 1) {
+        for (int64_t i = 0; i < n; i++) out[i] = (double)(float)g[i];
+    } else {
+        const int bits = gfmt == 2 ? 16 : 32;
+        int32_t *q = malloc(sizeof(int32_t) * n);
+        or_fix_pack(n, g, gmax, bits, q);
+        or_fix_unpack(n, q, gmax, bits, compute_f32, out);
+        free(q);
+    }
+    if (recon == 12) {
+        for (int mu = 0; mu < 4; mu++)
+            for (int64_t lex = 0; lex < V; lex++) {
+                int c[4];
+                coords_of(L, lex, c);
+                cplx *U = (cplx *)(out + ((int64_t)mu * V + lex) * 18);
+                rebuild_row2(U, link_sign(L, c, mu, k, antiperiodic_t));
+            }
+    }
+}
+
+/* Spinor format emulation: sfmt 0 FP64, 1 FP32, 2 half, 3 int20, 4 int30. */
+void or_spinor_emulate(int64_t nsites, int sfmt, const double *in, double *out)
+{
+    const int64_t n = nsites * 6;
+    if (sfmt == 0) {
+        memcpy(out, in, sizeof(double) * n);
+        return;
+    }
+    if (sfmt == 1) {
+        for (int64_t i = 0; i < n; i++) out[i] = (double)(float)in[i];
+        return;
+    }
+    if (sfmt == 4) {
+        uint32_t *w = malloc(sizeof(uint32_t) * 6 * nsites);
+        or_int30_pack(nsites, in, w);
+        or_int30_unpack(nsites, w, out);
+        free(w);
+        return;
+    }
+    float *f = malloc(sizeof(float) * n);
+    for (int64_t i = 0; i < n; i++) f[i] = (float)in[i];
+    if (sfmt == 2) {
+        unsigned char *r = malloc(16 * nsites);
+        or_half_pack(nsites, f, r);
+        or_half_unpack(nsites, r, f);
+        free(r);
+    } else {
+        uint32_t *w = malloc(sizeof(uint32_t) * 4 * nsites);
+        or_int20_pack(nsites, f, w);
+        or_int20_unpack(nsites, w, f);
+        free(w);
+    }
+    for (int64_t i = 0; i < n; i++) out[i] = (double)f[i];
+    free(f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* vector helpers (serial, fixed order)                                      */
+/* ------------------------------------------------------------------------ */
+static cplx cdot(int64_t n, const cplx *a, const cplx *b) /* a^+ b */
+{
+    cplx s = 0;
+    for (int64_t i = 0; i < n; i++) s += conj(a[i]) * b[i];
+    return s;
+}
+
+static double nrm2(int64_t n, const cplx *a)
+{
+    double s = 0;
+    for (int64_t i = 0; i < n; i++) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+    return s;
+}
+
+typedef struct {
+    const int *L;
+    const double *fat, *lng;
+    double m, sigma;
+    int full; /* 0: M_ee + sigma on even sites; 1: M = 2m + D full lattice */
+} op_t;
+
+static int64_t op_len(const op_t *op) { return vol_of(op->L) / 2 * 3 * (op->full ? 2 : 1); }
+
+static void op_apply(const op_t *op, const cplx *x, cplx *y)
+{
+    if (op->full)
+        or_mfull(op->L, op->fat, op->lng, op->m, (const double *)x, (double *)y);
+    else
+        or_mee(op->L, op->fat, op->lng, op->m, op->sigma, (const double *)x, (double *)y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* O6 conjugate gradient (Hestenes-Stiefel), FP64                            */
+/* ------------------------------------------------------------------------ */
+/* Solves (M_ee + sigma) x = b.  x holds the initial guess if use_x0, else it
+ * starts from zero.  Stops when the iterated residual reaches tol*|b|; then
+ * *true_res = |b - (M_ee+sigma) x| / |b|.  Returns 0 on convergence, 1 when
+ * maxiter was reached, 2 on breakdown. */
+int or_cg(const int *L, const double *fat, const double *lng, double m, double sigma,
+          const double *b_, double *x_, double tol, int maxiter, int use_x0,
+          int *iters, double *true_res)
+{
+    op_t op = {L, fat, lng, m, sigma, 0};
+    const int64_t n = op_len(&op);
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    cplx *r = malloc(sizeof(cplx) * n), *p = malloc(sizeof(cplx) * n), *Ap = malloc(sizeof(cplx) * n);
+    if (!use_x0) memset(x, 0, sizeof(cplx) * n);
+    op_apply(&op, x, Ap);
+    for (int64_t i = 0; i < n; i++) r[i] = b[i] - Ap[i];
+    memcpy(p, r, sizeof(cplx) * n);
+    const double bb = nrm2(n, b);
+    double rr = nrm2(n, r);
+    int k = 0, status = 1;
+    if (sqrt(rr) <= tol * sqrt(bb)) status = 0;
+    while (status == 1 && k < maxiter) {
+        op_apply(&op, p, Ap);
+        const double pAp = creal(cdot(n, p, Ap));
+        if (!(pAp > 0.0)) {
+            status = 2;
+            break;
+        }
+        const double alpha = rr / pAp;
+        for (int64_t i = 0; i < n; i++) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * Ap[i];
+        }
+        const double rr_new = nrm2(n, r);
+        k++;
+        if (sqrt(rr_new) <= tol * sqrt(bb)) {
+            status = 0;
+            break;
+        }
+        const double beta = rr_new / rr;
+        for (int64_t i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
+        rr = rr_new;
+    }
+    op_apply(&op, x, Ap);
+    for (int64_t i = 0; i < n; i++) r[i] = b[i] - Ap[i];
+    *true_res = sqrt(nrm2(n, r) / bb);
+    *iters = k;
+    free(r);
+    free(p);
+    free(Ap);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O7 multi-shift CG (Sec. 2.2; Jegerlehner, hep-lat/9612014), FP64          */
+/* ------------------------------------------------------------------------ */
+/* Solves (M_ee + sigma_i) x_i = b for i < nshift with sigma_0 the base shift.
+ * With A = M_ee + sigma_0 and s_i = sigma_i - sigma_0 the shifted residuals
+ * stay co-linear with the base one, r_i = zeta_i r, and
+ *   zeta_i' = zeta_i zeta_i^- alpha^- /
+ *             (alpha beta^- (zeta_i^- - zeta_i) + zeta_i^- alpha^- (1 + s_i alpha))
+ *   alpha_i = alpha zeta_i'/zeta_i,  beta_i = beta (zeta_i'/zeta_i)^2,
+ *   x_i += alpha_i p_i,  p_i = zeta_i' r + beta_i p_i,
+ * starting from zeta = zeta^- = 1, alpha^- = 1, beta^- = 0.  Shift i stops
+ * updating once zeta_i |r| <= tol_i |b|; the solve ends when every shift has
+ * stopped.  x is [nshift][Vh][3][2]; zeta_out[i] receives the final zeta_i,
+ * iters_out[i] the iteration at which shift i stopped; r_out (may be NULL)
+ * the final base residual.  Returns 0 on convergence, 1 at maxiter, 2 for
+ * an unsupported shift count (1..64). */
+int or_multishift_cg(const int *L, const double *fat, const double *lng, double m,
+                     int nshift, const double *sigma, const double *tol,
+                     const double *b_, double *x_, int maxiter,
+                     int *iters_out, double *zeta_out, double *r_out)
+{
+    if (nshift < 1 || nshift > 64) return 2;
+    op_t op = {L, fat, lng, m, sigma[0], 0};
+    const int64_t n = op_len(&op);
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    cplx *r = malloc(sizeof(cplx) * n), *w = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n * nshift);
+    double *z = malloc(sizeof(double) * nshift), *zm = malloc(sizeof(double) * nshift);
+    int *live = malloc(sizeof(int) * nshift);
+    memcpy(r, b, sizeof(cplx) * n);
+    memset(x, 0, sizeof(cplx) * n * nshift);
+    for (int i = 0; i < nshift; i++) {
+        memcpy(p + i * n, b, sizeof(cplx) * n);
+        z[i] = zm[i] = 1.0;
+        live[i] = 1;
+        iters_out[i] = 0;
+    }
+    const double bnorm = sqrt(nrm2(n, b));
+    double rr = nrm2(n, r), alpha_m = 1.0, beta_m = 0.0;
+    int k = 0, nlive = nshift;
+    while (nlive > 0 && k < maxiter) {
+        op_apply(&op, p, w);
+        const double alpha = rr / creal(cdot(n, p, w));
+        double zn[64], ai[64];
+        for (int i = 0; i < nshift; i++) {
+            if (!live[i]) continue;
+            const double s = sigma[i] - sigma[0];
+            zn[i] = z[i] * zm[i] * alpha_m /
+                    (alpha * beta_m * (zm[i] - z[i]) + zm[i] * alpha_m * (1.0 + s * alpha));
+            ai[i] = alpha * zn[i] / z[i];
+            for (int64_t j = 0; j < n; j++) x[i * n + j] += ai[i] * p[i * n + j];
+        }
+        for (int64_t j = 0; j < n; j++) r[j] -= alpha * w[j];
+        const double rr_new = nrm2(n, r);
+        const double beta = rr_new / rr;
+        k++;
+        for (int i = 0; i < nshift; i++) {
+            if (!live[i]) continue;
+            const double bi = beta * (zn[i] / z[i]) * (zn[i] / z[i]);
+            for (int64_t j = 0; j < n; j++) p[i * n + j] = zn[i] * r[j] + bi * p[i * n + j];
+            zm[i] = z[i];
+            z[i] = zn[i];
+            if (fabs(z[i]) * sqrt(rr_new) <= tol[i] * bnorm) {
+                live[i] = 0;
+                iters_out[i] = k;
+                nlive--;
+            }
+        }
+        rr = rr_new;
+        alpha_m = alpha;
+        beta_m = beta;
+    }
+    for (int i = 0; i < nshift; i++) {
+        zeta_out[i] = z[i];
+        if (live[i]) iters_out[i] = k;
+    }
+    if (r_out) memcpy(r_out, r, sizeof(cplx) * n);
+    free(r);
+    free(w);
+    free(p);
+    free(z);
+    free(zm);
+    free(live);
+    return nlive > 0 ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O8 BiCGStab(l) (Sec. 5.1; Sleijpen and Fokkema 1993), FP64                */
+/* ------------------------------------------------------------------------ */
+/* Solves (2m + D) x = b on the full lattice from x = 0 with shadow residual
+ * r~ = r_0.  Each cycle takes l BiCG steps and then minimises the residual
+ * over the l new directions by modified Gram-Schmidt.  Stops when |r| <=
+ * tol |b| (checked once per cycle).  *matvecs counts operator applications;
+ * *true_res = |b - M x|/|b|.  Returns 0 on convergence, 1 at maxiter
+ * (counted in matvecs), 2 on breakdown. */
+int or_bicgstabl(const int *L, const double *fat, const double *lng, double m, int l,
+                 const double *b_, double *x_, double tol, int max_matvecs,
+                 int *matvecs, double *true_res)
+{
+    op_t op = {L, fat, lng, m, 0.0, 1};
+    const int64_t n = op_len(&op);
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    if (l < 1 || l > 16) return 2;
+    cplx *R = malloc(sizeof(cplx) * n * (l + 1)); /* r_0..r_l */
+    cplx *U = malloc(sizeof(cplx) * n * (l + 1)); /* u_0..u_l */
+    cplx *rt = malloc(sizeof(cplx) * n);
+    memset(x, 0, sizeof(cplx) * n);
+    memcpy(R, b, sizeof(cplx) * n);
+    memcpy(rt, b, sizeof(cplx) * n);
+    memset(U, 0, sizeof(cplx) * n);
+    const double bnorm = sqrt(nrm2(n, b));
+    cplx rho0 = 1, alpha = 0, omega = 1;
+    cplx tau[17][17], gp[17], g[17], gpp[17];
+    double sig[17];
+    int mv = 0, status = 1;
+    if (sqrt(nrm2(n, R)) <= tol * bnorm) status = 0;
+    while (status == 1 && mv < max_matvecs) {
+        rho0 = -omega * rho0;
+        for (int j = 0; j < l; j++) {
+            cplx rho1 = cdot(n, rt, R + j * n);
+            if (cabs(rho0) == 0.0) { status = 2; break; }
+            cplx beta = alpha * rho1 / rho0;
+            rho0 = rho1;
+            for (int i = 0; i <= j; i++)
+                for (int64_t k = 0; k < n; k++) U[i * n + k] = R[i * n + k] - beta * U[i * n + k];
+            op_apply(&op, U + j * n, U + (j + 1) * n);
+            mv++;
+            cplx gam = cdot(n, rt, U + (j + 1) * n);
+            if (cabs(gam) == 0.0) { status = 2; break; }
+            alpha = rho0 / gam;
+            for (int i = 0; i <= j; i++)
+                for (int64_t k = 0; k < n; k++) R[i * n + k] -= alpha * U[(i + 1) * n + k];
+            op_apply(&op, R + j * n, R + (j + 1) * n);
+            mv++;
+            for (int64_t k = 0; k < n; k++) x[k] += alpha * U[k];
+        }
+        if (status == 2) break;
+        for (int j = 1; j <= l; j++) {
+            for (int i = 1; i < j; i++) {
+                tau[i][j] = cdot(n, R + i * n, R + j * n) / sig[i];
+                for (int64_t k = 0; k < n; k++) R[j * n + k] -= tau[i][j] * R[i * n + k];
+            }
+            sig[j] = nrm2(n, R + j * n);
+            if (!(sig[j] > 0.0)) { status = 2; break; }
+            gp[j] = cdot(n, R + j * n, R) / sig[j];
+        }
+        if (status == 2) break;
+        g[l] = gp[l];
+        omega = g[l];
+        for (int j = l - 1; j >= 1; j--) {
+            cplx s = 0;
+            for (int i = j + 1; i <= l; i++) s += tau[j][i] * g[i];
+            g[j] = gp[j] - s;
+        }
+        for (int j = 1; j <= l - 1; j++) {
+            cplx s = 0;
+            for (int i = j + 1; i <= l - 1; i++) s += tau[j][i] * g[i + 1];
+            gpp[j] = g[j + 1] + s;
+        }
+        for (int64_t k = 0; k < n; k++) {
+            x[k] += g[1] * R[k];
+            R[k] -= gp[l] * R[l * n + k];
+            U[k] -= g[l] * U[l * n + k];
+        }
+        for (int j = 1; j <= l - 1; j++)
+            for (int64_t k = 0; k < n; k++) {
+                U[k] -= g[j] * U[j * n + k];
+                x[k] += gpp[j] * R[j * n + k];
+                R[k] -= gp[j] * R[j * n + k];
+            }
+        if (sqrt(nrm2(n, R)) <= tol * bnorm) status = 0;
+    }
+    cplx *t = U; /* reuse as scratch */
+    op_apply(&op, x, t);
+    for (int64_t k = 0; k < n; k++) t[k] = b[k] - t[k];
+    *true_res = sqrt(nrm2(n, t)) / bnorm;
+    *matvecs = mv;
+    free(R);
+    free(U);
+    free(rt);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O9 dense reference                                                        */
+/* ------------------------------------------------------------------------ */
+/* Column k of the operator applied to unit vector e_k (complex, column-major
+ * A[k*n + i] = (A e_k)_i).  which = 0: M_ee + sigma; 1: M = 2m + D full;
+ * 2: the stencil D_eo (rows even, columns odd); 3: D_oe. */
+void or_dense(const int *L, const double *fat, const double *lng, double m, double sigma,
+              int which, double *A_)
+{
+    const int64_t nh = vol_of(L) / 2 * 3;
+    const int64_t n = which == 1 ? 2 * nh : nh;
+    cplx *A = (cplx *)A_;
+    cplx *e = calloc(n, sizeof(cplx));
+    op_t op = {L, fat, lng, m, sigma, which == 1};
+    for (int64_t k = 0; k < n; k++) {
+        e[k] = 1.0;
+        if (which <= 1)
+            op_apply(&op, e, A + k * n);
+        else
+            or_dslash(L, fat, lng, which == 2 ? 0 : 1, (const double *)e, (double *)(A + k * n));
+        e[k] = 0.0;
+    }
+    free(e);
+}
+
+/* Solves A y = rhs in place (y overwrites rhs) by LU with partial pivoting;
+ * A is complex column-major n x n and is overwritten.  Returns 0, or 1 if a
+ * pivot is exactly zero. */
+int or_lu_solve(int64_t n, double *A_, double *rhs_)
+{
+    cplx *A = (cplx *)A_, *y = (cplx *)rhs_;
+#define AE(i, j) A[(j) * n + (i)]
+    for (int64_t k = 0; k < n; k++) {
+        int64_t piv = k;
+        double best = cabs(AE(k, k));
+        for (int64_t i = k + 1; i < n; i++)
+            if (cabs(AE(i, k)) > best) {
+                best = cabs(AE(i, k));
+                piv = i;
+            }
+        if (best == 0.0) return 1;
+        if (piv != k) {
+            for (int64_t j = 0; j < n; j++) {
+                cplx t = AE(k, j);
+                AE(k, j) = AE(piv, j);
+                AE(piv, j) = t;
+            }
+            cplx t = y[k];
+            y[k] = y[piv];
+            y[piv] = t;
+        }
+        for (int64_t i = k + 1; i < n; i++) {
+            const cplx f = AE(i, k) / AE(k, k);
+            AE(i, k) = f;
+            for (int64_t j = k + 1; j < n; j++) AE(i, j) -= f * AE(k, j);
+            y[i] -= f * y[k];
+        }
+    }
+    for (int64_t i = n - 1; i >= 0; i--) {
+        cplx s = y[i];
+        for (int64_t j = i + 1; j < n; j++) s -= AE(i, j) * y[j];
+        y[i] = s / AE(i, i);
+    }
+#undef AE
+    return 0;
+}

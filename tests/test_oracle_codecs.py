@@ -1,0 +1,191 @@
+"""Pins of the oracle's storage formats (CPU only).
+
+* bit patterns derived by hand from the paper's codec rules
+  (``tests/golden/*_vectors.txt``: Appendix A, Listing 4 for 20-bit;
+  Sec. 2, Listing 1 for 16-bit; our stated reading of Listing 3 for 30-bit);
+* round-trip error within the format's epsilon (Sec. 2: 2^-15 relative to the
+  site maximum for the two's-complement 16-bit format; Sec. 3: about 2^-19
+  for 20-bit and 2^-29 for 30-bit);
+* idempotence ``pack(unpack(pack(v))) == pack(v)`` and exact round trip of
+  vectors that are already on the format's grid;
+* fixed-point gauge and reconstruct-12 round trips on random SU(3) links.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2302_09224_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            a, b = line.split("|")
+            rows.append(([float(v) for v in a.split()], b.split()))
+    return rows
+
+
+def test_int20_golden(orc):
+    for vals, words in _read("int20_vectors.txt"):
+        w, bad = orc.int20_pack(np.array([vals], dtype=np.float32))
+        assert bad == 0
+        assert [int(x, 16) for x in words] == [int(x) for x in w[0]], vals
+
+
+def test_int30_golden(orc):
+    for vals, words in _read("int30_vectors.txt"):
+        w, bad = orc.int30_pack(np.array([vals]))
+        assert bad == 0
+        assert [int(x, 16) for x in words] == [int(x) for x in w[0]], vals
+
+
+def test_half_golden(orc):
+    for vals, fields in _read("half_vectors.txt"):
+        rec, bad = orc.half_pack(np.array([vals], dtype=np.float32))
+        assert bad == 0
+        q = np.frombuffer(rec[0, :12].tobytes(), dtype=np.int16)
+        norm = np.frombuffer(rec[0, 12:].tobytes(), dtype=np.float32)[0]
+        assert list(q) == [int(v) for v in fields[:6]], vals
+        assert norm == np.float32(float(fields[6]))
+
+
+def _random_sites(n, seed):
+    g = np.random.Generator(np.random.Philox(key=seed))
+    v = g.standard_normal((n, 6)) * np.exp(g.uniform(-30, 30, size=(n, 1)))
+    v[::17, 2] = 0.0           # sites with zero components
+    v[::31] *= 1e-15          # tiny sites; max/(2^19-1) stays an FP32 normal
+    return v
+
+
+def test_int20_roundtrip_bound_and_idempotence(orc):
+    v = _random_sites(20000, 1).astype(np.float32)
+    w, bad = orc.int20_pack(v)
+    assert bad == 0
+    u = orc.int20_unpack(w)
+    mx = np.abs(v).max(axis=1, keepdims=True)
+    # step 2^(E-127) <= 2 max/(2^19-1): error <= max/(2^19-1) (+ FP32 rounding of t)
+    assert np.all(np.abs(u - v) <= mx / 524287.0 * (1 + 1e-6))
+    w2, _ = orc.int20_pack(u)
+    np.testing.assert_array_equal(w, w2)
+
+
+def test_int20_exact_grid_and_zero(orc):
+    g = np.random.Generator(np.random.Philox(key=4))
+    q = g.integers(-300000, 300001, size=(500, 6))
+    q[:, 0] = 300000  # max |q| in [2^18, 2^19): the scale is exactly 2^-10
+    v = (q * 2.0 ** -10).astype(np.float32)
+    u = orc.int20_unpack(orc.int20_pack(v)[0])
+    np.testing.assert_array_equal(u, v)
+    w, _ = orc.int20_pack(np.zeros((1, 6), np.float32))
+    assert np.all(orc.int20_unpack(w) == 0)
+
+
+def test_int20_exponent_floor(orc):
+    # the smallest exponent is E = 1 (scale 2^-126): sites below the FP32
+    # normal range round onto that grid rather than keeping 20 bits
+    v = np.array([[3e-39, -1e-40, 0, 0, 0, 2e-45]], np.float32)
+    w, _ = orc.int20_pack(v)
+    assert w[0, 3] >> 24 == 1
+    assert np.all(np.abs(orc.int20_unpack(w) - v) <= 2.0 ** -127)
+
+
+def test_int20_nonfinite_flagged(orc):
+    v = np.ones((3, 6), np.float32)
+    v[1, 4] = np.nan
+    v[2, 0] = np.inf
+    _, bad = orc.int20_pack(v)
+    assert bad == 2
+
+
+def test_half_roundtrip_bound_and_idempotence(orc):
+    v = _random_sites(20000, 2).astype(np.float32)
+    rec, bad = orc.half_pack(v)
+    assert bad == 0
+    u = orc.half_unpack(rec)
+    mx = np.abs(v).max(axis=1, keepdims=True)
+    # half a step of max/32767 plus FP32 rounding of the scale and product
+    assert np.all(np.abs(u - v) <= mx * (0.5 / 32767.0 + 3 * 2.0 ** -24))
+    assert np.all(np.abs(u - v) <= mx * 2.0 ** -15)   # the epsilon of Sec. 2
+    # the decoded maximum is max*(1 +- 2^-23), so a second pass may move a
+    # component by one step of the 16-bit grid, never more
+    rec2, _ = orc.half_pack(u)
+    q1 = rec[:, :12].copy().view(np.int16).astype(np.int64)
+    q2 = rec2[:, :12].copy().view(np.int16).astype(np.int64)
+    assert np.abs(q1 - q2).max() <= 1
+
+
+def test_int30_roundtrip_bound_and_idempotence(orc):
+    v = _random_sites(20000, 3)
+    w, bad = orc.int30_pack(v)
+    assert bad == 0
+    u = orc.int30_unpack(w)
+    mx = np.abs(v).max(axis=1, keepdims=True)
+    assert np.all(np.abs(u - v) <= mx / 536870911.0 * (1 + 1e-12))
+    assert np.all(np.abs(u - v) <= mx * 2.0 ** -29)
+    w2, _ = orc.int30_pack(u)
+    np.testing.assert_array_equal(w, w2)
+
+
+def test_int30_exact_grid(orc):
+    g = np.random.Generator(np.random.Philox(key=5))
+    # max |q| in [2^28, 2^29 - 1): t = max/(2^29-1) lies in [2^-41, 2^-40),
+    # so the scale is exactly 2^-40 (a max of 2^29-1 would give t = 2^-40
+    # and round the scale up to 2^-39)
+    q = g.integers(-(2 ** 29 - 2), 2 ** 29 - 1, size=(300, 6))
+    q[:, 3] = 2 ** 29 - 2
+    v = q * 2.0 ** -40
+    np.testing.assert_array_equal(orc.int30_unpack(orc.int30_pack(v)[0]), v)
+
+
+def test_spinor_emulate_orders(orc):
+    """Format error ordering of Sec. 3: int30 << f32 < int20 < half."""
+    v = synth.spinor((4, 4, 4, 4), 7).numpy().reshape(-1, 6)
+    err = {}
+    for f in ("f32", "half", "int20", "int30"):
+        e = orc.spinor_emulate(v, f)
+        err[f] = np.linalg.norm(e - v) / np.linalg.norm(v)
+    assert err["int30"] < 1e-8 < err["f32"] < 1e-6 < err["int20"] < err["half"] < 1e-4
+    assert err["half"] / err["int20"] > 8     # 4 more bits
+    np.testing.assert_array_equal(orc.spinor_emulate(v, "f64"), v)
+
+
+@pytest.mark.parametrize("bits", [16, 32])
+def test_fixed_point_gauge(orc, bits):
+    dims = (4, 4, 4, 4)
+    fat = synth.gauge_field(dims, "fat", seed=9).numpy()
+    gmax = orc.absmax(fat)
+    assert 0.5 < gmax <= 0.8 + 1e-12
+    q = orc.fix_pack(fat, gmax, bits)
+    qm = 32767 if bits == 16 else 2 ** 31 - 1
+    assert np.abs(q).max() == qm
+    d = orc.fix_unpack(q, gmax, bits, compute_f32=False)
+    assert np.abs(d - fat.reshape(-1)).max() <= 0.5 * gmax / qm * (1 + 1e-9)
+    d32 = orc.fix_unpack(q, gmax, bits, compute_f32=True)
+    np.testing.assert_array_equal(d32, (q.astype(np.float32) * np.float32(gmax / qm)).astype(np.float64))
+
+
+def test_reconstruct12(orc):
+    dims = (4, 4, 4, 6)
+    for anti in (False, True):
+        lng = synth.gauge_field(dims, "long", seed=4, antiperiodic_t=anti).numpy()
+        e = orc.gauge_emulate(dims, lng, "f64", 12, long_link=True, antiperiodic_t=anti)
+        assert np.abs(e - lng).max() <= 1e-14
+        # with the wrong boundary sign the t-boundary links come back negated
+        bad = orc.gauge_emulate(dims, lng, "f64", 12, long_link=True, antiperiodic_t=not anti)
+        assert np.abs(bad - lng).max() > 1.0
+    fat = synth.gauge_field(dims, "fat", seed=4).numpy()
+    # fat links are 0.8 eta U: not in SU(3) up to a sign, so row 2 is not rebuilt by r12
+    e = orc.gauge_emulate(dims, fat, "f64", 12, long_link=False)
+    assert np.abs(e - fat).max() > 0.1
+    lng = synth.gauge_field(dims, "long", seed=4).numpy()
+    e32 = orc.gauge_emulate(dims, lng, "f32", 12, long_link=True)
+    assert np.abs(e32 - lng).max() <= 1e-6
+    e16 = orc.gauge_emulate(dims, lng, "fix16", 12, long_link=True, compute_f32=False)
+    assert np.abs(e16 - lng).max() <= 4.0 / 32767
