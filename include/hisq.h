@@ -1,0 +1,275 @@
+/*
+ * hisq.h -- C ABI of the GB300 (sm_103a) HISQ staggered stencil with reduced-bit
+ * storage formats and the stabilised mixed-precision Krylov solvers of
+ * M. A. Clark, D. Howarth, J. Tu, M. Wagner, E. Weinberg,
+ * "Maximizing the Bang Per Bit" (Lattice 2022).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice extents dims = {Lx, Ly, Lz, Lt}, each even and >= 2 (the even/odd
+ * decomposition needs even extents).  lex = ((t*Lz + z)*Ly + y)*Lx + x,
+ * parity(x) = (x+y+z+t) mod 2, checkerboard index cb = lex/2, V = Lx*Ly*Lz*Lt,
+ * Vh = V/2.
+ *
+ * Host gauge layout (both link fields): double [mu][t][z][y][x][3][3][re,im],
+ * links already multiplied by the staggered phases eta_mu(x) (and by the
+ * boundary sign if antiperiodic in t).
+ *
+ * Spinor layout seen by callers: double [cb][color][re,im] on one parity
+ * (half lattice, Vh*6 doubles) or [parity][cb][color][re,im] on the full
+ * lattice (even first, V*6 doubles).  Pointers are host pointers unless the
+ * call's on_device flag is set, in which case they are device pointers of the
+ * context's GPU (e.g. a torch tensor's data_ptr()).  The caller keeps
+ * ownership of every pointer it passes; the library never frees them.
+ *
+ * The stencil (the HISQ operator of Sec. 1 and Sec. 4.2, whose form the paper
+ * does not write out; see the design notes for this reading):
+ *   (D psi)(x) = sum_mu [ F_mu(x) psi(x+mu) - F_mu(x-mu)^+ psi(x-mu)
+ *                       + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^+ psi(x-3mu) ]
+ * with fat links F and long (Naik) links L.  D is anti-Hermitian;
+ * D_eo / D_oe are its parity blocks (output even / odd).  Full-lattice
+ * operator M = 2m + D; even-even normal operator M_ee = 4m^2 - D_eo D_oe.
+ *
+ * Errors: every call returns a hisq_status; nothing aborts or exits.  After a
+ * failure hisq_last_error() describes it.  A context is not safe for
+ * concurrent calls from several threads except hisq_submit / hisq_poll.
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HISQ_API __attribute__((visibility("default")))
+#else
+#define HISQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HISQ_OK = 0,
+    HISQ_EINVAL = 1,      /* bad argument, unsupported combination, non-finite input */
+    HISQ_ENOMEM = 2,      /* HBM budget or device allocation exhausted */
+    HISQ_ENOTCONV = 3,    /* solver hit maxiter; best x returned, info filled */
+    HISQ_EBREAKDOWN = 4,  /* solver recurrence broke down (zero or non-finite scalar) */
+    HISQ_ECUDA = 5,       /* a CUDA runtime call failed */
+    HISQ_EBUSY = 6,       /* request queue full */
+    HISQ_ETIMEOUT = 7,    /* bounded wait expired */
+    HISQ_ENOTFOUND = 8    /* unknown ticket or gauge */
+} hisq_status;
+
+/* Storage format of the gauge field (Sec. 3, the three-precision triplet). */
+typedef enum {
+    HISQ_GAUGE_F64 = 0,
+    HISQ_GAUGE_F32 = 1,
+    HISQ_GAUGE_FIX16 = 2, /* 16-bit fixed point, scale = global max (Sec. 2 footnote) */
+    HISQ_GAUGE_FIX32 = 3  /* 32-bit fixed point, scale = global max (Sec. 3) */
+} hisq_gauge_fmt;
+
+/* Storage format of the fermion (spinor) field. */
+typedef enum {
+    HISQ_SPINOR_F64 = 0,    /* 48 B/site */
+    HISQ_SPINOR_F32 = 1,    /* 24 B/site */
+    HISQ_SPINOR_HALF16 = 2, /* 16 B/site: int16 v[6] + FP32 site max (Sec. 2, Listing 1) */
+    HISQ_SPINOR_INT20 = 3,  /* 16 B/site: 6 x int20 + 8-bit exponent (Sec. 3 Listing 2; Appendix A) */
+    HISQ_SPINOR_INT30 = 4   /* 24 B/site: 6 x int30 + 8-bit exponent (Sec. 3, Listing 3) */
+} hisq_spinor_fmt;
+
+/* Arithmetic precision (the third member of the triplet, Sec. 3). */
+typedef enum { HISQ_COMPUTE_F32 = 0, HISQ_COMPUTE_F64 = 1 } hisq_compute_fmt;
+
+/* Precision triplet gauge / fermion / compute plus link compression (Sec. 1:
+ * 18 -> 12 reals by SU(3) unitarity).  Supported combinations:
+ *   F64/F64/F64, F32/F32/F32, FIX16/HALF16/F32, FIX16/INT20/F32,
+ *   FIX32/INT30/F64, FIX32/INT30/F32;
+ * fat_recon must be 18 (smeared fat links are not unitary); long_recon 18 or
+ * 12 (12 needs long links that are a sign times SU(3), checked at load). */
+typedef struct {
+    int32_t gauge;      /* hisq_gauge_fmt */
+    int32_t spinor;     /* hisq_spinor_fmt */
+    int32_t compute;    /* hisq_compute_fmt */
+    int32_t fat_recon;  /* 18 */
+    int32_t long_recon; /* 18 or 12 */
+} hisq_prec;
+
+typedef struct hisq_ctx hisq_ctx;
+typedef struct hisq_gauge hisq_gauge;
+
+/* hisq_load_gauge flags */
+#define HISQ_GAUGE_ANTIPERIODIC_T 0x1u /* links crossing the t boundary carry -1 */
+#define HISQ_GAUGE_ON_DEVICE 0x2u      /* fat/lng are device pointers */
+
+/* Create a context on CUDA device `device`.  hbm_budget bounds the device
+ * memory the context may hold (0: 90% of the free memory at creation).  The
+ * context owns every device buffer, stream and scratch area it makes.
+ * Errors: EINVAL (bad device, out == NULL), ECUDA. */
+HISQ_API hisq_status hisq_create(int device, size_t hbm_budget, hisq_ctx **out);
+
+/* Release a context and everything it owns (gauge fields included). */
+HISQ_API void hisq_destroy(hisq_ctx *ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+HISQ_API const char *hisq_last_error(hisq_ctx *ctx);
+
+/* Device bytes the context currently holds. */
+HISQ_API size_t hisq_mem_used(hisq_ctx *ctx);
+
+/* Load a gauge configuration (Sec. 2 footnote, Sec. 3: one global scale per
+ * fixed-point field).  fat and lng are FP64 in the host gauge layout
+ * (4*V*18 doubles each).  The data are copied: an FP64 copy of each field
+ * stays resident for true residuals; reduced formats are built from it on
+ * first use.  Checks: extents even and >= 2 (EINVAL), every entry finite
+ * (EINVAL), budget (ENOMEM).  Whether each field can be compressed to 12 reals
+ * (a sign times SU(3), to 1e-6) is recorded; asking for r12 on a field that
+ * cannot be returns EINVAL at use.  Free with hisq_free_gauge. */
+HISQ_API hisq_status hisq_load_gauge(hisq_ctx *ctx, const int dims[4], const double *fat, const double *lng,
+                            unsigned flags, hisq_gauge **out);
+
+HISQ_API void hisq_free_gauge(hisq_ctx *ctx, hisq_gauge *g);
+
+/* Global max |element| of the fat (which = 0) or long (which = 1) field: the
+ * fixed-point scale of Sec. 2 footnote. */
+HISQ_API double hisq_gauge_scale(const hisq_gauge *g, int which);
+
+/* One application of the stencil in precision `prec` (Sec. 4.2-4.3: the
+ * fields are stored in the reduced formats, unpacked to the compute precision
+ * in registers and repacked on store):
+ *   out = a * xpay_in - D in      (a != 0)
+ *   out = D in                    (a == 0; xpay_in may be NULL)
+ * out_parity 0: out on even sites, in on odd sites (D_eo); 1: the reverse
+ * (D_oe); 2: full lattice (in, out, xpay_in full-lattice arrays).
+ * in / out / xpay_in are FP64 arrays in the caller's spinor layout; the input
+ * (and xpay_in) is rounded into the spinor storage format first, and the
+ * output is the decoded storage-format result.  on_device selects device or
+ * host pointers; stream is a cudaStream_t (NULL: the context's stream).
+ * Errors: EINVAL (unsupported prec, r12 not possible, non-finite input),
+ * ENOMEM, ECUDA. */
+HISQ_API hisq_status hisq_dslash(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec prec, int out_parity, double a,
+                        const double *xpay_in, const double *in, double *out, int on_device,
+                        void *stream);
+
+/* Device bytes of one half-lattice (n sites) spinor field in format sfmt, in
+ * this library's planar layout: the site record is split into 16-byte planes
+ * [plane][site] followed by one narrower tail plane (F32 and INT30: 16 + 8 B;
+ * F64: 3 x 16 B; HALF16 and INT20: one 16-B record = the paper's struct). */
+HISQ_API size_t hisq_spinor_bytes(int sfmt, int64_t n);
+
+/* Encode n sites (FP64 [n][6] on the device) into format sfmt (planar layout
+ * above) on the device, exactly as every kernel of the library stores a
+ * field: HALF16 and INT20 round the input to FP32 first and encode in FP32
+ * (Appendix A arithmetic for INT20); INT30 encodes in FP64.  *n_bad receives
+ * the number of sites with a non-finite (or, for INT30, unencodable)
+ * component; such sites are stored as zero.  Device pointers only. */
+HISQ_API hisq_status hisq_spinor_pack(hisq_ctx *ctx, int sfmt, int64_t n, const double *in, void *packed,
+                             int64_t *n_bad, void *stream);
+
+/* Decode n sites of format sfmt into FP64 [n][6] (device pointers).  compute
+ * selects the precision of the decode (F32 decodes as the F32 kernels do). */
+HISQ_API hisq_status hisq_spinor_unpack(hisq_ctx *ctx, int sfmt, int compute, int64_t n, const void *packed,
+                               double *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Kernel classes timed by the profiler. */
+#define HISQ_PROF_STENCIL 0     /* stencil passes in the call's (sloppy) precision */
+#define HISQ_PROF_STENCIL_HI 1  /* FP64 stencil passes of true residuals */
+#define HISQ_PROF_BLAS 2        /* fused BLAS-1 / reduction kernels */
+#define HISQ_PROF_CONVERT 3     /* format conversions */
+
+typedef struct {
+    double ms;          /* summed device time of the timed launches */
+    int64_t launches;   /* launches timed */
+    double bytes;       /* summed algorithmic bytes of those launches: each
+                           array touched once per launch (links, input and
+                           output spinors, xpay input) */
+} hisq_kernel_stats;
+
+/* While enabled, every launch made outside stream capture (solvers run their
+ * iterations without graphs then) is bracketed by CUDA events on its own
+ * stream and accumulated per class.  Reading synchronises on the events. */
+HISQ_API void hisq_profile_enable(hisq_ctx *ctx, int on);
+HISQ_API void hisq_profile_reset(hisq_ctx *ctx);
+HISQ_API hisq_status hisq_profile_read(hisq_ctx *ctx, int kind, hisq_kernel_stats *out);
+
+/* Kernels this context has launched so far (graph replays add their nodes). */
+HISQ_API int64_t hisq_launch_count(hisq_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Solvers                                                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double mass;          /* m */
+    double tol;           /* target |b - A x| / |b| on the FP64 true residual */
+    int32_t maxiter;      /* iteration cap (CG iterations; BiCGStab(l): matvecs) */
+    double delta;         /* reliable-update trigger (Sec. 2 footnote: 0.1) */
+    hisq_prec sloppy;     /* precision of the iterated vectors and matvecs */
+    hisq_prec refine;     /* multi-shift: precision of the refinement CG (Sec. 2.2) */
+    int32_t nbuf;         /* gradient vectors buffered before x is updated (Sec. 2.1 item 1); 1..16 */
+    int32_t use_init_guess; /* x holds the initial guess */
+    int32_t on_device;    /* b and x are device pointers */
+    int32_t pr_beta;      /* 1: Polak-Ribiere beta (Sec. 2.1 item 3), 0: Fletcher-Reeves */
+    int32_t reproject;    /* 1: re-project p at each reliable update (Sec. 2.1 item 2) */
+    int32_t l;            /* BiCGStab(l): l (Sec. 5.1 uses 4), 1..8 */
+    int32_t use_graph;    /* 1: replay each block of iterations as a CUDA graph */
+    void *stream;         /* cudaStream_t; NULL: the context's stream */
+} hisq_solver_params;
+
+/* Fills params with the defaults: delta 0.1, nbuf 8, pr_beta 1, reproject 1,
+ * l 4, use_graph 1, maxiter 100000, tol 1e-10, sloppy and refine
+ * FIX16/INT20/F32 with r12 long links. */
+HISQ_API void hisq_default_params(hisq_solver_params *p);
+
+#define HISQ_MAX_SHIFTS 32
+
+typedef struct {
+    int32_t iters;              /* iterations (CG) or BiCGStab(l) cycles */
+    int32_t matvecs;            /* operator applications in the sloppy precision */
+    int32_t matvecs_hi;         /* operator applications in FP64 (true residuals) */
+    int32_t reliable_updates;
+    double true_residual;       /* |b - A x| / |b| in FP64 at exit */
+    double seconds;             /* wall time of the solve */
+    int32_t nshift;
+    int32_t shift_iters[HISQ_MAX_SHIFTS];    /* multi-shift: iteration at which shift i froze */
+    double shift_resid_ms[HISQ_MAX_SHIFTS];  /* true residual of shift i after the multi-shift stage */
+    double shift_resid[HISQ_MAX_SHIFTS];     /* final true residual of shift i */
+    int32_t refine_iters[HISQ_MAX_SHIFTS];   /* refinement CG iterations of shift i */
+} hisq_solve_info;
+
+/* Even/odd CG (Sec. 2.1): solves (4m^2 - D_eo D_oe) x = b on the even sites
+ * with the sloppy triplet for the iterated residual and gradient vectors,
+ * FP64 for x (accumulated from nbuf buffered gradient vectors), reliable
+ * updates with an FP64 true residual whenever |r| drops below delta times its
+ * maximum since the last update, re-projection of p and Polak-Ribiere beta.
+ * With sloppy = F64/F64/F64 this is plain FP64 CG.  b, x: half-lattice FP64.
+ * Returns OK, ENOTCONV (x is the best iterate, info filled), EBREAKDOWN,
+ * EINVAL, ENOMEM, ECUDA. */
+HISQ_API hisq_status hisq_cg(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
+                    double *x, hisq_solve_info *info);
+
+/* Multi-shift CG (Sec. 2.2): solves (M_ee + sigma_i) x_i = b for nshift
+ * shifts (<= HISQ_MAX_SHIFTS) in the sloppy precision with reliable updates on
+ * the base (smallest) shift; shift i freezes when its iterated residual
+ * reaches tol[i] or the sloppy format's precision floor; then refinement CG in
+ * p->refine: the base system continuing with its gradient vector, the other
+ * shifts restarted from their x_i.  x[i]: half-lattice FP64 arrays. */
+HISQ_API hisq_status hisq_multishift_cg(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, int nshift,
+                               const double *sigma, const double *tol, const double *b, double *const *x,
+                               hisq_solve_info *info);
+
+/* BiCGStab(l) (Sec. 5.1) on the full-lattice M = 2m + D with sloppy vectors,
+ * FP64 x and a reliable update at the end of a cycle when triggered. */
+HISQ_API hisq_status hisq_bicgstabl(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
+                           double *x, hisq_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HISQ_H */

@@ -235,7 +235,9 @@ static float u2f(uint32_t u)
 /* 16-bit fixed point with a site-local FP32 norm (Sec. 2, Listing 1): record
  * of 16 bytes = int16 v[6] followed by float max.  The largest |component| of
  * the site sets the scale; components are rounded to nearest-even integers in
- * [-32767, 32767].  Decoding multiplies by max * fl(1/32767).
+ * [-32767, 32767].  Decoding multiplies by max * fl(1/32767).  A site whose
+ * max is below 2^-110 (where 32767/max would overflow FP32) is stored as zero
+ * with norm 0, like an all-zero site.
  * Returns the number of sites with a non-finite component. */
 int64_t or_half_pack(int64_t n, const float *v, unsigned char *rec)
 {
@@ -252,7 +254,9 @@ int64_t or_half_pack(int64_t n, const float *v, unsigned char *rec)
         if (!finite) {
             bad++;
             mx = 0.0f;
-        } else if (mx > 0.0f) {
+        } else if (mx < 0x1p-110f) {
+            mx = 0.0f;
+        } else {
             const float inv = 32767.0f / mx;
             for (int i = 0; i < 6; i++) {
                 long r = lrintf(x[i] * inv);

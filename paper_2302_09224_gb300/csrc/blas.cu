@@ -1,0 +1,203 @@
+// blas.cu -- fused BLAS-1 kernels of the stabilised mixed-precision CG
+// (Sec. 2.1), each a single pass over its vectors in the sloppy storage
+// format with the reduction it needs fused in (deterministic, FP64):
+//   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta)
+//   p_update      p' <- r + beta p       (into the next ring slot)
+//   x_flush       x_hi <- x_hi + sum_j alpha_j p_j   (buffered gradient vectors)
+//   true_residual r_hi <- b - A x_hi (FP64), r <- r_hi (sloppy),
+//                 |r_hi|^2 and <r_hi, p> for the re-projection of p
+//   p_reliable    p' <- coef r_hi + beta p   (re-projected FR restart)
+//   norm2         |v|^2 of an FP64 field
+#include <cuda_runtime.h>
+
+#include "blas.h"
+#include "codecs.cuh"
+#include "finish.cuh"
+#include "reduce.cuh"
+
+namespace hisq {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ bool skip(const int *active)
+{
+    return active != nullptr && *(volatile const int *)active == 0;
+}
+
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
+{
+    if (skip(a.active)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (i < a.n) {
+        real r[6], ap[6], rn[6];
+        Spinor<SF>::load(a.v0, a.n, i, r);
+        Spinor<SF>::load(a.v1, a.n, i, ap);
+        const real alpha = (real)a.st->alpha;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            rn[k] = r[k] - alpha * ap[k];
+            v[0] += (double)rn[k] * (double)rn[k];
+            v[1] += (double)rn[k] * (double)r[k];
+        }
+        if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
+    }
+    __shared__ double tot[2];
+    if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
+}
+
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
+{
+    if (skip(a.active)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.clear_ring && i == 0)
+        for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
+    if (i >= a.n) return;
+    real r[6], p[6];
+    Spinor<SF>::load(a.v0, a.n, i, r);
+    Spinor<SF>::load(a.v1, a.n, i, p);
+    const real beta = (real)a.st->beta;
+#pragma unroll
+    for (int k = 0; k < 6; k++) p[k] = r[k] + beta * p[k];
+    if (!Spinor<SF>::store(a.v2, a.n, i, p)) atomicExch(a.err, 1);
+}
+
+// x_hi += sum_{j < nslots} alpha_j p_j; slots are consecutive fields of
+// slot_bytes each starting at v0.  Unused slots carry alpha_j = 0.
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
+{
+    if (skip(a.active)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    double x[6];
+    Spinor<S_F64>::load(reinterpret_cast<const char *>(a.x64), a.n, i, x);
+    for (int j = 0; j < a.nslots; j++) {
+        const double al = a.st->alpha_ring[j];
+        if (al == 0.0) continue;
+        real p[6];
+        Spinor<SF>::load(a.v0 + (size_t)j * a.slot_bytes, a.n, i, p);
+#pragma unroll
+        for (int k = 0; k < 6; k++) x[k] += al * (double)p[k];
+    }
+    Spinor<S_F64>::store(reinterpret_cast<char *>(a.x64), a.n, i, x);
+}
+
+// r_hi = b - Ax (FP64); r (sloppy) = r_hi; sums for FIN_CG_TRUE with p = v1.
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) true_residual_kernel(BlasArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (i < a.n) {
+        double b[6], ax[6], r[6];
+        Spinor<S_F64>::load(reinterpret_cast<const char *>(a.b64), a.n, i, b);
+        if (a.ax64 != nullptr)
+            Spinor<S_F64>::load(reinterpret_cast<const char *>(a.ax64), a.n, i, ax);
+        else
+#pragma unroll
+            for (int k = 0; k < 6; k++) ax[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) r[k] = b[k] - ax[k];
+        Spinor<S_F64>::store(reinterpret_cast<char *>(a.r64), a.n, i, r);
+        if (!Spinor<SF>::store(a.v0, a.n, i, r)) atomicExch(a.err, 1);
+        real p[6];
+        Spinor<SF>::load(a.v1, a.n, i, p);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double rr = r[2 * c], ri = r[2 * c + 1], pr = p[2 * c], pi = p[2 * c + 1];
+            v[0] += rr * rr + ri * ri;
+            v[1] += rr * pr + ri * pi;  // Re conj(r) p
+            v[2] += rr * pi - ri * pr;  // Im conj(r) p
+        }
+    }
+    __shared__ double tot[3];
+    if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) run_finisher(FIN_CG_TRUE, tot, a.st, a.slot);
+}
+
+// p' = coef r_hi + beta p (coef complex); clears the alpha ring.
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) p_reliable_kernel(BlasArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0)
+        for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
+    if (i >= a.n) return;
+    double r[6];
+    real p[6], o[6];
+    Spinor<S_F64>::load(reinterpret_cast<const char *>(a.r64), a.n, i, r);
+    Spinor<SF>::load(a.v1, a.n, i, p);
+    const double cr = a.st->coef_re, ci = a.st->coef_im, beta = a.st->beta;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[2 * c] = (real)(cr * r[2 * c] - ci * r[2 * c + 1] + beta * (double)p[2 * c]);
+        o[2 * c + 1] = (real)(cr * r[2 * c + 1] + ci * r[2 * c] + beta * (double)p[2 * c + 1]);
+    }
+    if (!Spinor<SF>::store(a.v2, a.n, i, o)) atomicExch(a.err, 1);
+}
+
+__global__ void __launch_bounds__(kBlock) norm2_kernel(BlasArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (i < a.n) {
+        double x[6];
+        Spinor<S_F64>::load(reinterpret_cast<const char *>(a.x64), a.n, i, x);
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[0] += x[k] * x[k];
+    }
+    __shared__ double tot[1];
+    reduce_grid<1>(v, a.red, tot);
+}
+
+int nblk(int n) { return (n + kBlock - 1) / kBlock; }
+
+}  // namespace
+
+#define HISQ_SF_DISPATCH(SF_, CF_, KERNEL, ...)                                              \
+    do {                                                                                    \
+        const bool f64_ = (CF_) == HISQ_COMPUTE_F64;                                        \
+        switch (SF_) {                                                                      \
+        case S_F64: KERNEL<S_F64, double><<<__VA_ARGS__>>>(a); break;                       \
+        case S_F32: KERNEL<S_F32, float><<<__VA_ARGS__>>>(a); break;                        \
+        case S_HALF: KERNEL<S_HALF, float><<<__VA_ARGS__>>>(a); break;                      \
+        case S_INT20: KERNEL<S_INT20, float><<<__VA_ARGS__>>>(a); break;                    \
+        case S_INT30:                                                                       \
+            if (f64_) KERNEL<S_INT30, double><<<__VA_ARGS__>>>(a);                          \
+            else KERNEL<S_INT30, float><<<__VA_ARGS__>>>(a);                                \
+            break;                                                                          \
+        }                                                                                   \
+    } while (0)
+
+void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+{
+    HISQ_SF_DISPATCH(sf, cf, r_update_kernel, nblk(a.n), kBlock, 0, s);
+}
+
+void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+{
+    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, nblk(a.n), kBlock, 0, s);
+}
+
+void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+{
+    HISQ_SF_DISPATCH(sf, cf, x_flush_kernel, nblk(a.n), kBlock, 0, s);
+}
+
+void launch_true_residual(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+{
+    HISQ_SF_DISPATCH(sf, cf, true_residual_kernel, nblk(a.n), kBlock, 0, s);
+}
+
+void launch_p_reliable(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+{
+    HISQ_SF_DISPATCH(sf, cf, p_reliable_kernel, nblk(a.n), kBlock, 0, s);
+}
+
+void launch_norm2(const BlasArgs &a, cudaStream_t s) { norm2_kernel<<<nblk(a.n), kBlock, 0, s>>>(a); }
+
+}  // namespace hisq

@@ -1,0 +1,480 @@
+// cg.cu -- the stabilised mixed-precision even/odd CG of Sec. 2.1 and its C-ABI
+// entry point.
+//
+// Sloppy precision (the triplet's formats): iterated residual r, gradient
+// vectors p (a ring of nbuf slots) and the operator applications.  FP64: the
+// solution x_hi, the right-hand side, every true residual and all reductions.
+//   * reliable updates (Sec. 2, footnote): when |r| drops below delta times
+//     its maximum since the last update, x_hi is brought up to date, the true
+//     residual b - A x_hi is computed in FP64 and replaces r;
+//   * item 1: x_hi += sum_j alpha_j p_j once per nbuf iterations (and at each
+//     reliable update) from the buffered gradient vectors;
+//   * item 2: at a reliable update p is re-projected against the new residual
+//     and the recurrence restarts with Fletcher-Reeves beta;
+//   * item 3: beta = r_new^+(r_new - r_old)/|r_old|^2 (Polak-Ribiere).
+// One block of nbuf iterations is a fixed kernel sequence whose scalars live
+// on the device, so it is captured once as a CUDA graph and replayed; the host
+// reads the scalar state once per block.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "blas.h"
+#include "cg.h"
+#include "internal.h"
+
+namespace hisq {
+
+Workspace::~Workspace()
+{
+    if (!allocs.empty()) cudaStreamSynchronize(s);
+    for (auto &a : allocs) ctx_free(c, a.first, a.second);
+}
+
+hisq_status Workspace::alloc(size_t bytes, void **p)
+{
+    hisq_status st = ctx_alloc(c, bytes, p);
+    if (!st) allocs.emplace_back(*p, bytes);
+    return st;
+}
+
+double stencil_bytes(const hisq_prec &p, int vh, bool xpay)
+{
+    const double links = 8.0 * link_bytes(p.gauge, p.fat_recon) + 8.0 * link_bytes(p.gauge, p.long_recon);
+    return (links + (xpay ? 3.0 : 2.0) * spinor_site_bytes(p.spinor)) * vh;
+}
+
+hisq_prec prec_f64()
+{
+    hisq_prec p;
+    p.gauge = G_F64;
+    p.spinor = S_F64;
+    p.compute = HISQ_COMPUTE_F64;
+    p.fat_recon = 18;
+    p.long_recon = 18;
+    return p;
+}
+
+// out_even = diag * in_even - D_eo D_oe in_even, with tmp an odd-parity field.
+void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
+               const char *in, char *tmp, char *out, int fin, CGState *st, int slot, const int *active, int kind,
+               cudaStream_t s)
+{
+    DslashArgs d{};
+    d.g = geom;
+    d.gv = gv;
+    d.err = c->err_flag;
+    d.red = c->red;
+    d.active = active;
+    d.st = st;
+    d.slot = slot;
+    d.out_parity = 1;
+    d.in = in;
+    d.out = tmp;
+    d.sign = 1;
+    {
+        LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, false));
+        launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, false, d, s);
+    }
+    d.out_parity = 0;
+    d.in = tmp;
+    d.out = out;
+    d.y = in;
+    d.a = diag;
+    d.sign = -1;
+    d.xpay = 1;
+    d.fin = fin;
+    {
+        LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, true));
+        launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d, s);
+    }
+}
+
+namespace {
+
+struct CGRun {
+    hisq_ctx *c;
+    hisq_gauge *g;
+    const CGConfig &cfg;
+    cudaStream_t s;
+    Workspace ws;
+    int vh;
+    size_t sb;
+    char *r_s = nullptr, *ap_s = nullptr, *tmp_s = nullptr, *ring = nullptr;
+    double *r64 = nullptr, *ax64 = nullptr, *tmp64 = nullptr;
+    CGState *st = nullptr;
+    CGState *st_h = nullptr;
+    GaugeView gv_s{}, gv_d{};
+    double diag = 0;
+    int ru = 0, mv_hi = 0;
+
+    CGRun(hisq_ctx *c_, hisq_gauge *g_, const CGConfig &cfg_, cudaStream_t s_)
+        : c(c_), g(g_), cfg(cfg_), s(s_), ws(c_, s_), vh(g_->geom.vh)
+    {
+    }
+    ~CGRun()
+    {
+        if (st_h) cudaFreeHost(st_h);
+    }
+
+    char *slot(int j) { return ring + (size_t)j * sb; }
+
+    BlasArgs blas() const
+    {
+        BlasArgs a{};
+        a.n = vh;
+        a.err = c->err_flag;
+        a.red = c->red;
+        a.st = st;
+        return a;
+    }
+
+    hisq_status setup()
+    {
+        hisq_status e = gauge_view_for(c, g, cfg.sloppy, &gv_s);
+        if (!e) e = gauge_view_for(c, g, prec_f64(), &gv_d);
+        if (e) return e;
+        sb = spinor_field_bytes(cfg.sloppy.spinor, vh);
+        const size_t b64 = (size_t)48 * vh;
+        e = ws.alloc(sb, (void **)&r_s);
+        if (!e) e = ws.alloc(sb, (void **)&ap_s);
+        if (!e) e = ws.alloc(sb, (void **)&tmp_s);
+        if (!e) e = ws.alloc(sb * cfg.nbuf, (void **)&ring);
+        if (!e) e = ws.alloc(b64, (void **)&r64);
+        if (!e) e = ws.alloc(b64, (void **)&ax64);
+        if (!e) e = ws.alloc(b64, (void **)&tmp64);
+        if (!e) e = ws.alloc(sizeof(CGState), (void **)&st);
+        if (e) return e;
+        if (cudaMallocHost(&st_h, sizeof(CGState)) != cudaSuccess)
+            return fail(c, HISQ_ENOMEM, "pinned host state");
+        cudaMemsetAsync(ring, 0, sb * cfg.nbuf, s);
+        diag = 4.0 * cfg.mass * cfg.mass + cfg.sigma;
+        return HISQ_OK;
+    }
+
+    hisq_status pull_state()
+    {
+        cudaMemcpyAsync(st_h, st, sizeof(CGState), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "CG state");
+        return HISQ_OK;
+    }
+
+    // x_hi += sum over the first nslots ring slots (alpha ring on the device)
+    void flush(int nslots, const int *active, double *x64)
+    {
+        BlasArgs a = blas();
+        a.v0 = ring;
+        a.slot_bytes = sb;
+        a.nslots = nslots;
+        a.x64 = x64;
+        a.active = active;
+        LaunchScope ls(c, s, PROF_BLAS, (48.0 * 2 + (double)nslots * spinor_site_bytes(cfg.sloppy.spinor)) * vh);
+        launch_x_flush(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+    }
+
+    // True residual and restart of the recurrence from p in slot j into slot 0.
+    hisq_status reliable_update(const double *b64, double *x64, bool x_zero, int j)
+    {
+        if (!x_zero) {
+            apply_mee(c, g->geom, prec_f64(), gv_d, diag, (const char *)x64, (char *)tmp64, (char *)ax64, FIN_NONE,
+                      nullptr, 0, nullptr, PROF_STENCIL_HI, s);
+            mv_hi++;
+        }
+        BlasArgs a = blas();
+        a.b64 = b64;
+        a.ax64 = x_zero ? nullptr : ax64;
+        a.r64 = r64;
+        a.v0 = r_s;
+        a.v1 = slot(j);
+        a.slot = j;
+        {
+            LaunchScope ls(c, s, PROF_BLAS, (48.0 * 3 + 2.0 * spinor_site_bytes(cfg.sloppy.spinor)) * vh);
+            launch_true_residual(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+        }
+        a.v1 = slot(j);
+        a.v2 = slot(0);
+        {
+            LaunchScope ls(c, s, PROF_BLAS, (48.0 + 2.0 * spinor_site_bytes(cfg.sloppy.spinor)) * vh);
+            launch_p_reliable(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+        }
+        return pull_state();
+    }
+
+    // One block of nbuf iterations starting at ring slot 0.
+    void iterate_block(double *x64)
+    {
+        const int N = cfg.nbuf;
+        const int *act = &st->active;
+        for (int i = 0; i < N; i++) {
+            apply_mee(c, g->geom, cfg.sloppy, gv_s, diag, slot(i), tmp_s, ap_s, FIN_CG_ALPHA, st, i, act,
+                      PROF_STENCIL, s);
+            BlasArgs a = blas();
+            a.active = act;
+            a.slot = i;
+            a.v0 = r_s;
+            a.v1 = ap_s;
+            {
+                LaunchScope ls(c, s, PROF_BLAS, 3.0 * spinor_site_bytes(cfg.sloppy.spinor) * vh);
+                launch_r_update(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+            }
+            if (i == N - 1) flush(N, act, x64);
+            a.v0 = r_s;
+            a.v1 = slot(i);
+            a.v2 = slot((i + 1) % N);
+            a.clear_ring = i == N - 1;
+            {
+                LaunchScope ls(c, s, PROF_BLAS, 3.0 * spinor_site_bytes(cfg.sloppy.spinor) * vh);
+                launch_p_update(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+            }
+        }
+    }
+
+    hisq_status run(const double *b64, double *x64, bool x_zero, hisq_solve_info *info)
+    {
+        hisq_status e = setup();
+        if (e) return e;
+        // |b|^2
+        {
+            BlasArgs a = blas();
+            a.x64 = const_cast<double *>(b64);
+            LaunchScope ls(c, s, PROF_BLAS, 48.0 * vh);
+            launch_norm2(a, s);
+        }
+        double bb = 0.0;
+        cudaMemcpyAsync(&bb, c->red.result, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "norm");
+        info->iters = 0;
+        info->reliable_updates = 0;
+        if (!std::isfinite(bb)) return fail(c, HISQ_EINVAL, "non-finite right-hand side");
+        if (bb == 0.0) {
+            cudaMemsetAsync(x64, 0, (size_t)48 * vh, s);
+            info->true_residual = 0.0;
+            cudaStreamSynchronize(s);
+            return HISQ_OK;
+        }
+        CGState init{};
+        init.delta2 = cfg.delta * cfg.delta;
+        init.stop2 = cfg.tol * cfg.tol * bb;
+        init.pr = cfg.pr;
+        init.reproject = cfg.reproject;
+        init.active = 1;
+        cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s);
+        e = reliable_update(b64, x64, x_zero, 0);
+        if (e) return e;
+        hisq_status status = HISQ_OK;
+        bool done = st_h->hi_rr <= init.stop2;
+        const bool graph = cfg.use_graph && !c->prof.on;
+        cudaGraphExec_t exec = nullptr;
+        int64_t nodes = 0;
+        while (!done) {
+            if (st_h->k >= cfg.maxiter) {
+                status = HISQ_ENOTCONV;
+                break;
+            }
+            const int k0 = st_h->k;
+            if (graph) {
+                if (!exec) {
+                    cudaGraph_t gr = nullptr;
+                    c->capturing = true;
+                    cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+                    if (ce == cudaSuccess) {
+                        iterate_block(x64);
+                        ce = cudaStreamEndCapture(s, &gr);
+                    }
+                    c->capturing = false;
+                    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
+                    size_t nn = 0;
+                    if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
+                    if (gr) cudaGraphDestroy(gr);
+                    if (ce != cudaSuccess) return cuda_fail(c, ce, "CG graph capture");
+                    nodes = (int64_t)nn;
+                }
+                cudaGraphLaunch(exec, s);
+                c->launches += nodes;
+            } else {
+                iterate_block(x64);
+            }
+            e = pull_state();
+            if (e) break;
+            const int reason = st_h->reason;
+            if (reason == REASON_BREAKDOWN) {
+                status = HISQ_EBREAKDOWN;
+                fail(c, HISQ_EBREAKDOWN, "CG breakdown at iteration %d (non-positive p.Ap or non-finite scalar)",
+                     st_h->k);
+                break;
+            }
+            if (reason == REASON_RELIABLE || reason == REASON_CONVERGED) {
+                const int j = st_h->k - k0 - 1;
+                flush(j + 1, nullptr, x64);
+                e = reliable_update(b64, x64, false, j);
+                if (e) break;
+                ru++;
+                done = st_h->hi_rr <= init.stop2;
+            }
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (e) return e;
+        if (status != HISQ_OK) {
+            // bring x up to date (slots of an unfinished block) and measure it
+            const int j = st_h->k > 0 ? (st_h->k - 1) % cfg.nbuf : 0;
+            if (status == HISQ_EBREAKDOWN) flush(cfg.nbuf, nullptr, x64);
+            (void)j;
+            e = reliable_update(b64, x64, false, 0);
+            if (e) return e;
+        }
+        int herr = 0;
+        cudaMemcpyAsync(&herr, c->err_flag, sizeof herr, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        info->iters = st_h->k;
+        info->matvecs += st_h->k;
+        info->matvecs_hi += mv_hi;
+        info->reliable_updates += ru;
+        info->true_residual = std::sqrt(st_h->hi_rr / bb);
+        if (status == HISQ_ENOTCONV)
+            fail(c, HISQ_ENOTCONV, "CG reached maxiter=%d with true residual %.3e", cfg.maxiter, info->true_residual);
+        return status;
+    }
+};
+
+}  // namespace
+
+hisq_status run_cg(hisq_ctx *c, hisq_gauge *g, const CGConfig &cfg, const double *b64, double *x64, bool x_zero,
+                   hisq_solve_info *info, cudaStream_t s)
+{
+    CGRun run(c, g, cfg, s);
+    return run.run(b64, x64, x_zero, info);
+}
+
+hisq_status validate_params(hisq_ctx *c, const hisq_solver_params *p)
+{
+    if (!p) return fail(c, HISQ_EINVAL, "null parameters");
+    if (!std::isfinite(p->mass) || !(p->tol > 0.0) || p->maxiter < 0 || !(p->delta >= 0.0 && p->delta < 1.0))
+        return fail(c, HISQ_EINVAL, "bad solver parameters (mass, tol > 0, maxiter >= 0, 0 <= delta < 1)");
+    if (p->nbuf < 1 || p->nbuf > kMaxBuf) return fail(c, HISQ_EINVAL, "nbuf must be in 1..%d", kMaxBuf);
+    return check_prec(c, p->sloppy);
+}
+
+// Caller layout [site][6] (host or device) <-> FP64 planar device field.
+hisq_status to_planar(hisq_ctx *c, Workspace &ws, const double *user, int on_device, int64_t n, double *planar,
+                      cudaStream_t s)
+{
+    const double *src = user;
+    if (!on_device) {
+        double *stage = nullptr;
+        hisq_status e = ws.alloc((size_t)48 * n, (void **)&stage);
+        if (e) return e;
+        cudaMemcpyAsync(stage, user, (size_t)48 * n, cudaMemcpyHostToDevice, s);
+        src = stage;
+    }
+    cudaMemsetAsync(c->err_flag, 0, sizeof(int), s);
+    {
+        LaunchScope ls(c, s, PROF_CONVERT, 96.0 * n);
+        launch_pack_spinor(S_F64, n, src, (char *)planar, c->err_flag, s);
+    }
+    int bad = 0;
+    cudaMemcpyAsync(&bad, c->err_flag, sizeof bad, cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    if (bad) return fail(c, HISQ_EINVAL, "non-finite input vector");
+    return HISQ_OK;
+}
+
+hisq_status from_planar(hisq_ctx *c, Workspace &ws, const double *planar, int64_t n, double *user, int on_device,
+                        cudaStream_t s)
+{
+    double *dst = user;
+    if (!on_device) {
+        hisq_status e = ws.alloc((size_t)48 * n, (void **)&dst);
+        if (e) return e;
+    }
+    {
+        LaunchScope ls(c, s, PROF_CONVERT, 96.0 * n);
+        launch_unpack_spinor(S_F64, HISQ_COMPUTE_F64, n, (const char *)planar, dst, s);
+    }
+    if (!on_device) cudaMemcpyAsync(user, dst, (size_t)48 * n, cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "download");
+    return HISQ_OK;
+}
+
+CGConfig config_from(const hisq_solver_params *p, double sigma)
+{
+    CGConfig cfg;
+    cfg.mass = p->mass;
+    cfg.sigma = sigma;
+    cfg.tol = p->tol;
+    cfg.maxiter = p->maxiter;
+    cfg.delta = p->delta;
+    cfg.sloppy = p->sloppy;
+    cfg.nbuf = p->nbuf;
+    cfg.pr = p->pr_beta;
+    cfg.reproject = p->reproject;
+    cfg.use_graph = p->use_graph;
+    return cfg;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+void hisq_default_params(hisq_solver_params *p)
+{
+    if (!p) return;
+    *p = hisq_solver_params{};
+    p->mass = 0.1;
+    p->tol = 1e-10;
+    p->maxiter = 100000;
+    p->delta = 0.1;
+    hisq_prec s;
+    s.gauge = HISQ_GAUGE_FIX16;
+    s.spinor = HISQ_SPINOR_INT20;
+    s.compute = HISQ_COMPUTE_F32;
+    s.fat_recon = 18;
+    s.long_recon = 12;
+    p->sloppy = s;
+    p->refine = s;
+    p->nbuf = 8;
+    p->use_init_guess = 0;
+    p->on_device = 0;
+    p->pr_beta = 1;
+    p->reproject = 1;
+    p->l = 4;
+    p->use_graph = 1;
+    p->stream = nullptr;
+}
+
+hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params *p, const double *b, double *x,
+                    hisq_solve_info *info)
+{
+    if (!c || !gc || !b || !x || !info) return fail(c, HISQ_EINVAL, "hisq_cg: null argument");
+    *info = hisq_solve_info{};
+    hisq_status e = validate_params(c, p);
+    if (e) return e;
+    cudaSetDevice(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    hisq_gauge *g = const_cast<hisq_gauge *>(gc);
+    cudaStream_t s = pick_stream(c, p->stream);
+    const int64_t vh = g->geom.vh;
+    Workspace ws(c, s);
+    double *b64 = nullptr, *x64 = nullptr;
+    e = ws.alloc((size_t)48 * vh, (void **)&b64);
+    if (!e) e = ws.alloc((size_t)48 * vh, (void **)&x64);
+    if (!e) e = to_planar(c, ws, b, p->on_device, vh, b64, s);
+    if (!e && p->use_init_guess) e = to_planar(c, ws, x, p->on_device, vh, x64, s);
+    if (!e && !p->use_init_guess) cudaMemsetAsync(x64, 0, (size_t)48 * vh, s);
+    if (e) return e;
+    const CGConfig cfg = config_from(p, 0.0);
+    hisq_status st = run_cg(c, g, cfg, b64, x64, !p->use_init_guess, info, s);
+    if (st != HISQ_OK && st != HISQ_ENOTCONV && st != HISQ_EBREAKDOWN) return st;
+    e = from_planar(c, ws, x64, vh, x, p->on_device, s);
+    if (e) return e;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+}  // extern "C"

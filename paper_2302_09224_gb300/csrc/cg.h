@@ -1,0 +1,52 @@
+// cg.h -- shared pieces of the solver drivers (CG core, operator, buffers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace hisq {
+
+// Device allocations owned by one solve; freed (after the stream drains) on
+// destruction.
+struct Workspace {
+    hisq_ctx *c;
+    cudaStream_t s;
+    std::vector<std::pair<void *, size_t>> allocs;
+    Workspace(hisq_ctx *c_, cudaStream_t s_) : c(c_), s(s_) {}
+    ~Workspace();
+    hisq_status alloc(size_t bytes, void **p);
+};
+
+struct CGConfig {
+    double mass = 0, sigma = 0, tol = 1e-10;
+    int maxiter = 100000;
+    double delta = 0.1;
+    hisq_prec sloppy{};
+    int nbuf = 8;
+    int pr = 1, reproject = 1, use_graph = 1;
+};
+
+hisq_prec prec_f64();
+double stencil_bytes(const hisq_prec &p, int vh, bool xpay);
+
+void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
+               const char *in, char *tmp, char *out, int fin, CGState *st, int slot, const int *active, int kind,
+               cudaStream_t s);
+
+// Mixed-precision CG on (M_ee + sigma) x = b; b64 / x64 are FP64 planar device
+// fields (x64 holds the initial guess unless x_zero).
+hisq_status run_cg(hisq_ctx *c, hisq_gauge *g, const CGConfig &cfg, const double *b64, double *x64, bool x_zero,
+                   hisq_solve_info *info, cudaStream_t s);
+
+hisq_status validate_params(hisq_ctx *c, const hisq_solver_params *p);
+CGConfig config_from(const hisq_solver_params *p, double sigma);
+hisq_status to_planar(hisq_ctx *c, Workspace &ws, const double *user, int on_device, int64_t n, double *planar,
+                      cudaStream_t s);
+hisq_status from_planar(hisq_ctx *c, Workspace &ws, const double *planar, int64_t n, double *user, int on_device,
+                        cudaStream_t s);
+
+}  // namespace hisq

@@ -1,0 +1,370 @@
+// codecs.cuh -- device-side storage formats: every kernel reads a site or link
+// through these and converts to the compute precision in registers (Sec. 4.1:
+// the format is a property of the accessor, not of the computation).
+//
+// Spinor formats (one half-lattice field of n sites; planar layout: 16-byte
+// planes [plane][site] then a narrower tail plane):
+//   F64    3 x 16 B        complex c in plane c
+//   F32    16 + 8 B        (c0, c1) | (c2)
+//   HALF   16 B            int16 q[6] | FP32 site max  (Sec. 2, Listing 1)
+//   INT20  16 B            four words of the Appendix A bitfield layout
+//   INT30  16 + 8 B        words 0..3 | words 4..5 (Sec. 3, Listing 3; our layout)
+// Link formats ([plane][parity][mu][Vh]; reals row-major, first 12 for r12):
+//   F64 16 B = 1 complex, F32 16 B = 2 complex, FIX16 16 B = 8 int16,
+//   FIX32 16 B = 4 int32; leftover reals go to a 4- or 8-byte tail plane.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace hisq {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t sext_bits(uint32_t u, int bits)
+{
+    const uint32_t m = 1u << (bits - 1);
+    u &= (1u << bits) - 1u;
+    return (int32_t)((u ^ m) - m);
+}
+
+__device__ __forceinline__ uint32_t lo16(int v) { return (uint32_t)v & 0xffffu; }
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p)
+{
+    return __ldcs(p);  // read once: evict-first in L1 and L2
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_cached(const T *p)
+{
+    return __ldg(p);
+}
+
+// FP32 helpers that must not be contracted (codec arithmetic is specified
+// step by step and is bit-exact with the CPU definition).
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+
+// ---------------------------------------------------------------------------
+// spinor codecs
+// ---------------------------------------------------------------------------
+template <int SF>
+struct Spinor;
+
+template <>
+struct Spinor<S_F64> {
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(b);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double2 d = ld_cached(p + (size_t)c * n + i);
+            v[2 * c] = (real)d.x;
+            v[2 * c + 1] = (real)d.y;
+        }
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        double2 *p = reinterpret_cast<double2 *>(b);
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            p[(size_t)c * n + i] = make_double2((double)v[2 * c], (double)v[2 * c + 1]);
+            ok = ok && isfinite((double)v[2 * c]) && isfinite((double)v[2 * c + 1]);
+        }
+        return ok;
+    }
+};
+
+template <>
+struct Spinor<S_F32> {
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        const float4 a = ld_cached(reinterpret_cast<const float4 *>(b) + i);
+        const float2 c = ld_cached(reinterpret_cast<const float2 *>(b + (size_t)16 * n) + i);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y;
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        float f[6];
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            f[k] = (float)v[k];
+            ok = ok && isfinite(f[k]);
+        }
+        reinterpret_cast<float4 *>(b)[i] = make_float4(f[0], f[1], f[2], f[3]);
+        reinterpret_cast<float2 *>(b + (size_t)16 * n)[i] = make_float2(f[4], f[5]);
+        return ok;
+    }
+};
+
+// 16-bit fixed point with a site-local FP32 norm.  Encode: inv = 32767/max
+// (IEEE), q = rint(v*inv) clamped to +-32767; decode: v = q * (max*fl(1/32767)).
+// Sites with max below 2^-110 (32767/max would overflow) are stored as zero.
+template <>
+struct Spinor<S_HALF> {
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        const int4 r = ld_cached(reinterpret_cast<const int4 *>(b) + i);
+        const float scale = fmul(__int_as_float(r.w), 1.0f / 32767.0f);
+        const int q[6] = {(int)(short)(r.x & 0xffff), r.x >> 16, (int)(short)(r.y & 0xffff),
+                          r.y >> 16, (int)(short)(r.z & 0xffff), r.z >> 16};
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = (real)fmul((float)q[k], scale);
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        (void)n;
+        float f[6];
+        float mx = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            f[k] = (float)v[k];
+            ok = ok && isfinite(f[k]);
+            mx = fmaxf(mx, fabsf(f[k]));
+        }
+        int q[6] = {0, 0, 0, 0, 0, 0};
+        if (!ok || mx < 0x1p-110f) {  // non-finite, or too small for 32767/max in FP32
+            mx = 0.0f;
+        } else {
+            const float inv = __fdiv_rn(32767.0f, mx);
+#pragma unroll
+            for (int k = 0; k < 6; k++) q[k] = max(-32767, min(32767, __float2int_rn(fmul(f[k], inv))));
+        }
+        int4 r;
+        r.x = (int)(lo16(q[0]) | (lo16(q[1]) << 16));
+        r.y = (int)(lo16(q[2]) | (lo16(q[3]) << 16));
+        r.z = (int)(lo16(q[4]) | (lo16(q[5]) << 16));
+        r.w = __float_as_int(mx);
+        reinterpret_cast<int4 *>(b)[i] = r;
+        return ok;
+    }
+};
+
+// 20-bit shared exponent (Appendix A): E = exponent field of fl(max/(2^19-1))
+// plus one, q = rint(v * 2^-(E-127)), bitfields least-significant first.
+template <>
+struct Spinor<S_INT20> {
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        (void)n;
+        const uint4 w = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        const float up = __uint_as_float((w.w >> 24) << 23);
+        const uint32_t u[6] = {w.x & 0xfffffu,
+                               ((w.x >> 20) << 8) | (w.y & 0xffu),
+                               (w.y >> 8) & 0xfffffu,
+                               ((w.y >> 28) << 16) | (w.z & 0xffffu),
+                               ((w.z >> 16) << 4) | (w.w & 0xfu),
+                               (w.w >> 4) & 0xfffffu};
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = (real)fmul((float)sext_bits(u[k], 20), up);
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        (void)n;
+        float f[6];
+        float mx = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            f[k] = (float)v[k];
+            ok = ok && isfinite(f[k]);
+            mx = fmaxf(mx, fabsf(f[k]));
+        }
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t E = 1;
+        if (ok) {
+            const float t = __fdiv_rn(mx, 524287.0f);
+            E = ((__float_as_uint(t) >> 23) & 0xffu) + 1u;
+            const float down = __uint_as_float((254u - E) << 23);
+#pragma unroll
+            for (int k = 0; k < 6; k++) u[k] = (uint32_t)__float2int_rn(fmul(f[k], down));
+        }
+        uint4 w;
+        w.x = (u[0] & 0xfffffu) | (((u[1] >> 8) & 0xfffu) << 20);
+        w.y = (u[1] & 0xffu) | ((u[2] & 0xfffffu) << 8) | (((u[3] >> 16) & 0xfu) << 28);
+        w.z = (u[3] & 0xffffu) | (((u[4] >> 4) & 0xffffu) << 16);
+        w.w = (u[4] & 0xfu) | ((u[5] & 0xfffffu) << 4) | (E << 24);
+        reinterpret_cast<uint4 *>(b)[i] = w;
+        return ok;
+    }
+};
+
+// 30-bit shared exponent (our layout of Listing 3): words k < 6 hold q_k in
+// bits 0..29, bits 30..31 of words 0..3 hold exponent bits 2k..2k+1.  Encode
+// in FP64: t = max/(2^29-1), 2^(E-127) the power of two just above t.
+template <>
+struct Spinor<S_INT30> {
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        const uint4 a = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        const uint2 c = ld_cached(reinterpret_cast<const uint2 *>(b + (size_t)16 * n) + i);
+        const uint32_t E = (a.x >> 30) | ((a.y >> 30) << 2) | ((a.z >> 30) << 4) | ((a.w >> 30) << 6);
+        const int32_t q[6] = {sext_bits(a.x, 30), sext_bits(a.y, 30), sext_bits(a.z, 30),
+                              sext_bits(a.w, 30), sext_bits(c.x, 30), sext_bits(c.y, 30)};
+        if constexpr (sizeof(real) == 8) {
+            const double up = __longlong_as_double((long long)(E + 896u) << 52);  // 2^(E-127)
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = __dmul_rn((double)q[k], up);
+        } else {
+            const float up = __uint_as_float(E << 23);
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = fmul(__int2float_rn(q[k]), up);
+        }
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        double d[6];
+        double mx = 0.0;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            d[k] = (double)v[k];
+            ok = ok && isfinite(d[k]);
+            mx = fmax(mx, fabs(d[k]));
+        }
+        uint32_t E = 1;
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        if (ok) {
+            const double t = __ddiv_rn(mx, 536870911.0);
+            const int biased = (int)((__double_as_longlong(t) >> 52) & 0x7ff);
+            int e = (t > 0.0 && biased > 0) ? biased - 895 : 1;  // frexp exponent + 127
+            if (e < 1) e = 1;
+            if (e > 254) ok = false;
+            if (ok) {
+                E = (uint32_t)e;
+                const double down = __longlong_as_double((long long)(1150 - e) << 52);  // 2^-(E-127)
+#pragma unroll
+                for (int k = 0; k < 6; k++) u[k] = (uint32_t)(int32_t)__double2ll_rn(__dmul_rn(d[k], down));
+            }
+        }
+        uint4 a;
+        a.x = (u[0] & 0x3fffffffu) | ((E & 3u) << 30);
+        a.y = (u[1] & 0x3fffffffu) | (((E >> 2) & 3u) << 30);
+        a.z = (u[2] & 0x3fffffffu) | (((E >> 4) & 3u) << 30);
+        a.w = (u[3] & 0x3fffffffu) | (((E >> 6) & 3u) << 30);
+        reinterpret_cast<uint4 *>(b)[i] = a;
+        reinterpret_cast<uint2 *>(b + (size_t)16 * n)[i] = make_uint2(u[4] & 0x3fffffffu, u[5] & 0x3fffffffu);
+        return ok;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// link codecs (read-only in the stencil; written by the gauge loader)
+// ---------------------------------------------------------------------------
+// Row 2 of a compressed link: sign * conj(row0 x row1) (SU(3) up to a sign).
+template <typename real>
+__device__ __forceinline__ void rebuild_row2(real U[18], real sign)
+{
+    // U[2k], U[2k+1]: re, im of element k = 3*row + col
+#define RE(k) U[2 * (k)]
+#define IM(k) U[2 * (k) + 1]
+    const real c0r = RE(1) * RE(5) - IM(1) * IM(5) - (RE(2) * RE(4) - IM(2) * IM(4));
+    const real c0i = RE(1) * IM(5) + IM(1) * RE(5) - (RE(2) * IM(4) + IM(2) * RE(4));
+    const real c1r = RE(2) * RE(3) - IM(2) * IM(3) - (RE(0) * RE(5) - IM(0) * IM(5));
+    const real c1i = RE(2) * IM(3) + IM(2) * RE(3) - (RE(0) * IM(5) + IM(0) * RE(5));
+    const real c2r = RE(0) * RE(4) - IM(0) * IM(4) - (RE(1) * RE(3) - IM(1) * IM(3));
+    const real c2i = RE(0) * IM(4) + IM(0) * RE(4) - (RE(1) * IM(3) + IM(1) * RE(3));
+    RE(6) = sign * c0r; IM(6) = -sign * c0i;
+    RE(7) = sign * c1r; IM(7) = -sign * c1i;
+    RE(8) = sign * c2r; IM(8) = -sign * c2i;
+#undef RE
+#undef IM
+}
+
+template <int GF, int RECON>
+struct Link {
+    static constexpr int n16 = link_n16(GF, RECON);
+    static constexpr int tail = link_tail(GF, RECON);
+
+    // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16)
+    template <typename real>
+    __device__ static void load(const char *base, size_t pstride, int li, real U[18], float sf, double sd)
+    {
+        if constexpr (GF == G_F64) {
+#pragma unroll
+            for (int k = 0; k < RECON / 2; k++) {
+                const double2 d = ld_stream(reinterpret_cast<const double2 *>(base + k * pstride) + li);
+                U[2 * k] = (real)d.x;
+                U[2 * k + 1] = (real)d.y;
+            }
+        } else if constexpr (GF == G_F32) {
+#pragma unroll
+            for (int k = 0; k < n16; k++) {
+                const float4 d = ld_stream(reinterpret_cast<const float4 *>(base + k * pstride) + li);
+                U[4 * k] = d.x; U[4 * k + 1] = d.y; U[4 * k + 2] = d.z; U[4 * k + 3] = d.w;
+            }
+            if constexpr (tail == 8) {
+                const float2 d = ld_stream(reinterpret_cast<const float2 *>(base + n16 * pstride) + li);
+                U[4 * n16] = d.x; U[4 * n16 + 1] = d.y;
+            }
+        } else if constexpr (GF == G_FIX16) {
+            int q[RECON];
+#pragma unroll
+            for (int k = 0; k < n16; k++) {
+                const int4 d = ld_stream(reinterpret_cast<const int4 *>(base + k * pstride) + li);
+                const int w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    q[8 * k + 2 * j] = (int)(short)(w[j] & 0xffff);
+                    q[8 * k + 2 * j + 1] = w[j] >> 16;
+                }
+            }
+            if constexpr (tail == 4) {
+                const int d = ld_stream(reinterpret_cast<const int *>(base + n16 * pstride) + li);
+                q[8 * n16] = (int)(short)(d & 0xffff);
+                q[8 * n16 + 1] = d >> 16;
+            } else if constexpr (tail == 8) {
+                const int2 d = ld_stream(reinterpret_cast<const int2 *>(base + n16 * pstride) + li);
+                q[8 * n16] = (int)(short)(d.x & 0xffff);
+                q[8 * n16 + 1] = d.x >> 16;
+                q[8 * n16 + 2] = (int)(short)(d.y & 0xffff);
+                q[8 * n16 + 3] = d.y >> 16;
+            }
+#pragma unroll
+            for (int k = 0; k < RECON; k++) {
+                if constexpr (sizeof(real) == 8)
+                    U[k] = (double)q[k] * sd;
+                else
+                    U[k] = (float)q[k] * sf;
+            }
+        } else {  // G_FIX32
+            int q[RECON];
+#pragma unroll
+            for (int k = 0; k < n16; k++) {
+                const int4 d = ld_stream(reinterpret_cast<const int4 *>(base + k * pstride) + li);
+                q[4 * k] = d.x; q[4 * k + 1] = d.y; q[4 * k + 2] = d.z; q[4 * k + 3] = d.w;
+            }
+            if constexpr (tail == 8) {
+                const int2 d = ld_stream(reinterpret_cast<const int2 *>(base + n16 * pstride) + li);
+                q[4 * n16] = d.x; q[4 * n16 + 1] = d.y;
+            }
+#pragma unroll
+            for (int k = 0; k < RECON; k++) {
+                if constexpr (sizeof(real) == 8)
+                    U[k] = (double)q[k] * sd;
+                else
+                    U[k] = __int2float_rn(q[k]) * sf;
+            }
+        }
+    }
+};
+
+}  // namespace hisq

@@ -1,0 +1,248 @@
+// convert.cu -- format conversion kernels: spinor pack/unpack between the
+// caller's FP64 [site][6] layout and the storage formats, and the gauge
+// loader's scale, compression check and quantisation passes.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "codecs.cuh"
+#include "internal.h"
+
+namespace hisq {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int SF>
+__global__ void pack_kernel(int64_t n, const double *in, char *out, int *bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = in[6 * i + k];
+    if (!Spinor<SF>::store(out, (int)n, (int)i, v)) atomicAdd(bad, 1);
+}
+
+template <int SF, typename real>
+__global__ void unpack_kernel(int64_t n, const char *in, double *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    real v[6];
+    Spinor<SF>::load(in, (int)n, (int)i, v);
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[6 * i + k] = (double)v[k];
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v)
+{
+    // non-negative doubles order like their bit patterns (NaN sorts above Inf)
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void absmax_kernel(int64_t n, const double *x, double *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs(x[i]);
+        m = (a > m || a != a) ? a : m;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, m, off);
+        m = (o > m || o != o) ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+__device__ __forceinline__ void lex_coords(const Geom &g, int lex, int c[4])
+{
+    c[0] = lex % g.L[0];
+    int r = lex / g.L[0];
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+}
+
+// Largest deviation of row 2 from sign * conj(row0 x row1) over all links of
+// a field (k = 1 fat, k = 3 long): zero to rounding when the field can be
+// stored as 12 reals (Sec. 1, 18 -> 12 compression).
+__global__ void r12_check_kernel(Geom g, const double *links, int k, double *out)
+{
+    const int V = 2 * g.vh;
+    double m = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < 4LL * V;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int mu = (int)(idx / V), lex = (int)(idx % V);
+        int c[4];
+        lex_coords(g, lex, c);
+        int ps = 0;
+        for (int nu = 0; nu < mu; nu++) ps += c[nu];
+        double sign = (ps & 1) ? -1.0 : 1.0;
+        if (g.antiperiodic_t && mu == 3 && c[3] + k >= g.L[3]) sign = -sign;
+        double U[18];
+        const double *src = links + idx * 18;
+        for (int j = 0; j < 18; j++) U[j] = src[j];
+        double R[18];
+        for (int j = 0; j < 18; j++) R[j] = U[j];
+        rebuild_row2(R, sign);
+        for (int j = 12; j < 18; j++) {
+            const double d = fabs(R[j] - U[j]);
+            m = (d > m || d != d) ? d : m;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, m, off);
+        m = (o > m || o != o) ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// FP64 [mu][lex][18] -> stored copy [plane][parity][mu][Vh] in format GF with
+// RECON reals per link.  Fixed point: q = rint(x * inv) clamped to +-qmax,
+// inv = qmax / global max (Sec. 2 footnote; Sec. 3 for 32 bits).
+template <int GF, int RECON>
+__global__ void quantise_kernel(Geom g, const double *links, double inv, char *out)
+{
+    const int vh = g.vh;
+    const int64_t n = 8LL * vh;
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= n) return;
+    const int cb = (int)(li % vh);
+    const int pm = (int)(li / vh);
+    const int par = pm >> 2, mu = pm & 3;
+    int r = cb / g.xh;
+    const int xh = cb - r * g.xh;
+    const int y = r % g.L[1];
+    r /= g.L[1];
+    const int z = r % g.L[2];
+    const int t = r / g.L[2];
+    const int x = 2 * xh + ((y + z + t + par) & 1);
+    const int lex = 2 * cb + (x & 1);
+    const double *src = links + ((int64_t)mu * 2 * vh + lex) * 18;
+    const size_t pstride = (size_t)n * 16;
+    constexpr int n16 = link_n16(GF, RECON), tail = link_tail(GF, RECON);
+    if constexpr (GF == G_F64) {
+        for (int k = 0; k < RECON / 2; k++)
+            reinterpret_cast<double2 *>(out + k * pstride)[li] = make_double2(src[2 * k], src[2 * k + 1]);
+    } else if constexpr (GF == G_F32) {
+        for (int k = 0; k < n16; k++)
+            reinterpret_cast<float4 *>(out + k * pstride)[li] =
+                make_float4((float)src[4 * k], (float)src[4 * k + 1], (float)src[4 * k + 2], (float)src[4 * k + 3]);
+        if constexpr (tail == 8)
+            reinterpret_cast<float2 *>(out + n16 * pstride)[li] =
+                make_float2((float)src[4 * n16], (float)src[4 * n16 + 1]);
+    } else {
+        constexpr double qmax = GF == G_FIX16 ? 32767.0 : 2147483647.0;
+        int q[RECON];
+        for (int k = 0; k < RECON; k++) {
+            double v = rint(__dmul_rn(src[k], inv));
+            v = fmin(qmax, fmax(-qmax, v));
+            q[k] = (int)v;
+        }
+        if constexpr (GF == G_FIX16) {
+            for (int k = 0; k < n16; k++) {
+                int4 w;
+                w.x = (int)((q[8 * k] & 0xffff) | ((uint32_t)q[8 * k + 1] << 16));
+                w.y = (int)((q[8 * k + 2] & 0xffff) | ((uint32_t)q[8 * k + 3] << 16));
+                w.z = (int)((q[8 * k + 4] & 0xffff) | ((uint32_t)q[8 * k + 5] << 16));
+                w.w = (int)((q[8 * k + 6] & 0xffff) | ((uint32_t)q[8 * k + 7] << 16));
+                reinterpret_cast<int4 *>(out + k * pstride)[li] = w;
+            }
+            if constexpr (tail == 4) {
+                reinterpret_cast<int *>(out + n16 * pstride)[li] =
+                    (int)((q[8 * n16] & 0xffff) | ((uint32_t)q[8 * n16 + 1] << 16));
+            } else if constexpr (tail == 8) {
+                reinterpret_cast<int2 *>(out + n16 * pstride)[li] =
+                    make_int2((int)((q[8 * n16] & 0xffff) | ((uint32_t)q[8 * n16 + 1] << 16)),
+                              (int)((q[8 * n16 + 2] & 0xffff) | ((uint32_t)q[8 * n16 + 3] << 16)));
+            }
+        } else {
+            for (int k = 0; k < n16; k++)
+                reinterpret_cast<int4 *>(out + k * pstride)[li] =
+                    make_int4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+            if constexpr (tail == 8)
+                reinterpret_cast<int2 *>(out + n16 * pstride)[li] = make_int2(q[4 * n16], q[4 * n16 + 1]);
+        }
+    }
+}
+
+int nblocks(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *bad, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nb = nblocks(n, kBlock);
+    switch (sf) {
+    case S_F64: pack_kernel<S_F64><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_F32: pack_kernel<S_F32><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_HALF: pack_kernel<S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT20: pack_kernel<S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT30: pack_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    default: break;
+    }
+}
+
+void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nb = nblocks(n, kBlock);
+    const bool f64 = cf == HISQ_COMPUTE_F64;
+    switch (sf) {
+    case S_F64:
+        if (f64) unpack_kernel<S_F64, double><<<nb, kBlock, 0, s>>>(n, in, out);
+        else unpack_kernel<S_F64, float><<<nb, kBlock, 0, s>>>(n, in, out);
+        break;
+    case S_F32: unpack_kernel<S_F32, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
+    case S_HALF: unpack_kernel<S_HALF, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
+    case S_INT20: unpack_kernel<S_INT20, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
+    case S_INT30:
+        if (f64) unpack_kernel<S_INT30, double><<<nb, kBlock, 0, s>>>(n, in, out);
+        else unpack_kernel<S_INT30, float><<<nb, kBlock, 0, s>>>(n, in, out);
+        break;
+    default: break;
+    }
+}
+
+void launch_absmax(int64_t n, const double *x, double *out, cudaStream_t s)
+{
+    const int nb = (int)std::min<int64_t>(nblocks(n, kBlock), 4096);
+    absmax_kernel<<<nb, kBlock, 0, s>>>(n, x, out);
+}
+
+void launch_r12_check(const Geom &g, const double *links, int k, double *out, cudaStream_t s)
+{
+    const int nb = (int)std::min<int64_t>(nblocks(8LL * g.vh, kBlock), 4096);
+    r12_check_kernel<<<nb, kBlock, 0, s>>>(g, links, k, out);
+}
+
+void launch_quantise_links(const Geom &g, int gf, int recon, const double *links, double inv, char *out,
+                           cudaStream_t s)
+{
+    const int nb = nblocks(8LL * g.vh, kBlock);
+#define Q(GF, R) quantise_kernel<GF, R><<<nb, kBlock, 0, s>>>(g, links, inv, out)
+    if (recon == 18) {
+        switch (gf) {
+        case G_F64: Q(G_F64, 18); break;
+        case G_F32: Q(G_F32, 18); break;
+        case G_FIX16: Q(G_FIX16, 18); break;
+        case G_FIX32: Q(G_FIX32, 18); break;
+        }
+    } else {
+        switch (gf) {
+        case G_F64: Q(G_F64, 12); break;
+        case G_F32: Q(G_F32, 12); break;
+        case G_FIX16: Q(G_FIX16, 12); break;
+        case G_FIX32: Q(G_FIX32, 12); break;
+        }
+    }
+#undef Q
+}
+
+}  // namespace hisq

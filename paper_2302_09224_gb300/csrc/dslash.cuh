@@ -1,0 +1,175 @@
+// dslash.cuh -- the HISQ staggered stencil pass (the dominant kernel of every
+// solver; Sec. 1 and Sec. 4.3), templated on the storage formats of the gauge
+// and spinor fields and on the compute precision (Sec. 3: the triplet).
+//
+// One thread per output site x of parity p:
+//   out(x) = a*y(x) + sign * sum_mu [ F_mu(x) in(x+mu) - F_mu(x-mu)^+ in(x-mu)
+//                                    + L_mu(x) in(x+3mu) - L_mu(x-3mu)^+ in(x-3mu) ]
+// Links are read exactly once per pass with evict-first loads (16 per site,
+// each used once); neighbour spinors are read through the read-only path so
+// the 16-fold reuse is served by L1/L2.  Coordinates come from the
+// checkerboard index (no index tables), neighbours wrap periodically.
+// Compressed long links (r12) rebuild row 2 in registers with the staggered
+// phase times boundary sign of the link's site.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "codecs.cuh"
+#include "finish.cuh"
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace hisq {
+
+constexpr int kDslashBlock = 128;
+
+__device__ __forceinline__ int wrap_coord(int c, int L)
+{
+    c += (c < 0) ? L : 0;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return c;
+}
+
+// acc += U s
+template <typename real>
+__device__ __forceinline__ void mv_add(real acc[6], const real U[18], const real s[6])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const real ur = U[2 * (3 * i + j)], ui = U[2 * (3 * i + j) + 1];
+            acc[2 * i] += ur * s[2 * j] - ui * s[2 * j + 1];
+            acc[2 * i + 1] += ur * s[2 * j + 1] + ui * s[2 * j];
+        }
+}
+
+// acc -= U^+ s
+template <typename real>
+__device__ __forceinline__ void mv_adj_sub(real acc[6], const real U[18], const real s[6])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const real ur = U[2 * (3 * j + i)], ui = U[2 * (3 * j + i) + 1];  // conj(U_ji)
+            acc[2 * i] -= ur * s[2 * j] + ui * s[2 * j + 1];
+            acc[2 * i + 1] -= ur * s[2 * j + 1] - ui * s[2 * j];
+        }
+}
+
+template <int GF, int SF, typename real, int LREC, bool RED>
+__global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a)
+{
+    if (a.active != nullptr && *(volatile const int *)a.active == 0) return;  // uniform over the grid
+    const Geom &g = a.g;
+    const int vh = g.vh;
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    const int po = a.out_parity, pi = 1 - po;
+    const size_t pstride = (size_t)8 * vh * 16;
+    double rv[2] = {0.0, 0.0};
+
+    if (cb < vh) {
+        int r = cb / g.xh;
+        const int xh = cb - r * g.xh;
+        const int y = r % g.L[1];
+        r /= g.L[1];
+        const int z = r % g.L[2];
+        const int t = r / g.L[2];
+        const int x = 2 * xh + ((y + z + t + po) & 1);
+        const int c[4] = {x, y, z, t};
+        const int lex = 2 * cb + (x & 1);
+        real acc[6] = {0, 0, 0, 0, 0, 0};
+        int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
+
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int L = g.L[mu], st = g.stride[mu];
+            const int cp1 = wrap_coord(c[mu] + 1, L), cm1 = wrap_coord(c[mu] - 1, L);
+            const int cp3 = wrap_coord(c[mu] + 3, L), cm3 = wrap_coord(c[mu] - 3, L);
+            const int base = lex - c[mu] * st;
+            const int np1 = (base + cp1 * st) >> 1, nm1 = (base + cm1 * st) >> 1;
+            const int np3 = (base + cp3 * st) >> 1, nm3 = (base + cm3 * st) >> 1;
+            real U[18], s[6];
+
+            Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U, a.gv.fat_scale_f,
+                               a.gv.fat_scale_d);
+            Spinor<SF>::load(a.in, vh, np1, s);
+            mv_add(acc, U, s);
+
+            Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U, a.gv.fat_scale_f,
+                               a.gv.fat_scale_d);
+            Spinor<SF>::load(a.in, vh, nm1, s);
+            mv_adj_sub(acc, U, s);
+
+            const real eta = (phase_sum & 1) ? real(-1) : real(1);
+            const size_t lps = (size_t)8 * vh * 16;
+            Link<GF, LREC>::load(a.gv.lng, lps, (po * 4 + mu) * vh + cb, U, a.gv.lng_scale_f, a.gv.lng_scale_d);
+            if constexpr (LREC == 12) {
+                const bool flip = g.antiperiodic_t && mu == 3 && c[3] + 3 >= L;
+                rebuild_row2(U, flip ? -eta : eta);
+            }
+            Spinor<SF>::load(a.in, vh, np3, s);
+            mv_add(acc, U, s);
+
+            Link<GF, LREC>::load(a.gv.lng, lps, (pi * 4 + mu) * vh + nm3, U, a.gv.lng_scale_f, a.gv.lng_scale_d);
+            if constexpr (LREC == 12) {
+                const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
+                rebuild_row2(U, flip ? -eta : eta);
+            }
+            Spinor<SF>::load(a.in, vh, nm3, s);
+            mv_adj_sub(acc, U, s);
+
+            phase_sum += c[mu];
+        }
+
+        const real sgn = (real)a.sign;
+        real o[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) o[k] = sgn * acc[k];
+        if (a.xpay) {
+            real yv[6];
+            Spinor<SF>::load(a.y, vh, cb, yv);
+            const real aa = (real)a.a;
+#pragma unroll
+            for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
+            if constexpr (RED) {
+#pragma unroll
+                for (int k = 0; k < 6; k++) rv[0] += (double)yv[k] * (double)o[k];
+            }
+        }
+        if constexpr (RED) {
+#pragma unroll
+            for (int k = 0; k < 6; k++) rv[1] += (double)o[k] * (double)o[k];
+        }
+        if (!Spinor<SF>::store(a.out, vh, cb, o)) atomicExch(a.err, 1);
+    }
+
+    if constexpr (RED) {
+        __shared__ double tot[2];
+        if (reduce_grid<2>(rv, a.red, tot) && threadIdx.x == 0) run_finisher(a.fin, tot, a.st, a.slot);
+    }
+}
+
+template <int GF, int SF, typename real>
+bool launch_dslash_t(int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
+{
+    const int nblk = (a.g.vh + kDslashBlock - 1) / kDslashBlock;
+    if (long_recon == 12) {
+        if (reduce)
+            dslash_kernel<GF, SF, real, 12, true><<<nblk, kDslashBlock, 0, s>>>(a);
+        else
+            dslash_kernel<GF, SF, real, 12, false><<<nblk, kDslashBlock, 0, s>>>(a);
+    } else {
+        if (reduce)
+            dslash_kernel<GF, SF, real, 18, true><<<nblk, kDslashBlock, 0, s>>>(a);
+        else
+            dslash_kernel<GF, SF, real, 18, false><<<nblk, kDslashBlock, 0, s>>>(a);
+    }
+    return true;
+}
+
+}  // namespace hisq

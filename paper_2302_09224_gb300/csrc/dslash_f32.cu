@@ -1,0 +1,9 @@
+// Stencil kernels for the F32 gauge / F32 spinor / float compute triplet.
+#include "dslash.cuh"
+
+namespace hisq {
+bool launch_dslash_f32(int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
+{
+    return launch_dslash_t<G_F32, S_F32, float>(long_recon, reduce, a, s);
+}
+}  // namespace hisq

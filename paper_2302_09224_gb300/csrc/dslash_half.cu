@@ -1,0 +1,9 @@
+// Stencil kernels for the FIX16 gauge / HALF spinor / float compute triplet.
+#include "dslash.cuh"
+
+namespace hisq {
+bool launch_dslash_half(int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
+{
+    return launch_dslash_t<G_FIX16, S_HALF, float>(long_recon, reduce, a, s);
+}
+}  // namespace hisq

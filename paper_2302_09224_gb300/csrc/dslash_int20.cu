@@ -1,0 +1,9 @@
+// Stencil kernels for the FIX16 gauge / INT20 spinor / float compute triplet.
+#include "dslash.cuh"
+
+namespace hisq {
+bool launch_dslash_int20(int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
+{
+    return launch_dslash_t<G_FIX16, S_INT20, float>(long_recon, reduce, a, s);
+}
+}  // namespace hisq

@@ -1,0 +1,244 @@
+// internal.h -- host/device declarations shared by the library's translation
+// units (never installed; the public interface is include/hisq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hisq.h"
+
+namespace hisq {
+
+// ---------------------------------------------------------------------------
+// formats
+// ---------------------------------------------------------------------------
+enum GaugeFmt { G_F64 = 0, G_F32 = 1, G_FIX16 = 2, G_FIX32 = 3 };
+enum SpinorFmt { S_F64 = 0, S_F32 = 1, S_HALF = 2, S_INT20 = 3, S_INT30 = 4 };
+
+__host__ __device__ constexpr int spinor_site_bytes(int sf)
+{
+    return sf == S_F64 ? 48 : (sf == S_F32 || sf == S_INT30) ? 24 : 16;
+}
+__host__ __device__ constexpr int spinor_n16(int sf) { return spinor_site_bytes(sf) / 16; }
+__host__ __device__ constexpr int spinor_tail(int sf) { return spinor_site_bytes(sf) % 16; }
+
+__host__ __device__ constexpr int gauge_real_bytes(int gf)
+{
+    return gf == G_F64 ? 8 : gf == G_FIX16 ? 2 : 4;
+}
+__host__ __device__ constexpr int link_bytes(int gf, int recon) { return gauge_real_bytes(gf) * recon; }
+__host__ __device__ constexpr int link_n16(int gf, int recon) { return link_bytes(gf, recon) / 16; }
+__host__ __device__ constexpr int link_tail(int gf, int recon) { return link_bytes(gf, recon) % 16; }
+
+// Bytes of a half-lattice field of n sites in the planar layout: 16-B planes
+// [plane][site], then the tail plane [site] (all planes of one field are
+// contiguous and start 16-B aligned).
+inline size_t spinor_field_bytes(int sf, int64_t n) { return (size_t)spinor_site_bytes(sf) * (size_t)n; }
+
+// Bytes of one stored link field: [plane][parity][mu][Vh] chunks.
+inline size_t link_field_bytes(int gf, int recon, int64_t vh)
+{
+    return (size_t)link_bytes(gf, recon) * 8u * (size_t)vh;
+}
+
+// ---------------------------------------------------------------------------
+// lattice geometry passed to kernels
+// ---------------------------------------------------------------------------
+struct Geom {
+    int L[4];        // extents x, y, z, t
+    int stride[4];   // lex strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int xh;          // Lx / 2
+    int vh;          // sites per parity
+    int antiperiodic_t;
+};
+
+Geom make_geom(const int dims[4], int antiperiodic_t);
+
+// ---------------------------------------------------------------------------
+// deterministic two-level reductions (last block finishes)
+// ---------------------------------------------------------------------------
+constexpr int kMaxRed = 8;          // values reduced per launch
+constexpr int kMaxRedBlocks = 1 << 16;
+
+struct RedBuf {
+    double *partials;        // [kMaxRedBlocks][kMaxRed]
+    unsigned int *counter;   // zero between launches
+    double *result;          // [kMaxRed] written by the last block
+};
+
+// ---------------------------------------------------------------------------
+// solver scalar state kept on the device (one per solve)
+// ---------------------------------------------------------------------------
+constexpr int kMaxBuf = 16;
+
+struct CGState {
+    double rr;          // |r_k|^2 of the iterated residual
+    double rr_prev;     // |r_{k-1}|^2
+    double rr_max;      // max |r|^2 since the last reliable update
+    double pAp;
+    double alpha;
+    double beta;
+    double delta2;      // delta^2 (reliable-update trigger)
+    double stop2;       // (tol |b|)^2: iterated residual below it asks for a check
+    double alpha_ring[kMaxBuf];
+    double hi_rr;       // |r_hi|^2 of the last true residual
+    double proj_re, proj_im;  // projection coefficient of p onto r_hi
+    double coef_re, coef_im;  // p <- coef * r_hi + beta * p at a reliable update
+    int active;         // kernels of an iteration run only while 1
+    int reason;         // why the iteration stopped (REASON_*)
+    int k;              // iterations done
+    int pr;             // Polak-Ribiere beta
+    int reproject;
+    int pad;
+};
+
+enum { REASON_NONE = 0, REASON_RELIABLE = 1, REASON_CONVERGED = 2, REASON_BREAKDOWN = 3 };
+
+// Finisher selected by a reducing kernel: what the last block does with the
+// reduced values.
+enum FinOp {
+    FIN_NONE = 0,
+    FIN_CG_ALPHA = 1,     // values: Re<p,Ap>, |Ap|^2            -> alpha
+    FIN_CG_BETA = 2,      // values: |r_new|^2, Re<r_new, r_old> -> beta, checks
+    FIN_CG_TRUE = 3,      // values: |r_hi|^2, Re/Im <r_hi, p>   -> projection, coef, beta
+    FIN_STORE = 4         // copy the sums to RedBuf::result only
+};
+
+// ---------------------------------------------------------------------------
+// kernel parameter blocks
+// ---------------------------------------------------------------------------
+struct GaugeView {
+    const char *fat;
+    const char *lng;
+    float fat_scale_f, lng_scale_f;    // decode scale of fixed point (FP32 compute)
+    double fat_scale_d, lng_scale_d;   // decode scale (FP64 compute)
+};
+
+struct DslashArgs {
+    Geom g;
+    GaugeView gv;
+    int out_parity;
+    const char *in;         // input parity field
+    char *out;              // output parity field
+    const char *y;          // xpay field (output parity), may be null
+    double a;               // out = a*y + sign*D in (xpay) or sign*D in
+    int sign;               // +1 or -1
+    int xpay;
+    const int *active;      // skip when *active == 0 (null: always run)
+    int *err;               // set to 1 on a non-finite store
+    RedBuf red;
+    int fin;
+    CGState *st;
+    int slot;               // ring slot handed to the finisher
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// Returns false when the (gauge, spinor, compute, long_recon) combination has
+// no kernel.
+bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a,
+                   cudaStream_t s);
+
+void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);
+void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s);
+
+// gauge preparation
+// out_max / out_maxdev must be zeroed before the launch (atomic max)
+void launch_absmax(int64_t n, const double *x, double *out_max, cudaStream_t s);
+void launch_r12_check(const Geom &g, const double *links, int k, double *out_maxdev, cudaStream_t s);
+void launch_quantise_links(const Geom &g, int gf, int recon, const double *links, double inv, char *out,
+                           cudaStream_t s);
+
+
+// ---------------------------------------------------------------------------
+// host objects behind the opaque ABI handles
+// ---------------------------------------------------------------------------
+struct LinkCopy {
+    int gf = -1, recon = 0;
+    char *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace hisq
+
+struct hisq_gauge {
+    hisq::Geom geom;
+    int dims[4];
+    unsigned flags;
+    double *fat64 = nullptr;   // device FP64 [mu][lex][18]
+    double *lng64 = nullptr;
+    double fat_max = 0, lng_max = 0;
+    bool fat_r12_ok = false, lng_r12_ok = false;
+    std::vector<hisq::LinkCopy> fat_copies, lng_copies;
+};
+
+namespace hisq {
+// Optional per-launch timing (benchmarks): launches made outside graph
+// capture are bracketed by CUDA events on their own stream.
+enum ProfKind { PROF_STENCIL = 0, PROF_STENCIL_HI = 1, PROF_BLAS = 2, PROF_CONVERT = 3, PROF_NKIND = 4 };
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+        double bytes;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[PROF_NKIND] = {0, 0, 0, 0};
+    int64_t launches[PROF_NKIND] = {0, 0, 0, 0};
+    double bytes[PROF_NKIND] = {0, 0, 0, 0};
+};
+}  // namespace hisq
+
+struct hisq_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    cudaStream_t stream = nullptr;
+    hisq::RedBuf red{};
+    int *err_flag = nullptr;         // device int
+    std::string last_error;
+    std::mutex mu;
+    std::vector<hisq_gauge *> gauges;
+    // scratch fields used by hisq_dslash (grown on demand)
+    char *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int64_t launches = 0;            // kernels launched (graph replays count their nodes)
+    bool capturing = false;          // a solver is recording a graph on its stream
+    hisq::Profiler prof;
+};
+
+namespace hisq {
+
+// status helpers (context.cu)
+hisq_status fail(hisq_ctx *c, hisq_status s, const char *fmt, ...);
+hisq_status cuda_fail(hisq_ctx *c, cudaError_t e, const char *what);
+hisq_status ctx_alloc(hisq_ctx *c, size_t bytes, void **p);
+void ctx_free(hisq_ctx *c, void *p, size_t bytes);
+cudaStream_t pick_stream(hisq_ctx *c, void *s);
+
+// launch bookkeeping: call before / after every kernel launch on stream s
+struct LaunchScope {
+    hisq_ctx *c;
+    cudaStream_t s;
+    int kind;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchScope(hisq_ctx *c, cudaStream_t s, int kind, double bytes);
+    ~LaunchScope();
+};
+void prof_flush(hisq_ctx *c);   // resolve pending event pairs (synchronises on them)
+bool stream_capturing(cudaStream_t s);
+
+// A validated triplet: returns HISQ_OK and the device view of the gauge copy.
+hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, GaugeView *v);
+hisq_status check_prec(hisq_ctx *c, const hisq_prec &p);
+
+}  // namespace hisq

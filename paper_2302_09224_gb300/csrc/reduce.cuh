@@ -1,0 +1,84 @@
+// reduce.cuh -- deterministic FP64 reductions fused into producing kernels.
+//
+// Each block reduces its threads' values with a fixed shuffle/shared-memory
+// tree and writes one partial per value; the last block to finish (detected
+// with a device-scope counter) sums the partials in a fixed order, so the
+// result depends only on the grid shape, never on block scheduling.  The last
+// block then runs a finisher that updates the solver's device-side scalars,
+// which keeps a whole iteration on the device (and capturable in a graph).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hisq {
+
+template <int NR>
+__device__ __forceinline__ void warp_sum(double v[NR])
+{
+#pragma unroll
+    for (int k = 0; k < NR; k++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+}
+
+// Sum over the block; the result is valid in thread 0 only.
+template <int NR>
+__device__ __forceinline__ void block_sum(double v[NR], double (*sh)[NR])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    warp_sum<NR>(v);
+    __syncthreads();  // sh may be reused from a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NR; k++) sh[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) v[k] = lane < nw ? sh[lane][k] : 0.0;
+        warp_sum<NR>(v);
+    }
+}
+
+// Returns true in every thread of the last block, with the grid totals in
+// `tot` (shared memory).  All threads of every block must call it.
+template <int NR>
+__device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
+{
+    __shared__ double sh[32][NR];
+    __shared__ int is_last;
+    block_sum<NR>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) rb.partials[(size_t)blockIdx.x * NR + k] = v[k];
+        __threadfence();
+        const unsigned prev = atomicAdd(rb.counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double w[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) w[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        const volatile double *p = rb.partials + (size_t)b * NR;
+#pragma unroll
+        for (int k = 0; k < NR; k++) w[k] += p[k];
+    }
+    block_sum<NR>(w, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) {
+            tot[k] = w[k];
+            rb.result[k] = w[k];
+        }
+        *rb.counter = 0u;
+    }
+    __syncthreads();
+    return true;
+}
+
+}  // namespace hisq

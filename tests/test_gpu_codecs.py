@@ -1,0 +1,114 @@
+"""GPU storage-format codecs against the oracle's codecs, bit for bit.
+
+Every kernel of the library stores and loads fields through the same device
+codecs; ``hisq_spinor_pack`` / ``hisq_spinor_unpack`` expose them.  Packed
+records must equal the oracle's byte for byte (the planar device layout is
+re-assembled into per-site records first), including zeros, ties, extreme
+exponents and non-finite inputs, which both sides count and store as zero.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_09224_gb300 import hisq
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hisq.hisq_create(0)
+    yield c
+    hisq.hisq_destroy(c)
+
+
+def sites(n, seed):
+    g = np.random.Generator(np.random.Philox(key=seed))
+    v = g.standard_normal((n, 6)) * np.exp(g.uniform(-20, 20, size=(n, 1)))
+    v[::7, 3] = 0.0
+    v[5] = 0.0
+    v[6] = [1, 0.5, -0.25, 0, 0, 0]                                   # ties
+    v[7] = [1, 5.7220458984375e-06, 9.5367431640625e-06, -5.7220458984375e-06, 0, 0]
+    v[8] = [3e-39, -1e-40, 0, 0, 0, 2e-45]                            # below FP32 normal
+    v[9] = [3.0e38, -1e38, 0, 1, 0, 0]                                # near FP32 max
+    v[10, 2] = np.nan
+    v[11, 0] = np.inf
+    return v
+
+
+def device_pack(ctx, fmt, v):
+    n = len(v)
+    x = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    buf = torch.zeros(hisq.hisq_spinor_bytes(fmt, n), dtype=torch.uint8, device="cuda")
+    bad = hisq.hisq_spinor_pack(ctx, fmt, n, x, buf)
+    return buf.cpu().numpy(), bad
+
+
+@pytest.mark.parametrize("n", [1, 37, 4096 + 13])
+def test_half_bit_exact(ctx, orc, n):
+    v = sites(max(n, 16), n)[:max(n, 16)]
+    buf, bad = device_pack(ctx, hisq.HISQ_SPINOR_HALF16, v)
+    rec, obad = orc.half_pack(v.astype(np.float32))
+    assert bad == obad
+    np.testing.assert_array_equal(buf.reshape(-1, 16), rec)
+
+
+@pytest.mark.parametrize("n", [16, 4096 + 13])
+def test_int20_bit_exact(ctx, orc, n):
+    v = sites(n, 100 + n)
+    buf, bad = device_pack(ctx, hisq.HISQ_SPINOR_INT20, v)
+    w, obad = orc.int20_pack(v.astype(np.float32))
+    assert bad == obad
+    np.testing.assert_array_equal(buf.view(np.uint32).reshape(-1, 4), w)
+
+
+@pytest.mark.parametrize("n", [16, 4096 + 13])
+def test_int30_bit_exact(ctx, orc, n):
+    v = sites(n, 200 + n)
+    v[12] = [1e300, 0, 0, 0, 0, 0]    # beyond the 8-bit exponent: flagged on both sides
+    buf, bad = device_pack(ctx, hisq.HISQ_SPINOR_INT30, v)
+    w, obad = orc.int30_pack(v)
+    assert bad == obad >= 3
+    a = buf[:16 * n].view(np.uint32).reshape(n, 4)
+    b = buf[16 * n:].view(np.uint32).reshape(n, 2)
+    np.testing.assert_array_equal(np.concatenate([a, b], axis=1), w)
+
+
+def test_f32_f64_layouts(ctx):
+    n = 1000
+    v = sites(n, 7)[20:]
+    n = len(v)
+    buf, _ = device_pack(ctx, hisq.HISQ_SPINOR_F32, v)
+    f = v.astype(np.float32)
+    np.testing.assert_array_equal(buf[:16 * n].view(np.float32).reshape(n, 4), f[:, :4])
+    np.testing.assert_array_equal(buf[16 * n:].view(np.float32).reshape(n, 2), f[:, 4:])
+    buf, _ = device_pack(ctx, hisq.HISQ_SPINOR_F64, v)
+    d = buf.view(np.float64).reshape(3, n, 2)
+    np.testing.assert_array_equal(d.transpose(1, 0, 2).reshape(n, 6), v)
+
+
+@pytest.mark.parametrize("fmt,compute", [("half", 0), ("int20", 0), ("int30", 1), ("int30", 0), ("f32", 0)])
+def test_unpack_matches_oracle(ctx, orc, fmt, compute):
+    n = 3000
+    v = sites(n, 300)
+    v = v[np.all(np.isfinite(v), axis=1)]
+    v = v[np.abs(v).max(axis=1) < 1e30]
+    n = len(v)
+    code = hisq.SPINOR_FMT[fmt]
+    x = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    buf = torch.zeros(hisq.hisq_spinor_bytes(code, n), dtype=torch.uint8, device="cuda")
+    hisq.hisq_spinor_pack(ctx, code, n, x, buf)
+    out = torch.empty_like(x)
+    hisq.hisq_spinor_unpack(ctx, code, compute, n, buf, out)
+    got = out.cpu().numpy()
+    if fmt == "half":
+        ref = orc.half_unpack(orc.half_pack(v.astype(np.float32))[0]).astype(np.float64)
+    elif fmt == "int20":
+        ref = orc.int20_unpack(orc.int20_pack(v.astype(np.float32))[0]).astype(np.float64)
+    elif fmt == "int30":
+        ref = orc.int30_unpack(orc.int30_pack(v)[0])
+        if compute == 0:  # FP32 decode: round the integer, scale exactly
+            ref = ref.astype(np.float32).astype(np.float64)
+    else:
+        ref = v.astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(got, ref)

@@ -1,0 +1,200 @@
+"""GPU stencil against the FP64 oracle, per precision triplet (Sec. 3, Sec. 4.2).
+
+For every triplet the C-ABI ``hisq_dslash`` (input rounded into the spinor
+format, links in the gauge format, arithmetic in the compute precision,
+output repacked) is compared with
+
+* the exact FP64 stencil (the oracle's O3), relative L2 within the stated
+  per-format bound, and
+* the oracle's format emulation (fields rounded exactly as stored, then the
+  FP64 stencil): the remaining difference is compute rounding plus the
+  rounding of the stored output, bounded per format,
+
+on lattices that exercise a ragged last block, the 2^4 and 4^4 aliasing of the
+three-hop term, non-cubic extents and antiperiodic time.  The orderings the
+paper reports for the deviation (Sec. 4.2: 30-bit with FP64 compute about two
+orders below FP32; 20-bit only modestly better than half) are checked too.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_09224_gb300 import hisq, synth
+
+pytestmark = pytest.mark.gpu
+
+# relative L2 bounds against the exact FP64 stencil
+BOUND_EXACT = {"f64": 1e-12, "f32": 1e-6, "half": 1e-3, "int20": 3e-4, "int30": 1e-8, "int30f32": 2e-6}
+# relative L2 bounds against the format emulation (compute + output rounding)
+BOUND_EMUL = {"f64": 1e-13, "f32": 1e-6, "half": 5e-5, "int20": 3e-6, "int30": 3e-9, "int30f32": 1e-6}
+SPINOR = {"f64": "f64", "f32": "f32", "half": "half", "int20": "int20", "int30": "int30", "int30f32": "int30"}
+GAUGE = {"f64": "f64", "f32": "f32", "half": "fix16", "int20": "fix16", "int30": "fix32", "int30f32": "fix32"}
+COMPUTE_F32 = {"f64": False, "f32": True, "half": True, "int20": True, "int30": False, "int30f32": True}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hisq.hisq_create(0)
+    yield c
+    hisq.hisq_destroy(c)
+
+
+_cache = {}
+
+
+def lattice(dims, anti):
+    key = (dims, anti)
+    if key not in _cache:
+        fat, lng = synth.gauge_pair(dims, seed=0, antiperiodic_t=anti)
+        _cache[key] = (fat.numpy(), lng.numpy())
+    return _cache[key]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def run_gpu(ctx, dims, anti, name, recon, parity, a, on_device=True):
+    fat, lng = lattice(dims, anti)
+    flags = hisq.HISQ_GAUGE_ANTIPERIODIC_T if anti else 0
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda(), flags)
+    try:
+        full = parity == 2
+        x = synth.spinor(dims, 1000, full=full).numpy()
+        y = synth.spinor(dims, 1001, full=full).numpy()
+        if on_device:
+            xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+            out = torch.empty_like(xd)
+            hisq.hisq_dslash(ctx, g, hisq.prec(name, recon), parity, a, yd if a else None, xd, out, True)
+            torch.cuda.synchronize()
+            out = out.cpu().numpy()
+        else:
+            out = np.empty_like(x)
+            hisq.hisq_dslash(ctx, g, hisq.prec(name, recon), parity, a, y if a else None, x, out, False)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+    return x, y, out
+
+
+def oracle_apply(orc, dims, fat, lng, parity, a, x, y):
+    if parity == 2:
+        d = np.stack([orc.dslash(dims, fat, lng, 0, x[1]), orc.dslash(dims, fat, lng, 1, x[0])])
+    else:
+        d = orc.dslash(dims, fat, lng, parity, x)
+    return a * y - d if a else d
+
+
+CASES = [
+    ((4, 4, 4, 4), False, 0, 0.0),
+    ((6, 4, 4, 10), False, 1, 0.0),     # Vh = 480: ragged last block
+    ((4, 6, 8, 10), True, 2, 0.0),      # non-cubic, antiperiodic, full lattice
+    ((2, 2, 2, 2), False, 1, 0.3),      # every hop aliases
+    ((8, 8, 8, 8), False, 0, 0.7),      # several blocks, xpay
+]
+
+
+@pytest.mark.parametrize("name", list(BOUND_EXACT))
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("dims,anti,parity,a", CASES)
+def test_dslash_parity(ctx, orc, name, recon, dims, anti, parity, a):
+    fat, lng = lattice(dims, anti)
+    x, y, out = run_gpu(ctx, dims, anti, name, recon, parity, a)
+    exact = oracle_apply(orc, dims, fat, lng, parity, a, x, y)
+    err = rel(out, exact)
+    assert err <= BOUND_EXACT[name], (name, recon, err)
+    # format emulation: the fields exactly as the kernel sees them
+    sf = SPINOR[name]
+    c32 = COMPUTE_F32[name]
+    fe = orc.gauge_emulate(dims, fat, GAUGE[name], 18, long_link=False, antiperiodic_t=anti, compute_f32=c32)
+    le = orc.gauge_emulate(dims, lng, GAUGE[name], recon, long_link=True, antiperiodic_t=anti, compute_f32=c32)
+    xe = orc.spinor_emulate(x, sf).reshape(x.shape)
+    ye = orc.spinor_emulate(y, sf).reshape(y.shape)
+    emul = oracle_apply(orc, dims, fe, le, parity, a, xe, ye)
+    assert rel(out, emul) <= BOUND_EMUL[name], (name, recon, rel(out, emul))
+
+
+def test_host_pointers_match_device(ctx):
+    dims = (4, 4, 4, 8)
+    _, _, o1 = run_gpu(ctx, dims, False, "int20", 12, 0, 0.5, on_device=True)
+    _, _, o2 = run_gpu(ctx, dims, False, "int20", 12, 0, 0.5, on_device=False)
+    np.testing.assert_array_equal(o1, o2)
+
+
+def test_deviation_orderings(ctx, orc):
+    """Sec. 4.2: 30-bit + FP64 ~100x below FP32; 30-bit + FP32 ~ FP32; 20-bit < half."""
+    dims = (8, 8, 8, 8)
+    fat, lng = lattice(dims, False)
+    err = {}
+    for name in ("f32", "half", "int20", "int30", "int30f32"):
+        x, y, out = run_gpu(ctx, dims, False, name, 12, 0, 0.0)
+        err[name] = rel(out, orc.dslash(dims, fat, lng, 0, x))
+    assert err["int30"] * 30 < err["f32"]
+    assert 0.2 < err["int30f32"] / err["f32"] < 5
+    assert err["int20"] < err["half"]
+
+
+def test_r12_refused_for_fat_and_nonunitary(ctx):
+    dims = (4, 4, 4, 4)
+    fat, lng = lattice(dims, False)
+    bad = lng.copy()
+    bad[0, 0, 0, 0, 0, 2, 2, 0] += 0.5   # breaks unitarity of one long link
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(bad).cuda())
+    try:
+        x = synth.spinor(dims, 1).cuda()
+        out = torch.empty_like(x)
+        with pytest.raises(hisq.HisqError, match="EINVAL"):
+            hisq.hisq_dslash(ctx, g, hisq.prec("half", 12), 0, 0.0, None, x, out, True)
+        hisq.hisq_dslash(ctx, g, hisq.prec("half", 18), 0, 0.0, None, x, out, True)
+        p = hisq.prec("half", 18)
+        p.fat_recon = 12
+        with pytest.raises(hisq.HisqError, match="EINVAL"):
+            hisq.hisq_dslash(ctx, g, p, 0, 0.0, None, x, out, True)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+
+
+def test_invalid_inputs(ctx):
+    dims = (4, 4, 4, 4)
+    fat, lng = lattice(dims, False)
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_load_gauge(ctx, (4, 4, 3, 4), torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    nan = fat.copy()
+    nan[1, 1, 1, 1, 1, 0, 0, 1] = np.nan
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(nan).cuda(), torch.from_numpy(lng).cuda())
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    try:
+        x = synth.spinor(dims, 1).cuda()
+        x[3, 1, 0] = float("inf")
+        out = torch.empty_like(x)
+        with pytest.raises(hisq.HisqError, match="non-finite"):
+            hisq.hisq_dslash(ctx, g, hisq.prec("int20"), 0, 0.0, None, x, out, True)
+        bad = hisq.prec("int20")
+        bad.compute = hisq.HISQ_COMPUTE_F64
+        with pytest.raises(hisq.HisqError, match="unsupported"):
+            hisq.hisq_dslash(ctx, g, bad, 0, 0.0, None, x, out, True)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+
+
+@pytest.mark.parametrize("name", ["f64", "half", "int20"])
+def test_full_size_sampled(ctx, orc, name):
+    """32^3 x 64 (the benchmark lattice), whole-lattice launch, sampled sites vs the oracle."""
+    dims = (32, 32, 32, 64)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    try:
+        x = synth.spinor(dims, 1000, device="cuda")
+        out = torch.empty_like(x)
+        hisq.hisq_dslash(ctx, g, hisq.prec(name, 12), 1, 0.0, None, x, out, True)
+        torch.cuda.synchronize()
+        vh = x.shape[0]
+        cbs = np.unique(np.concatenate([np.arange(64), vh - 1 - np.arange(64),
+                                        np.random.Generator(np.random.Philox(key=9)).integers(0, vh, 2000)]))
+        ref = orc.dslash_sites(dims, fat.cpu(), lng.cpu(), 1, x.cpu(), cbs)
+        got = out.cpu().numpy()[cbs]
+        assert rel(got, ref) <= BOUND_EXACT[name]
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+        del fat, lng
+        torch.cuda.empty_cache()

@@ -189,3 +189,13 @@ def test_reconstruct12(orc):
     assert np.abs(e32 - lng).max() <= 1e-6
     e16 = orc.gauge_emulate(dims, lng, "fix16", 12, long_link=True, compute_f32=False)
     assert np.abs(e16 - lng).max() <= 4.0 / 32767
+
+
+def test_half_floor(orc):
+    # 32767/max overflows FP32 below ~1e-34: such sites are stored as zero
+    v = np.array([[1e-35, 0, 0, 0, 0, -2e-36], [2.0 ** -109, 0, 0, 0, 0, 0]], np.float32)
+    rec, bad = orc.half_pack(v)
+    assert bad == 0
+    u = orc.half_unpack(rec)
+    assert np.all(u[0] == 0)
+    assert abs(u[1, 0] - 2.0 ** -109) <= 2.0 ** -109 / 32767
