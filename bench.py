@@ -1,0 +1,410 @@
+"""Benchmark: HISQ stencil bandwidth and time-to-1e-10 of the mixed-precision CG.
+
+One step = one complete even/odd CG solve, (4m^2 - D_eo D_oe) x = b, to a
+1e-10 FP64 true residual on a 32^3 x 64 lattice (m = 0.01, delta = 0.1) with
+the sloppy iteration in the paper's 16-bit gauge / 20-bit fermion / FP32
+triplet and FP64 reliable updates, from a right-hand side already resident in
+HBM.  ``value`` is the solve's algorithmic HBM traffic (every kernel's arrays
+counted once per launch) divided by the step time; ``roofline`` reports the
+stencil kernel alone from CUDA events around each of its launches in the
+timed region; ``time_to_solution`` compares the same solve with the plain FP64
+GPU CG.  ``e2e`` repeats the step through the C ABI with host buffers (the
+right-hand side uploaded and the solution read back inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle (the only other implementation
+of this method here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HISQ Dslash HBM GB/s (% of peak); time-to-1e-10 solve, custom fmt vs FP64 GPU"
+DIMS = (32, 32, 32, 64)
+MASS = 0.01
+TOL = 1e-10
+DELTA = 0.1
+SLOPPY = "int20"
+WORKLOAD = ("mixed-precision even/odd CG to 1e-10 (16-bit gauge / 20-bit fermion / FP32 sloppy, r12 long links, "
+            "FP64 x, true residuals and reductions, delta 0.1) on a 32^3x64 lattice, m=0.01, seeded near-identity "
+            "SU(3) links (eps 0.3, fat x0.8, staggered phases), Gaussian source")
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("dslash.cuh", "codecs.cuh", "reduce.cuh", "finish.cuh"):
+        with open(os.path.join(ROOT, "paper_2302_09224_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the stencil from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "stencil_int20_32x32x32x64.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram bytes per launch \(scaled to 32\^3x64, mean of both passes\):\s*([0-9.eE+]+)", text)
+    if not (m_hash and m_b) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v, device):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, v, device):
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(fat_h, lng_h, b_h, iters):
+    """Time `iters` FP64 CG iterations of the oracle on the host cores."""
+    import oracle
+
+    t0 = time.perf_counter()
+    x, st, it, tr = oracle.cg(DIMS, fat_h, lng_h, MASS, b_h, TOL, maxiter=iters)
+    dt = time.perf_counter() - t0
+    return dt, it, oracle.get_threads()
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2302_09224_gb300 import synth
+
+    oracle.build()
+    fat, lng = synth.gauge_pair(DIMS, seed=0)
+    b = synth.spinor(DIMS, synth.rhs_seed(0))
+    fat_h, lng_h, b_h = fat.numpy(), lng.numpy(), b.numpy()
+    sample_iters = args.ref_iters
+    times = []
+    for s in range(args.warmup + args.steps):
+        dt, it, cores = oracle_sample(fat_h, lng_h, b_h, sample_iters)
+        if s >= args.warmup:
+            times.append(dt / (it + 2))  # it iterations + the initial and final residual operator applications
+    per_iter = statistics.median(times)
+    # the GPU solve's iteration count and bytes are the unit of one step
+    gpu_iters = args.solve_iters
+    bytes_per_step = args.solve_bytes
+    step_s = per_iter * gpu_iters
+    value = bytes_per_step / step_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample_iters} FP64 CG iterations of the C oracle on the full 32^3x64 "
+                                       f"lattice per step, extrapolated to the GPU solve's {gpu_iters} iterations"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = hisq.hisq_create(local)
+    fat, lng = synth.gauge_pair(DIMS, seed=0, device=dev)
+    g = hisq.hisq_load_gauge(ctx, DIMS, fat, lng)
+    b = synth.spinor(DIMS, synth.rhs_seed(rank), device=dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.Stream(device=dev)
+
+    def params(name, delta, on_device=1, graph=0):
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.delta, p.on_device = MASS, TOL, delta, on_device
+        p.sloppy = hisq.prec(name, 12 if name != "f64" else 18)
+        p.use_graph = graph
+        p.stream = stream.cuda_stream
+        p.maxiter = 100000
+        return p
+
+    p = params(SLOPPY, DELTA)
+    # one untimed solve with per-launch accounting: algorithmic bytes per step
+    hisq.hisq_profile_reset(ctx)
+    hisq.hisq_profile_enable(ctx, True)
+    with torch.cuda.stream(stream):
+        st, info0 = hisq.hisq_cg(ctx, g, p, b, x)
+    bytes_per_step = sum(hisq.hisq_profile_read(ctx, k).bytes for k in range(3))
+    for _ in range(max(0, args.warmup - 1)):
+        x.zero_()
+        with torch.cuda.stream(stream):
+            hisq.hisq_cg(ctx, g, p, b, x)
+    hisq.hisq_profile_reset(ctx)
+    torch.cuda.synchronize()
+    barrier(pg)
+    l0 = hisq.hisq_launch_count(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.zero_()  # start each solve from x = 0 (on the default stream, ordered by the sync below)
+            torch.cuda.current_stream().synchronize()
+            with torch.cuda.stream(stream):
+                st, info = hisq.hisq_cg(ctx, g, p, b, x)
+            infos.append((st, info.iters, info.true_residual, info.reliable_updates))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = hisq.hisq_launch_count(ctx) - l0
+    stencil = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+    blas = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_BLAS)
+    hisq.hisq_profile_enable(ctx, False)
+    barrier(pg)
+    ms_max = max_over_ranks(pg, ms, dev)
+    total_bytes = sum_over_ranks(pg, bytes_per_step * args.steps, dev)
+    value = total_bytes / (ms_max / 1e3) / 1e9
+
+    # oracle check of the returned solution (FP64 true residual on the CPU)
+    true_res_oracle = None
+    cpu = None
+    if rank == 0:
+        import oracle
+
+        oracle.build()
+        fat_h, lng_h, b_h = fat.cpu().numpy(), lng.cpu().numpy(), b.cpu().numpy()
+        xs = x.cpu().numpy()
+        r = b_h - oracle.mee(DIMS, fat_h, lng_h, MASS, xs)
+        true_res_oracle = float(np.linalg.norm(r) / np.linalg.norm(b_h))
+        if world == 1 and not args.no_cpu:
+            dt, it, cores = oracle_sample(fat_h, lng_h, b_h, args.ref_iters)
+            per_iter = dt / (it + 2)
+            cpu_step = per_iter * info.iters
+            cpu = {"value": bytes_per_step / cpu_step / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{args.ref_iters} FP64 CG iterations of the C oracle (OpenMP) on the full 32^3x64 "
+                             f"lattice, {dt:.1f} s, extrapolated to the GPU solve's {info.iters} iterations"}
+
+    # end to end through the ABI with host buffers
+    bh = b.cpu().numpy()
+    xh = np.zeros_like(bh)
+    ph = params(SLOPPY, DELTA, on_device=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        xh[:] = 0
+        hisq.hisq_cg(ctx, g, ph, bh, xh)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(pg, e2e_s, dev)
+    e2e_value = sum_over_ranks(pg, bytes_per_step, dev) / e2e_s / 1e9
+
+    # plain FP64 GPU CG on the same system (time-to-solution comparison)
+    p64 = params("f64", 0.0, graph=0)
+    x64 = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    with torch.cuda.stream(stream):
+        st64, info64 = hisq.hisq_cg(ctx, g, p64, b, x64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_s = f0.elapsed_time(f1) / 1e3
+
+    peak, peak_kind = measured_peak()
+    achieved = stencil.bytes / (stencil.ms / 1e3) / 1e9 if stencil.ms > 0 else 0.0
+    per_launch_bytes = stencil.bytes / max(1, stencil.launches)
+    traffic = profiled_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL, "delta": DELTA,
+                   "sloppy": "fix16/int20/f32 r12", "l2": "no flush: every step streams >1 GB per iteration "
+                   "(links 0.5 GB per stencil pass), far above the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "dslash_kernel<FIX16, INT20, float, r12> (both passes of M_ee)",
+                     "bytes_per_launch": per_launch_bytes, "launches": stencil.launches,
+                     "ms_per_launch": stencil.ms / max(1, stencil.launches)},
+        "blas": {"achieved_gbs": blas.bytes / (blas.ms / 1e3) / 1e9 if blas.ms > 0 else 0.0,
+                 "share_of_step": blas.ms / ms if ms > 0 else 0.0},
+        "time_to_solution": {"custom_s": ms / args.steps / 1e3, "fp64_s": fp64_s,
+                             "speedup_vs_fp64": fp64_s / (ms / args.steps / 1e3),
+                             "iters_custom": infos[-1][1], "iters_fp64": info64.iters,
+                             "reliable_updates": infos[-1][3],
+                             "true_residual_custom": infos[-1][2], "true_residual_fp64": info64.true_residual,
+                             "true_residual_oracle": true_res_oracle,
+                             "status": [hisq.STATUS_NAMES[i[0]] for i in infos] + [hisq.STATUS_NAMES[st64]]},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(bh.nbytes),
+                "d2h_bytes_per_step": int(xh.nbytes), "s_per_step": e2e_s},
+        "gpu_launches": int(sum_over_ranks(pg, launches, dev)),
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def run_stencil_only(args):
+    """A few stencil applications on one lattice (the small case for ncu captures)."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims = tuple(int(v) for v in args.stencil.split(","))
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    del fat, lng
+    x = synth.spinor(dims, 1000, device="cuda")
+    out = torch.empty_like(x)
+    for _ in range(args.launches):
+        hisq.hisq_dslash(ctx, g, hisq.prec(args.prec, 12), 0, 0.0, None, x, out, True)
+    torch.cuda.synchronize()
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    print(json.dumps({"stencil": list(dims), "prec": args.prec, "launches": args.launches}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per CPU sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--solve-iters", type=int, default=2100,
+                    help="reference arm: iterations of one GPU solve (extrapolation unit)")
+    ap.add_argument("--solve-bytes", type=float, default=2.6e12,
+                    help="reference arm: algorithmic bytes of one GPU solve")
+    ap.add_argument("--stencil", default=None, help="LX,LY,LZ,LT: only run stencil applications (profiling)")
+    ap.add_argument("--prec", default="int20")
+    ap.add_argument("--launches", type=int, default=3)
+    args = ap.parse_args()
+    if args.stencil:
+        return run_stencil_only(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
         real r[6], ap[6], rn[6];
         Spinor<SF>::load(a.v0, a.n, i, r);
         Spinor<SF>::load(a.v1, a.n, i, ap);
-        const real alpha = (real)a.st->alpha;
+        const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             rn[k] = r[k] - alpha * ap[k];
@@ -46,7 +46,12 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
         if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
     }
     __shared__ double tot[2];
-    if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
+    if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) {
+        if (a.fin)
+            run_finisher(a.fin, tot, a.fst, a.slot);
+        else
+            run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
+    }
 }
 
 template <int SF, typename real>
@@ -116,7 +121,12 @@ __global__ void __launch_bounds__(kBlock) true_residual_kernel(BlasArgs a)
         }
     }
     __shared__ double tot[3];
-    if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) run_finisher(FIN_CG_TRUE, tot, a.st, a.slot);
+    if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) {
+        if (a.fin)
+            run_finisher(a.fin, tot, a.fst, a.slot);
+        else
+            run_finisher(FIN_CG_TRUE, tot, a.st, a.slot);
+    }
 }
 
 // p' = coef r_hi + beta p (coef complex); clears the alpha ring.

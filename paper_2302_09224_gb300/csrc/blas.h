@@ -24,6 +24,9 @@ struct BlasArgs {
     int *err;
     RedBuf red;
     CGState *st;
+    int fin;                 // finisher override (0: the kernel's CG default)
+    void *fst;               // state for the override finisher
+    const double *alpha_src; // r_update: step size (null: st->alpha)
 };
 
 void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s);

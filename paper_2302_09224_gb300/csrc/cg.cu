@@ -59,7 +59,7 @@ hisq_prec prec_f64()
 
 // out_even = diag * in_even - D_eo D_oe in_even, with tmp an odd-parity field.
 void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
-               const char *in, char *tmp, char *out, int fin, CGState *st, int slot, const int *active, int kind,
+               const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
                cudaStream_t s)
 {
     DslashArgs d{};
@@ -261,6 +261,13 @@ struct CGRun {
         init.pr = cfg.pr;
         init.reproject = cfg.reproject;
         init.active = 1;
+        if (cfg.p_init) {
+            // continue a previous recurrence: its gradient vector enters the
+            // first restart (re-projected, with beta = |r_hi|^2 / rr_prev_init)
+            LaunchScope ls(c, s, PROF_CONVERT, 2.0 * 48 * vh);
+            launch_convert(cfg.p_init_fmt, cfg.sloppy.spinor, vh, cfg.p_init, slot(0), c->err_flag, s);
+            init.rr_prev = cfg.rr_prev_init;
+        }
         cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s);
         e = reliable_update(b64, x64, x_zero, 0);
         if (e) return e;
@@ -318,10 +325,8 @@ struct CGRun {
         if (exec) cudaGraphExecDestroy(exec);
         if (e) return e;
         if (status != HISQ_OK) {
-            // bring x up to date (slots of an unfinished block) and measure it
-            const int j = st_h->k > 0 ? (st_h->k - 1) % cfg.nbuf : 0;
+            // bring x up to date (an unfinished block's slots) and measure it
             if (status == HISQ_EBREAKDOWN) flush(cfg.nbuf, nullptr, x64);
-            (void)j;
             e = reliable_update(b64, x64, false, 0);
             if (e) return e;
         }

@@ -28,13 +28,21 @@ struct CGConfig {
     hisq_prec sloppy{};
     int nbuf = 8;
     int pr = 1, reproject = 1, use_graph = 1;
+    // continuation (multi-shift refinement of the base system): a gradient
+    // vector in format p_init_fmt and the |r|^2 it was built against
+    const char *p_init = nullptr;
+    int p_init_fmt = 0;
+    double rr_prev_init = 0.0;
 };
+
+// field conversion between any two storage formats (ms.cu)
+void launch_convert(int si, int so, int n, const char *in, char *out, int *err, cudaStream_t s);
 
 hisq_prec prec_f64();
 double stencil_bytes(const hisq_prec &p, int vh, bool xpay);
 
 void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
-               const char *in, char *tmp, char *out, int fin, CGState *st, int slot, const int *active, int kind,
+               const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
                cudaStream_t s);
 
 // Mixed-precision CG on (M_ee + sigma) x = b; b64 / x64 are FP64 planar device

@@ -15,9 +15,102 @@ __device__ __forceinline__ void stop_iterating(CGState *st, int reason)
     st->active = 0;
 }
 
-// sums: the grid totals of the reducing kernel; slot: ring slot of p.
-__device__ __forceinline__ void run_finisher(int fin, const double *sums, CGState *st, int slot)
+__device__ __forceinline__ void ms_stop(MSState *m, int reason)
 {
+    m->reason = reason;
+    m->active = 0;
+}
+
+// Multi-shift finishers (Sec. 2.2; the shifted recurrences of Jegerlehner,
+// hep-lat/9612014): r_i = zeta_i r with
+//   zeta_i' = zeta_i zeta_i^- a^- / (a b^- (zeta_i^- - zeta_i) + zeta_i^- a^- (1 + s_i a))
+//   alpha_i = a zeta_i'/zeta_i,  beta_i = b (zeta_i'/zeta_i)^2.
+__device__ __forceinline__ void run_ms_finisher(int fin, const double *sums, MSState *m)
+{
+    if (fin == FIN_MS_ALPHA) {
+        const double pAp = sums[0];
+        const double a = m->rr / pAp;
+        if (!(pAp > 0.0) || !isfinite(a)) {
+            m->alpha = 0.0;
+            ms_stop(m, REASON_BREAKDOWN);
+            return;
+        }
+        m->pAp = pAp;
+        m->alpha = a;
+        for (int i = 0; i < m->nshift; i++) {
+            if (!m->live[i]) {
+                m->alpha_i[i] = 0.0;
+                continue;
+            }
+            const double z = m->zeta[i], zm = m->zeta_prev[i];
+            const double den = a * m->beta_prev * (zm - z) + zm * m->alpha_prev * (1.0 + m->shift[i] * a);
+            const double zn = z * zm * m->alpha_prev / den;
+            if (!isfinite(zn) || zn == 0.0) {  // the shift has converged beyond representability
+                m->live[i] = 0;
+                m->frozen_at[i] = m->k;
+                m->alpha_i[i] = 0.0;
+                continue;
+            }
+            m->zeta_new[i] = zn;
+            m->alpha_i[i] = a * zn / z;
+        }
+    } else if (fin == FIN_MS_BETA) {
+        const double rr_new = sums[0];
+        const double b = rr_new / m->rr;
+        m->k += 1;
+        if (!isfinite(rr_new) || !isfinite(b)) {
+            ms_stop(m, REASON_BREAKDOWN);
+            return;
+        }
+        m->beta = b;
+        bool all_frozen = true;
+        for (int i = 0; i < m->nshift; i++) {
+            if (!m->live[i]) continue;
+            const double q = m->zeta_new[i] / m->zeta[i];
+            m->beta_i[i] = b * q * q;
+            m->zeta_prev[i] = m->zeta[i];
+            m->zeta[i] = m->zeta_new[i];
+            const double zr2 = m->zeta[i] * m->zeta[i] * rr_new;
+            m->freeze_next[i] = zr2 <= m->stop2[i];
+            if (i > 0 && !m->freeze_next[i]) all_frozen = false;
+        }
+        if (m->nshift == 1) all_frozen = m->freeze_next[0] != 0;
+        m->alpha_prev = m->alpha;
+        m->beta_prev = b;
+        m->rr_prev = m->rr;
+        m->rr = rr_new;
+        if (rr_new > m->rr_max) m->rr_max = rr_new;
+        if (all_frozen)
+            m->pending = REASON_CONVERGED;
+        else if (rr_new < m->delta2 * m->rr_max)
+            m->pending = REASON_RELIABLE;
+    } else if (fin == FIN_MS_APPLY) {
+        for (int i = 0; i < m->nshift; i++)
+            if (m->live[i] && m->freeze_next[i] && (i > 0 || m->nshift == 1)) {
+                m->live[i] = 0;
+                m->frozen_at[i] = m->k;
+            }
+        if (m->pending != REASON_NONE) {
+            ms_stop(m, m->pending);
+            m->pending = REASON_NONE;
+        }
+    } else if (fin == FIN_MS_TRUE) {
+        m->rr = sums[0];
+        m->rr_max = sums[0];
+        m->reason = REASON_NONE;
+        m->active = isfinite(sums[0]) ? 1 : 0;
+        if (!m->active) m->reason = REASON_BREAKDOWN;
+    }
+}
+
+// sums: the grid totals of the reducing kernel; slot: ring slot of p.
+__device__ __forceinline__ void run_finisher(int fin, const double *sums, void *state, int slot)
+{
+    if (fin >= FIN_MS_ALPHA) {
+        run_ms_finisher(fin, sums, static_cast<MSState *>(state));
+        return;
+    }
+    CGState *st = static_cast<CGState *>(state);
     if (fin == FIN_CG_ALPHA) {
         // sums = {Re<p, A p>, |A p|^2}
         const double pAp = sums[0];

@@ -99,6 +99,28 @@ struct CGState {
 
 enum { REASON_NONE = 0, REASON_RELIABLE = 1, REASON_CONVERGED = 2, REASON_BREAKDOWN = 3 };
 
+// Multi-shift CG (Sec. 2.2): the base recurrence plus, per shift, the
+// co-linearity factor zeta_i (r_i = zeta_i r) and its step sizes.
+constexpr int kMaxShift = 32;
+
+struct MSState {
+    double rr, rr_prev, rr_max, pAp;
+    double alpha, alpha_prev, beta, beta_prev;
+    double delta2;
+    double bb;                         // |b|^2
+    double shift[kMaxShift];           // s_i = sigma_i - sigma_0
+    double stop2[kMaxShift];           // (max(tol_i, floor) |b|)^2 on zeta_i^2 |r|^2
+    double zeta[kMaxShift], zeta_prev[kMaxShift], zeta_new[kMaxShift];
+    double alpha_i[kMaxShift], beta_i[kMaxShift];
+    int live[kMaxShift];               // shift still updated
+    int freeze_next[kMaxShift];        // freeze after this iteration's update
+    int frozen_at[kMaxShift];
+    int nshift;
+    int active, reason, pending;
+    int k;
+    int pad;
+};
+
 // Finisher selected by a reducing kernel: what the last block does with the
 // reduced values.
 enum FinOp {
@@ -106,7 +128,11 @@ enum FinOp {
     FIN_CG_ALPHA = 1,     // values: Re<p,Ap>, |Ap|^2            -> alpha
     FIN_CG_BETA = 2,      // values: |r_new|^2, Re<r_new, r_old> -> beta, checks
     FIN_CG_TRUE = 3,      // values: |r_hi|^2, Re/Im <r_hi, p>   -> projection, coef, beta
-    FIN_STORE = 4         // copy the sums to RedBuf::result only
+    FIN_STORE = 4,        // copy the sums to RedBuf::result only
+    FIN_MS_ALPHA = 5,     // values: Re<p0,Ap0>                  -> alpha, zeta_i', alpha_i
+    FIN_MS_BETA = 6,      // values: |r_new|^2                   -> beta, beta_i, freezing, decisions
+    FIN_MS_TRUE = 7,      // values: |r_hi|^2                    -> restart after a reliable update
+    FIN_MS_APPLY = 8      // no values: apply pending freezes and stop decisions
 };
 
 // ---------------------------------------------------------------------------
@@ -133,7 +159,7 @@ struct DslashArgs {
     int *err;               // set to 1 on a non-finite store
     RedBuf red;
     int fin;
-    CGState *st;
+    void *st;               // CGState or MSState, per finisher
     int slot;               // ring slot handed to the finisher
 };
 

@@ -43,19 +43,22 @@ __device__ __forceinline__ void block_sum(double v[NR], double (*sh)[NR])
 }
 
 // Returns true in every thread of the last block, with the grid totals in
-// `tot` (shared memory).  All threads of every block must call it.
+// `tot` (shared memory).  All threads of every block must call it.  Grids may
+// be two-dimensional (blocks are numbered x fastest).
 template <int NR>
 __device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
 {
     __shared__ double sh[32][NR];
     __shared__ int is_last;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
     block_sum<NR>(v, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; k++) rb.partials[(size_t)blockIdx.x * NR + k] = v[k];
+        for (int k = 0; k < NR; k++) rb.partials[(size_t)bid * NR + k] = v[k];
         __threadfence();
         const unsigned prev = atomicAdd(rb.counter, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return false;
@@ -63,7 +66,7 @@ __device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
     double w[NR];
 #pragma unroll
     for (int k = 0; k < NR; k++) w[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const volatile double *p = rb.partials + (size_t)b * NR;
 #pragma unroll
         for (int k = 0; k < NR; k++) w[k] += p[k];

@@ -1,0 +1,115 @@
+"""GPU multi-shift CG with refinement (Sec. 2.2) against the oracle.
+
+* 4^4: every shift's solution against a dense direct solve of M_ee + sigma_i;
+* 8^4 with twelve log-spaced shifts and log-spaced targets (the structure of
+  the rational-approximation workload): every shift's FP64 true residual,
+  recomputed by the CPU oracle, meets its own target for each sloppy /
+  refinement pairing;
+* Table 3's finding as an ordering: after the multi-shift stage the shifted
+  systems' true residuals are much smaller with the 30-bit format than with
+  FP32 at the same word size, so refinement needs fewer iterations;
+* the caller's shift order is kept (shifts are sorted internally), one shift
+  reduces to CG, bad arguments give EINVAL.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_09224_gb300 import hisq, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hisq.hisq_create(0)
+    yield c
+    hisq.hisq_destroy(c)
+
+
+def cvec(a):
+    a = np.asarray(a)
+    return (a[..., 0] + 1j * a[..., 1]).reshape(-1)
+
+
+def run_ms(ctx, dims, fat, lng, m, b, sig, tols, sloppy="int20", refine="int20", **kw):
+    g = hisq.hisq_load_gauge(ctx, dims, torch.as_tensor(fat).cuda(), torch.as_tensor(lng).cuda())
+    try:
+        p = hisq.hisq_default_params()
+        p.mass, p.on_device = m, 1
+        p.sloppy = hisq.prec(sloppy, 12)
+        p.refine = hisq.prec(refine, 12)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        bd = torch.as_tensor(b).cuda()
+        xs = [torch.zeros_like(bd) for _ in sig]
+        st, info = hisq.hisq_multishift_cg(ctx, g, p, sig, tols, bd, xs)
+        return st, info, [x.cpu().numpy() for x in xs]
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+
+
+def test_vs_dense_and_order(ctx, orc):
+    dims, m = (4, 4, 4, 4), 0.05
+    fat, lng = synth.gauge_pair(dims, seed=0)
+    b = synth.spinor(dims, 1000).numpy()
+    sig = [0.1, 0.001, 1.0, 0.01]      # unsorted on purpose
+    tols = [1e-10] * 4
+    st, info, xs = run_ms(ctx, dims, fat, lng, m, b, sig, tols)
+    assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+    for i, s in enumerate(sig):
+        a = orc.dense(dims, fat, lng, "mee", m=m, sigma=s)
+        xd = np.linalg.solve(a, cvec(b))
+        ev = np.linalg.eigvalsh(a)
+        assert np.linalg.norm(cvec(xs[i]) - xd) <= 10 * ev.max() / ev.min() * 1e-10 * np.linalg.norm(xd)
+        assert info.shift_resid[i] <= 1e-10
+
+
+def true_res(orc, dims, fat, lng, m, b, x, s):
+    r = b - orc.mee(dims, fat, lng, m, x, sigma=s)
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("sloppy,refine", [("int20", "int20"), ("int30", "int20"), ("f32", "half"), ("f64", "f64")])
+def test_twelve_shifts(ctx, orc, sloppy, refine):
+    dims, m = (8, 8, 8, 8), 0.005
+    fat, lng = synth.gauge_pair(dims, seed=0)
+    b = synth.spinor(dims, 1000).numpy()
+    sig = synth.shifts_logspaced(12)
+    tols = synth.shift_tolerances(12)
+    st, info, xs = run_ms(ctx, dims, fat, lng, m, b, sig, tols, sloppy, refine)
+    assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+    for i, s in enumerate(sig):
+        tr = true_res(orc, dims, fat, lng, m, b, xs[i], s)
+        assert tr <= tols[i] * 1.0000001, (i, tr, tols[i])
+        assert abs(tr - info.shift_resid[i]) <= 1e-3 * tr + 1e-16
+    # heavier shifts freeze no later than lighter ones
+    assert all(info.shift_iters[i] >= info.shift_iters[i + 1] for i in range(1, 11))
+
+
+def test_int30_beats_single_before_refinement(ctx):
+    """Table 3: shifted residuals after the multi-shift stage drop >10x with 30-bit vs FP32."""
+    dims, m = (8, 8, 8, 8), 0.005
+    fat, lng = synth.gauge_pair(dims, seed=0)
+    b = synth.spinor(dims, 1000).numpy()
+    sig = synth.shifts_logspaced(12)
+    tols = [1e-12] * 12
+    _, i32, _ = run_ms(ctx, dims, fat, lng, m, b, sig, tols, "f32", "half")
+    _, i30, _ = run_ms(ctx, dims, fat, lng, m, b, sig, tols, "int30", "int20")
+    r32 = np.array(i32.shift_resid_ms[1:12])
+    r30 = np.array(i30.shift_resid_ms[1:12])
+    assert np.median(r32 / r30) > 10
+    assert sum(i30.refine_iters[1:12]) < sum(i32.refine_iters[1:12])
+
+
+def test_single_shift_and_invalid(ctx, orc):
+    dims, m = (8, 8, 8, 8), 0.1
+    fat, lng = synth.gauge_pair(dims, seed=0)
+    b = synth.spinor(dims, 1000).numpy()
+    st, info, xs = run_ms(ctx, dims, fat, lng, m, b, [0.0], [1e-10])
+    assert st == hisq.HISQ_OK
+    assert true_res(orc, dims, fat, lng, m, b, xs[0], 0.0) <= 1e-10
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        run_ms(ctx, dims, fat, lng, m, b, [0.1] * 33, [1e-8] * 33)
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        run_ms(ctx, dims, fat, lng, m, b, [0.1, -1.0], [1e-8, 1e-8])
