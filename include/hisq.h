@@ -22,7 +22,7 @@
  * context's GPU (e.g. a torch tensor's data_ptr()).  The caller keeps
  * ownership of every pointer it passes; the library never frees them.
  *
- * The stencil (the HISQ operator of Sec. 1 and Sec. 4.2, whose form the paper
+ * The stencil (the HISQ operator of Sec. 1 and Sec. 5.2, whose form the paper
  * does not write out; see the design notes for this reading):
  *   (D psi)(x) = sum_mu [ F_mu(x) psi(x+mu) - F_mu(x-mu)^+ psi(x-mu)
  *                       + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^+ psi(x-3mu) ]
@@ -62,12 +62,12 @@ typedef enum {
     HISQ_ENOTFOUND = 8    /* unknown ticket or gauge */
 } hisq_status;
 
-/* Storage format of the gauge field (Sec. 3, the three-precision triplet). */
+/* Storage format of the gauge field (Sec. 4, the three-precision triplet). */
 typedef enum {
     HISQ_GAUGE_F64 = 0,
     HISQ_GAUGE_F32 = 1,
     HISQ_GAUGE_FIX16 = 2, /* 16-bit fixed point, scale = global max (Sec. 2 footnote) */
-    HISQ_GAUGE_FIX32 = 3  /* 32-bit fixed point, scale = global max (Sec. 3) */
+    HISQ_GAUGE_FIX32 = 3  /* 32-bit fixed point, scale = global max (Sec. 4) */
 } hisq_gauge_fmt;
 
 /* Storage format of the fermion (spinor) field. */
@@ -75,11 +75,11 @@ typedef enum {
     HISQ_SPINOR_F64 = 0,    /* 48 B/site */
     HISQ_SPINOR_F32 = 1,    /* 24 B/site */
     HISQ_SPINOR_HALF16 = 2, /* 16 B/site: int16 v[6] + FP32 site max (Sec. 2, Listing 1) */
-    HISQ_SPINOR_INT20 = 3,  /* 16 B/site: 6 x int20 + 8-bit exponent (Sec. 3 Listing 2; Appendix A) */
-    HISQ_SPINOR_INT30 = 4   /* 24 B/site: 6 x int30 + 8-bit exponent (Sec. 3, Listing 3) */
+    HISQ_SPINOR_INT20 = 3,  /* 16 B/site: 6 x int20 + 8-bit exponent (Sec. 4 Listing 2; Appendix A) */
+    HISQ_SPINOR_INT30 = 4   /* 24 B/site: 6 x int30 + 8-bit exponent (Sec. 4, Listing 3) */
 } hisq_spinor_fmt;
 
-/* Arithmetic precision (the third member of the triplet, Sec. 3). */
+/* Arithmetic precision (the third member of the triplet, Sec. 4). */
 typedef enum { HISQ_COMPUTE_F32 = 0, HISQ_COMPUTE_F64 = 1 } hisq_compute_fmt;
 
 /* Precision triplet gauge / fermion / compute plus link compression (Sec. 1:
@@ -118,7 +118,7 @@ HISQ_API const char *hisq_last_error(hisq_ctx *ctx);
 /* Device bytes the context currently holds. */
 HISQ_API size_t hisq_mem_used(hisq_ctx *ctx);
 
-/* Load a gauge configuration (Sec. 2 footnote, Sec. 3: one global scale per
+/* Load a gauge configuration (Sec. 2 footnote, Sec. 4: one global scale per
  * fixed-point field).  fat and lng are FP64 in the host gauge layout
  * (4*V*18 doubles each).  The data are copied: an FP64 copy of each field
  * stays resident for true residuals; reduced formats are built from it on
@@ -135,7 +135,7 @@ HISQ_API void hisq_free_gauge(hisq_ctx *ctx, hisq_gauge *g);
  * fixed-point scale of Sec. 2 footnote. */
 HISQ_API double hisq_gauge_scale(const hisq_gauge *g, int which);
 
-/* One application of the stencil in precision `prec` (Sec. 4.2-4.3: the
+/* One application of the stencil in precision `prec` (Sec. 5.2-5.3: the
  * fields are stored in the reduced formats, unpacked to the compute precision
  * in registers and repacked on store):
  *   out = a * xpay_in - D in      (a != 0)
@@ -208,15 +208,15 @@ typedef struct {
     double mass;          /* m */
     double tol;           /* target |b - A x| / |b| on the FP64 true residual */
     int32_t maxiter;      /* iteration cap (CG iterations; BiCGStab(l): matvecs) */
-    double delta;         /* reliable-update trigger (Sec. 2 footnote: 0.1) */
+    double delta;         /* reliable-update trigger (Sec. 3 footnote: 0.1) */
     hisq_prec sloppy;     /* precision of the iterated vectors and matvecs */
-    hisq_prec refine;     /* multi-shift: precision of the refinement CG (Sec. 2.2) */
-    int32_t nbuf;         /* gradient vectors buffered before x is updated (Sec. 2.1 item 1); 1..16 */
+    hisq_prec refine;     /* multi-shift: precision of the refinement CG (Sec. 3.2) */
+    int32_t nbuf;         /* gradient vectors buffered before x is updated (Sec. 3.1 item 1); 1..16 */
     int32_t use_init_guess; /* x holds the initial guess */
     int32_t on_device;    /* b and x are device pointers */
-    int32_t pr_beta;      /* 1: Polak-Ribiere beta (Sec. 2.1 item 3), 0: Fletcher-Reeves */
-    int32_t reproject;    /* 1: re-project p at each reliable update (Sec. 2.1 item 2) */
-    int32_t l;            /* BiCGStab(l): l (Sec. 5.1 uses 4), 1..8 */
+    int32_t pr_beta;      /* 1: Polak-Ribiere beta (Sec. 3.1 item 3), 0: Fletcher-Reeves */
+    int32_t reproject;    /* 1: re-project p at each reliable update (Sec. 3.1 item 2) */
+    int32_t l;            /* BiCGStab(l): l (Sec. 6.1 uses 4), 1..8 */
     int32_t use_graph;    /* 1: replay each block of iterations as a CUDA graph */
     void *stream;         /* cudaStream_t; NULL: the context's stream */
 } hisq_solver_params;
@@ -242,7 +242,7 @@ typedef struct {
     int32_t refine_iters[HISQ_MAX_SHIFTS];   /* refinement CG iterations of shift i */
 } hisq_solve_info;
 
-/* Even/odd CG (Sec. 2.1): solves (4m^2 - D_eo D_oe) x = b on the even sites
+/* Even/odd CG (Sec. 3.1): solves (4m^2 - D_eo D_oe) x = b on the even sites
  * with the sloppy triplet for the iterated residual and gradient vectors,
  * FP64 for x (accumulated from nbuf buffered gradient vectors), reliable
  * updates with an FP64 true residual whenever |r| drops below delta times its
@@ -253,7 +253,7 @@ typedef struct {
 HISQ_API hisq_status hisq_cg(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
                     double *x, hisq_solve_info *info);
 
-/* Multi-shift CG (Sec. 2.2): solves (M_ee + sigma_i) x_i = b for nshift
+/* Multi-shift CG (Sec. 3.2): solves (M_ee + sigma_i) x_i = b for nshift
  * shifts (<= HISQ_MAX_SHIFTS) in the sloppy precision with reliable updates on
  * the base (smallest) shift; shift i freezes when its iterated residual
  * reaches tol[i] or the sloppy format's precision floor; then refinement CG in
@@ -263,7 +263,7 @@ HISQ_API hisq_status hisq_multishift_cg(hisq_ctx *ctx, const hisq_gauge *g, cons
                                const double *sigma, const double *tol, const double *b, double *const *x,
                                hisq_solve_info *info);
 
-/* BiCGStab(l) (Sec. 5.1) on the full-lattice M = 2m + D with sloppy vectors,
+/* BiCGStab(l) (Sec. 6.1) on the full-lattice M = 2m + D with sloppy vectors,
  * FP64 x and a reliable update at the end of a cycle when triggered. */
 HISQ_API hisq_status hisq_bicgstabl(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
                            double *x, hisq_solve_info *info);

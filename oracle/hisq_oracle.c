@@ -16,7 +16,7 @@
  *   spinor : double [cb][color][re,im] on one parity (Vh = V/2 sites);
  *            full lattice = [parity][cb][color][re,im], even first.
  *
- * The stencil (the HISQ operator, named in Sec. 1 and Sec. 4.2 but never
+ * The stencil (the HISQ operator, named in Sec. 1 and Sec. 5.2 but never
  * written out) is read as
  *   (D psi)(x) = sum_mu [ F_mu(x) psi(x+mu) - F_mu(x-mu)^+ psi(x-mu)
  *                       + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^+ psi(x-3mu) ]
@@ -284,7 +284,7 @@ void or_half_unpack(int64_t n, const unsigned char *rec, float *v)
     }
 }
 
-/* 20-bit shared-exponent format (Sec. 3, Listing 2; the codec of Appendix A,
+/* 20-bit shared-exponent format (Sec. 4, Listing 2; the codec of Appendix A,
  * Listing 4).  Per site: six 20-bit two's-complement integers and an 8-bit
  * exponent in four 32-bit words.  Steps of the appendix:
  *   max  = largest |component| (FP32; the garbled vector initialisation of
@@ -358,7 +358,7 @@ void or_int20_unpack(int64_t n, const uint32_t *w, float *v)
     }
 }
 
-/* 30-bit shared-exponent format (Sec. 3, Listing 3; no layout is given, so
+/* 30-bit shared-exponent format (Sec. 4, Listing 3; no layout is given, so
  * this is our reading): six 32-bit words; bits 0..29 of word k hold the 30-bit
  * two's-complement integer q_k; bits 30..31 of words 0..3 hold bits 2k..2k+1
  * of the 8-bit exponent E; the top bits of words 4, 5 are zero.  The exponent
@@ -415,7 +415,7 @@ void or_int30_unpack(int64_t n, const uint32_t *w, double *v)
     }
 }
 
-/* Fixed-point gauge (Sec. 2 and its footnote on smeared fields; Sec. 3 for the
+/* Fixed-point gauge (Sec. 2 and its footnote on smeared fields; Sec. 4 for the
  * 32-bit variant): one scale per field set by the global max |element|;
  * q = rint(x * (qmax / gmax)) in FP64, clamped to [-qmax, qmax],
  * qmax = 2^15-1 (16-bit) or 2^31-1 (32-bit). */
@@ -621,7 +621,7 @@ int or_cg(const int *L, const double *fat, const double *lng, double m, double s
 }
 
 /* ------------------------------------------------------------------------ */
-/* O7 multi-shift CG (Sec. 2.2; Jegerlehner, hep-lat/9612014), FP64          */
+/* O7 multi-shift CG (Sec. 3.2; Jegerlehner, hep-lat/9612014), FP64          */
 /* ------------------------------------------------------------------------ */
 /* Solves (M_ee + sigma_i) x_i = b for i < nshift with sigma_0 the base shift.
  * With A = M_ee + sigma_0 and s_i = sigma_i - sigma_0 the shifted residuals
@@ -708,7 +708,7 @@ int or_multishift_cg(const int *L, const double *fat, const double *lng, double 
 }
 
 /* ------------------------------------------------------------------------ */
-/* O8 BiCGStab(l) (Sec. 5.1; Sleijpen and Fokkema 1993), FP64                */
+/* O8 BiCGStab(l) (Sec. 6.1; Sleijpen and Fokkema 1993), FP64                */
 /* ------------------------------------------------------------------------ */
 /* Solves (2m + D) x = b on the full lattice from x = 0 with shadow residual
  * r~ = r_0.  Each cycle takes l BiCG steps and then minimises the residual

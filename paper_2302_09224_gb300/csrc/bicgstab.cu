@@ -1,4 +1,4 @@
-// bicgstab.cu -- mixed-precision BiCGStab(l) (Sec. 5.1; Sleijpen and Fokkema)
+// bicgstab.cu -- mixed-precision BiCGStab(l) (Sec. 6.1; Sleijpen and Fokkema)
 // on the full-lattice operator M = 2m + D, and its C-ABI entry point.
 //
 // Each cycle: l BiCG steps (two matvecs each) followed by a minimal-residual
@@ -544,6 +544,8 @@ struct BRun {
         if (!e) e = ws.alloc(sizeof(BState), (void **)&b);
         if (e) return e;
         if (cudaMallocHost(&bh, sizeof(BState)) != cudaSuccess) return fail(c, HISQ_ENOMEM, "pinned host state");
+        tune_stencil(c, g->geom, p.sloppy, gv_s, U, R, st);
+        tune_stencil(c, g->geom, prec_f64(), gv_d, (char *)ax64, (char *)r64, st);
         cudaMemsetAsync(U, 0, fb * (l + 1), st);
         cudaMemsetAsync(R, 0, fb * (l + 1), st);
         // |b|^2 over both halves

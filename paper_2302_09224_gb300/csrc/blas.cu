@@ -1,5 +1,5 @@
 // blas.cu -- fused BLAS-1 kernels of the stabilised mixed-precision CG
-// (Sec. 2.1), each a single pass over its vectors in the sloppy storage
+// (Sec. 3.1), each a single pass over its vectors in the sloppy storage
 // format with the reduction it needs fused in (deterministic, FP64):
 //   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta)
 //   p_update      p' <- r + beta p       (into the next ring slot)
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
     if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) {
         if (a.fin)
             run_finisher(a.fin, tot, a.fst, a.slot);
-        else
+        else if (a.st)
             run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
     }
 }
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBlock) true_residual_kernel(BlasArgs a)
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) {
         if (a.fin)
             run_finisher(a.fin, tot, a.fst, a.slot);
-        else
+        else if (a.st)
             run_finisher(FIN_CG_TRUE, tot, a.st, a.slot);
     }
 }

@@ -1,10 +1,10 @@
-// cg.cu -- the stabilised mixed-precision even/odd CG of Sec. 2.1 and its C-ABI
+// cg.cu -- the stabilised mixed-precision even/odd CG of Sec. 3.1 and its C-ABI
 // entry point.
 //
 // Sloppy precision (the triplet's formats): iterated residual r, gradient
 // vectors p (a ring of nbuf slots) and the operator applications.  FP64: the
 // solution x_hi, the right-hand side, every true residual and all reductions.
-//   * reliable updates (Sec. 2, footnote): when |r| drops below delta times
+//   * reliable updates (Sec. 3, footnote): when |r| drops below delta times
 //     its maximum since the last update, x_hi is brought up to date, the true
 //     residual b - A x_hi is computed in FP64 and replaces r;
 //   * item 1: x_hi += sum_j alpha_j p_j once per nbuf iterations (and at each
@@ -92,6 +92,23 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
     }
 }
 
+void tune_stencil(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, char *zero_in, char *out,
+                  cudaStream_t s)
+{
+    if (c->capturing || stream_capturing(s)) return;
+    cudaMemsetAsync(zero_in, 0, spinor_field_bytes(p.spinor, geom.vh), s);
+    DslashArgs d{};
+    d.g = geom;
+    d.gv = gv;
+    d.err = c->err_flag;
+    d.red = c->red;
+    d.out_parity = 1;
+    d.in = zero_in;
+    d.out = out;
+    d.sign = 1;
+    tune_dslash(p.gauge, p.spinor, p.compute, p.long_recon, d, s);
+}
+
 namespace {
 
 struct CGRun {
@@ -151,6 +168,8 @@ struct CGRun {
             return fail(c, HISQ_ENOMEM, "pinned host state");
         cudaMemsetAsync(ring, 0, sb * cfg.nbuf, s);
         diag = 4.0 * cfg.mass * cfg.mass + cfg.sigma;
+        tune_stencil(c, g->geom, cfg.sloppy, gv_s, ap_s, tmp_s, s);
+        tune_stencil(c, g->geom, prec_f64(), gv_d, (char *)ax64, (char *)tmp64, s);
         return HISQ_OK;
     }
 

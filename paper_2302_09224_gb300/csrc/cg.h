@@ -39,6 +39,10 @@ struct CGConfig {
 void launch_convert(int si, int so, int n, const char *in, char *out, int *err, cudaStream_t s);
 
 hisq_prec prec_f64();
+// Tune the stencil's launch shape for this triplet and lattice (zeroes zero_in,
+// overwrites out); a no-op during stream capture or once tuned.
+void tune_stencil(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, char *zero_in, char *out,
+                  cudaStream_t s);
 double stencil_bytes(const hisq_prec &p, int vh, bool xpay);
 
 void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,

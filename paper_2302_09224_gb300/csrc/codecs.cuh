@@ -1,5 +1,5 @@
 // codecs.cuh -- device-side storage formats: every kernel reads a site or link
-// through these and converts to the compute precision in registers (Sec. 4.1:
+// through these and converts to the compute precision in registers (Sec. 5.1:
 // the format is a property of the accessor, not of the computation).
 //
 // Spinor formats (one half-lattice field of n sites; planar layout: 16-byte
@@ -8,7 +8,7 @@
 //   F32    16 + 8 B        (c0, c1) | (c2)
 //   HALF   16 B            int16 q[6] | FP32 site max  (Sec. 2, Listing 1)
 //   INT20  16 B            four words of the Appendix A bitfield layout
-//   INT30  16 + 8 B        words 0..3 | words 4..5 (Sec. 3, Listing 3; our layout)
+//   INT30  16 + 8 B        words 0..3 | words 4..5 (Sec. 4, Listing 3; our layout)
 // Link formats ([plane][parity][mu][Vh]; reals row-major, first 12 for r12):
 //   F64 16 B = 1 complex, F32 16 B = 2 complex, FIX16 16 B = 8 int16,
 //   FIX32 16 B = 4 int32; leftover reals go to a 4- or 8-byte tail plane.
@@ -49,6 +49,24 @@ __device__ __forceinline__ T ld_cached(const T *p)
 // FP32 helpers that must not be contracted (codec arithmetic is specified
 // step by step and is bit-exact with the CPU definition).
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+
+// Exact integer -> float conversions on the FP32 and integer pipes instead of
+// the (quarter-rate) conversion pipe: a b-bit two's-complement field u, offset
+// by 2^(b-1), is placed in the mantissa of 2^23 (b <= 23) and the offset is
+// subtracted; both operands are integers below 2^24, so the subtraction is
+// exact and the result equals (float)q.
+__device__ __forceinline__ float i16lo_to_f(uint32_t w)
+{
+    return __fsub_rn(__uint_as_float((w & 0xffffu) ^ 0x4B008000u), 8421376.0f);  // 2^23 + 2^15
+}
+__device__ __forceinline__ float i16hi_to_f(uint32_t w)
+{
+    return __fsub_rn(__uint_as_float((w >> 16) ^ 0x4B008000u), 8421376.0f);
+}
+__device__ __forceinline__ float i20_to_f(uint32_t u)
+{
+    return __fsub_rn(__uint_as_float((u & 0xfffffu) ^ 0x4B080000u), 8912896.0f);  // 2^23 + 2^19
+}
 
 // ---------------------------------------------------------------------------
 // spinor codecs
@@ -116,12 +134,12 @@ struct Spinor<S_HALF> {
     template <typename real>
     __device__ static void load(const char *b, int n, int i, real v[6])
     {
-        const int4 r = ld_cached(reinterpret_cast<const int4 *>(b) + i);
-        const float scale = fmul(__int_as_float(r.w), 1.0f / 32767.0f);
-        const int q[6] = {(int)(short)(r.x & 0xffff), r.x >> 16, (int)(short)(r.y & 0xffff),
-                          r.y >> 16, (int)(short)(r.z & 0xffff), r.z >> 16};
+        const uint4 r = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        const float scale = fmul(__uint_as_float(r.w), 1.0f / 32767.0f);
+        const float q[6] = {i16lo_to_f(r.x), i16hi_to_f(r.x), i16lo_to_f(r.y),
+                            i16hi_to_f(r.y), i16lo_to_f(r.z), i16hi_to_f(r.z)};
 #pragma unroll
-        for (int k = 0; k < 6; k++) v[k] = (real)fmul((float)q[k], scale);
+        for (int k = 0; k < 6; k++) v[k] = (real)fmul(q[k], scale);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -164,14 +182,14 @@ struct Spinor<S_INT20> {
         (void)n;
         const uint4 w = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
         const float up = __uint_as_float((w.w >> 24) << 23);
-        const uint32_t u[6] = {w.x & 0xfffffu,
+        const uint32_t u[6] = {w.x,
                                ((w.x >> 20) << 8) | (w.y & 0xffu),
-                               (w.y >> 8) & 0xfffffu,
+                               w.y >> 8,
                                ((w.y >> 28) << 16) | (w.z & 0xffffu),
                                ((w.z >> 16) << 4) | (w.w & 0xfu),
-                               (w.w >> 4) & 0xfffffu};
+                               w.w >> 4};
 #pragma unroll
-        for (int k = 0; k < 6; k++) v[k] = (real)fmul((float)sext_bits(u[k], 20), up);
+        for (int k = 0; k < 6; k++) v[k] = (real)fmul(i20_to_f(u[k]), up);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -289,6 +307,14 @@ __device__ __forceinline__ void rebuild_row2(real U[18], real sign)
 #undef IM
 }
 
+// Fixed-point links are returned unscaled: the integers q as exact reals.
+// Their scale gmax/qmax is one number per field, so the stencil multiplies
+// each field's accumulated sum by it once instead of every element.
+template <int GF>
+struct LinkScaled {
+    static constexpr bool value = GF == G_FIX16 || GF == G_FIX32;
+};
+
 template <int GF, int RECON>
 struct Link {
     static constexpr int n16 = link_n16(GF, RECON);
@@ -296,7 +322,7 @@ struct Link {
 
     // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16)
     template <typename real>
-    __device__ static void load(const char *base, size_t pstride, int li, real U[18], float sf, double sd)
+    __device__ static void load(const char *base, size_t pstride, int li, real U[18])
     {
         if constexpr (GF == G_F64) {
 #pragma unroll
@@ -316,34 +342,27 @@ struct Link {
                 U[4 * n16] = d.x; U[4 * n16 + 1] = d.y;
             }
         } else if constexpr (GF == G_FIX16) {
-            int q[RECON];
+            uint32_t w[RECON / 2];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
-                const int4 d = ld_stream(reinterpret_cast<const int4 *>(base + k * pstride) + li);
-                const int w[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    q[8 * k + 2 * j] = (int)(short)(w[j] & 0xffff);
-                    q[8 * k + 2 * j + 1] = w[j] >> 16;
-                }
+                const uint4 d = ld_stream(reinterpret_cast<const uint4 *>(base + k * pstride) + li);
+                w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
             }
             if constexpr (tail == 4) {
-                const int d = ld_stream(reinterpret_cast<const int *>(base + n16 * pstride) + li);
-                q[8 * n16] = (int)(short)(d & 0xffff);
-                q[8 * n16 + 1] = d >> 16;
+                w[4 * n16] = ld_stream(reinterpret_cast<const unsigned int *>(base + n16 * pstride) + li);
             } else if constexpr (tail == 8) {
-                const int2 d = ld_stream(reinterpret_cast<const int2 *>(base + n16 * pstride) + li);
-                q[8 * n16] = (int)(short)(d.x & 0xffff);
-                q[8 * n16 + 1] = d.x >> 16;
-                q[8 * n16 + 2] = (int)(short)(d.y & 0xffff);
-                q[8 * n16 + 3] = d.y >> 16;
+                const uint2 d = ld_stream(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
+                w[4 * n16] = d.x; w[4 * n16 + 1] = d.y;
             }
 #pragma unroll
-            for (int k = 0; k < RECON; k++) {
-                if constexpr (sizeof(real) == 8)
-                    U[k] = (double)q[k] * sd;
-                else
-                    U[k] = (float)q[k] * sf;
+            for (int k = 0; k < RECON / 2; k++) {
+                if constexpr (sizeof(real) == 8) {
+                    U[2 * k] = (double)(int)(short)(w[k] & 0xffffu);
+                    U[2 * k + 1] = (double)((int)w[k] >> 16);
+                } else {
+                    U[2 * k] = i16lo_to_f(w[k]);
+                    U[2 * k + 1] = i16hi_to_f(w[k]);
+                }
             }
         } else {  // G_FIX32
             int q[RECON];
@@ -359,9 +378,9 @@ struct Link {
 #pragma unroll
             for (int k = 0; k < RECON; k++) {
                 if constexpr (sizeof(real) == 8)
-                    U[k] = (double)q[k] * sd;
+                    U[k] = (double)q[k];
                 else
-                    U[k] = __int2float_rn(q[k]) * sf;
+                    U[k] = __int2float_rn(q[k]);
             }
         }
     }

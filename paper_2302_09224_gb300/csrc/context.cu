@@ -449,6 +449,18 @@ hisq_status hisq_dslash(hisq_ctx *c, const hisq_gauge *gc, hisq_prec prec, int o
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash pack");
     if (bad_in) return fail(c, HISQ_EINVAL, "non-finite input spinor");
+    {
+        DslashArgs td{};
+        td.g = g->geom;
+        td.gv = gv;
+        td.err = c->err_flag;
+        td.red = c->red;
+        td.out_parity = 0;
+        td.in = in_s;
+        td.out = out_s;
+        td.sign = 1;
+        if (!stream_capturing(s)) tune_dslash(prec.gauge, prec.spinor, prec.compute, prec.long_recon, td, s);
+    }
     const double link_b = 8.0 * link_bytes(prec.gauge, prec.fat_recon) + 8.0 * link_bytes(prec.gauge, prec.long_recon);
     const double site_b = spinor_site_bytes(prec.spinor);
     for (int h = 0; h < nhalf; h++) {

@@ -104,7 +104,7 @@ __global__ void r12_check_kernel(Geom g, const double *links, int k, double *out
 
 // FP64 [mu][lex][18] -> stored copy [plane][parity][mu][Vh] in format GF with
 // RECON reals per link.  Fixed point: q = rint(x * inv) clamped to +-qmax,
-// inv = qmax / global max (Sec. 2 footnote; Sec. 3 for 32 bits).
+// inv = qmax / global max (Sec. 2 footnote; Sec. 4 for 32 bits).
 template <int GF, int RECON>
 __global__ void quantise_kernel(Geom g, const double *links, double inv, char *out)
 {

@@ -1,6 +1,6 @@
 // dslash.cuh -- the HISQ staggered stencil pass (the dominant kernel of every
-// solver; Sec. 1 and Sec. 4.3), templated on the storage formats of the gauge
-// and spinor fields and on the compute precision (Sec. 3: the triplet).
+// solver; Sec. 1 and Sec. 5.3), templated on the storage formats of the gauge
+// and spinor fields and on the compute precision (Sec. 4: the triplet).
 //
 // One thread per output site x of parity p:
 //   out(x) = a*y(x) + sign * sum_mu [ F_mu(x) in(x+mu) - F_mu(x-mu)^+ in(x-mu)
@@ -21,8 +21,6 @@
 #include "reduce.cuh"
 
 namespace hisq {
-
-constexpr int kDslashBlock = 128;
 
 __device__ __forceinline__ int wrap_coord(int c, int L)
 {
@@ -61,8 +59,19 @@ __device__ __forceinline__ void mv_adj_sub(real acc[6], const real U[18], const 
         }
 }
 
-template <int GF, int SF, typename real, int LREC, bool RED>
-__global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a)
+// Launch shapes tried by the tuner: threads per block and the minimum number
+// of resident blocks per SM asked of the register allocator (trading loads in
+// flight per thread against warps per SM): 128/1 (no cap), 128/6 (<= 85
+// registers), 128/8 (<= 64), 256/4 (<= 64), 64/16 (<= 64).
+constexpr int kNumStencilConfigs = 5;
+__host__ __device__ constexpr int stencil_block(int cfg) { return cfg == 3 ? 256 : cfg == 4 ? 64 : 128; }
+__host__ __device__ constexpr int stencil_minb(int cfg)
+{
+    return cfg == 1 ? 6 : cfg == 2 ? 8 : cfg == 3 ? 4 : cfg == 4 ? 16 : 1;
+}
+
+template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
+__global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG)) dslash_kernel(const DslashArgs a)
 {
     if (a.active != nullptr && *(volatile const int *)a.active == 0) return;  // uniform over the grid
     const Geom &g = a.g;
@@ -71,6 +80,10 @@ __global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a
     const int po = a.out_parity, pi = 1 - po;
     const size_t pstride = (size_t)8 * vh * 16;
     double rv[2] = {0.0, 0.0};
+    constexpr bool kScaled = LinkScaled<GF>::value;
+    // fixed-point links are accumulated unscaled, one sum per field
+    const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.fat_scale_d : (real)a.gv.fat_scale_f) : real(1);
+    const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
 
     if (cb < vh) {
         int r = cb / g.xh;
@@ -82,7 +95,8 @@ __global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a
         const int x = 2 * xh + ((y + z + t + po) & 1);
         const int c[4] = {x, y, z, t};
         const int lex = 2 * cb + (x & 1);
-        real acc[6] = {0, 0, 0, 0, 0, 0};
+        real accf[6] = {0, 0, 0, 0, 0, 0};
+        real accl[6] = {0, 0, 0, 0, 0, 0};
         int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
 
 #pragma unroll
@@ -95,41 +109,39 @@ __global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a
             const int np3 = (base + cp3 * st) >> 1, nm3 = (base + cm3 * st) >> 1;
             real U[18], s[6];
 
-            Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U, a.gv.fat_scale_f,
-                               a.gv.fat_scale_d);
+            Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
             Spinor<SF>::load(a.in, vh, np1, s);
-            mv_add(acc, U, s);
+            mv_add(accf, U, s);
 
-            Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U, a.gv.fat_scale_f,
-                               a.gv.fat_scale_d);
+            Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
             Spinor<SF>::load(a.in, vh, nm1, s);
-            mv_adj_sub(acc, U, s);
+            mv_adj_sub(accf, U, s);
 
-            const real eta = (phase_sum & 1) ? real(-1) : real(1);
-            const size_t lps = (size_t)8 * vh * 16;
-            Link<GF, LREC>::load(a.gv.lng, lps, (po * 4 + mu) * vh + cb, U, a.gv.lng_scale_f, a.gv.lng_scale_d);
+            // row 2 of an r12 link in the units of the accumulated sum: sign * lsc * conj(row0 x row1)
+            const real eta = (phase_sum & 1) ? -lsc : lsc;
+            Link<GF, LREC>::load(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
             if constexpr (LREC == 12) {
                 const bool flip = g.antiperiodic_t && mu == 3 && c[3] + 3 >= L;
                 rebuild_row2(U, flip ? -eta : eta);
             }
             Spinor<SF>::load(a.in, vh, np3, s);
-            mv_add(acc, U, s);
+            mv_add(accl, U, s);
 
-            Link<GF, LREC>::load(a.gv.lng, lps, (pi * 4 + mu) * vh + nm3, U, a.gv.lng_scale_f, a.gv.lng_scale_d);
+            Link<GF, LREC>::load(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
             if constexpr (LREC == 12) {
                 const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
                 rebuild_row2(U, flip ? -eta : eta);
             }
             Spinor<SF>::load(a.in, vh, nm3, s);
-            mv_adj_sub(acc, U, s);
+            mv_adj_sub(accl, U, s);
 
             phase_sum += c[mu];
         }
 
-        const real sgn = (real)a.sign;
+        const real sf = (real)a.sign * fsc, sl = (real)a.sign * lsc;
         real o[6];
 #pragma unroll
-        for (int k = 0; k < 6; k++) o[k] = sgn * acc[k];
+        for (int k = 0; k < 6; k++) o[k] = sf * accf[k] + sl * accl[k];
         if (a.xpay) {
             real yv[6];
             Spinor<SF>::load(a.y, vh, cb, yv);
@@ -154,20 +166,38 @@ __global__ void __launch_bounds__(kDslashBlock) dslash_kernel(const DslashArgs a
     }
 }
 
-template <int GF, int SF, typename real>
-bool launch_dslash_t(int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
+template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
+void launch_cfg(const DslashArgs &a, cudaStream_t s)
 {
-    const int nblk = (a.g.vh + kDslashBlock - 1) / kDslashBlock;
+    constexpr int B = stencil_block(CFG);
+    dslash_kernel<GF, SF, real, LREC, RED, CFG><<<(a.g.vh + B - 1) / B, B, 0, s>>>(a);
+}
+
+template <int GF, int SF, typename real, int LREC, bool RED>
+void launch_any(int cfg, const DslashArgs &a, cudaStream_t s)
+{
+    switch (cfg) {
+    case 1: launch_cfg<GF, SF, real, LREC, RED, 1>(a, s); break;
+    case 2: launch_cfg<GF, SF, real, LREC, RED, 2>(a, s); break;
+    case 3: launch_cfg<GF, SF, real, LREC, RED, 3>(a, s); break;
+    case 4: launch_cfg<GF, SF, real, LREC, RED, 4>(a, s); break;
+    default: launch_cfg<GF, SF, real, LREC, RED, 0>(a, s); break;
+    }
+}
+
+template <int GF, int SF, typename real>
+bool launch_dslash_t(int long_recon, bool reduce, int cfg, const DslashArgs &a, cudaStream_t s)
+{
     if (long_recon == 12) {
         if (reduce)
-            dslash_kernel<GF, SF, real, 12, true><<<nblk, kDslashBlock, 0, s>>>(a);
+            launch_any<GF, SF, real, 12, true>(cfg, a, s);
         else
-            dslash_kernel<GF, SF, real, 12, false><<<nblk, kDslashBlock, 0, s>>>(a);
+            launch_any<GF, SF, real, 12, false>(cfg, a, s);
     } else {
         if (reduce)
-            dslash_kernel<GF, SF, real, 18, true><<<nblk, kDslashBlock, 0, s>>>(a);
+            launch_any<GF, SF, real, 18, true>(cfg, a, s);
         else
-            dslash_kernel<GF, SF, real, 18, false><<<nblk, kDslashBlock, 0, s>>>(a);
+            launch_any<GF, SF, real, 18, false>(cfg, a, s);
     }
     return true;
 }

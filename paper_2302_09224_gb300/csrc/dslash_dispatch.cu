@@ -1,26 +1,118 @@
-// Dispatch from a runtime precision triplet to the compiled stencil kernels.
+// Dispatch from a runtime precision triplet to the compiled stencil kernels,
+// and the launch-shape tuner: the first time a (triplet, lattice) pair is
+// prepared outside graph capture every launch shape is timed on the device and
+// the fastest is kept for the rest of the process.
+#include <cuda_runtime.h>
+
+#include <array>
+#include <map>
+#include <mutex>
+
+#include "dslash.cuh"
 #include "internal.h"
 
 namespace hisq {
 
-bool launch_dslash_f64(int, bool, const DslashArgs &, cudaStream_t);
-bool launch_dslash_f32(int, bool, const DslashArgs &, cudaStream_t);
-bool launch_dslash_half(int, bool, const DslashArgs &, cudaStream_t);
-bool launch_dslash_int20(int, bool, const DslashArgs &, cudaStream_t);
-bool launch_dslash_int30d(int, bool, const DslashArgs &, cudaStream_t);
-bool launch_dslash_int30f(int, bool, const DslashArgs &, cudaStream_t);
+bool launch_dslash_f64(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_f32(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_half(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_int20(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_int30d(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_int30f(int, bool, int, const DslashArgs &, cudaStream_t);
+
+namespace {
+
+bool launch_with(int gf, int sf, int cf, int lrec, bool red, int cfg, const DslashArgs &a, cudaStream_t s)
+{
+    const bool f64 = cf == HISQ_COMPUTE_F64;
+    if (gf == G_F64 && sf == S_F64 && f64) return launch_dslash_f64(lrec, red, cfg, a, s);
+    if (gf == G_F32 && sf == S_F32 && !f64) return launch_dslash_f32(lrec, red, cfg, a, s);
+    if (gf == G_FIX16 && sf == S_HALF && !f64) return launch_dslash_half(lrec, red, cfg, a, s);
+    if (gf == G_FIX16 && sf == S_INT20 && !f64) return launch_dslash_int20(lrec, red, cfg, a, s);
+    if (gf == G_FIX32 && sf == S_INT30) {
+        if (f64) return launch_dslash_int30d(lrec, red, cfg, a, s);
+        return launch_dslash_int30f(lrec, red, cfg, a, s);
+    }
+    return false;
+}
+
+using TuneKey = std::array<int, 8>;
+std::mutex tune_mu;
+std::map<TuneKey, int> tune_cache;
+
+TuneKey key_of(int gf, int sf, int cf, int lrec, const Geom &g)
+{
+    return {gf, sf, cf, lrec, g.L[0], g.L[1], g.L[2], g.L[3]};
+}
+
+}  // namespace
+
+int stencil_config(int gf, int sf, int cf, int lrec, const Geom &g)
+{
+    std::lock_guard<std::mutex> lk(tune_mu);
+    auto it = tune_cache.find(key_of(gf, sf, cf, lrec, g));
+    return it == tune_cache.end() ? 0 : it->second;
+}
 
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
 {
-    const bool f64 = cf == HISQ_COMPUTE_F64;
-    if (gf == G_F64 && sf == S_F64 && f64) return launch_dslash_f64(long_recon, reduce, a, s);
-    if (gf == G_F32 && sf == S_F32 && !f64) return launch_dslash_f32(long_recon, reduce, a, s);
-    if (gf == G_FIX16 && sf == S_HALF && !f64) return launch_dslash_half(long_recon, reduce, a, s);
-    if (gf == G_FIX16 && sf == S_INT20 && !f64) return launch_dslash_int20(long_recon, reduce, a, s);
-    if (gf == G_FIX32 && sf == S_INT30) {
-        if (f64) return launch_dslash_int30d(long_recon, reduce, a, s);
-        return launch_dslash_int30f(long_recon, reduce, a, s);
+    return launch_with(gf, sf, cf, long_recon, reduce, stencil_config(gf, sf, cf, long_recon, a.g), a, s);
+}
+
+void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaStream_t s)
+{
+    const TuneKey key = key_of(gf, sf, cf, lrec, args.g);
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        if (tune_cache.count(key)) return;
     }
+    DslashArgs a = args;  // a plain pass: no finisher, no skip flag
+    a.fin = FIN_NONE;
+    a.active = nullptr;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int cfg = 0; cfg < kNumStencilConfigs; cfg++) {
+        launch_with(gf, sf, cf, lrec, false, cfg, a, s);  // warm
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; r++) launch_with(gf, sf, cf, lrec, false, cfg, a, s);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    std::lock_guard<std::mutex> lk(tune_mu);
+    tune_cache[key] = best;
+}
+
+}  // namespace hisq
+
+namespace hisq {
+
+bool launch_mrhs_f32(int, bool, int, const DslashMArgs &, cudaStream_t);
+bool launch_mrhs_half(int, bool, int, const DslashMArgs &, cudaStream_t);
+bool launch_mrhs_int20(int, bool, int, const DslashMArgs &, cudaStream_t);
+
+bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, const DslashMArgs &a,
+                        cudaStream_t s)
+{
+    if (T != 1 && T != 2 && T != 4 && T != 8 && T != 16) return false;
+    if (a.nrhs < 1 || a.nrhs > kMaxRHS || a.nrhs % T) return false;
+    if (cf != HISQ_COMPUTE_F32) return false;
+    if (gf == G_F32 && sf == S_F32) return launch_mrhs_f32(long_recon, reduce, T, a, s);
+    if (gf == G_FIX16 && sf == S_HALF) return launch_mrhs_half(long_recon, reduce, T, a, s);
+    if (gf == G_FIX16 && sf == S_INT20) return launch_mrhs_int20(long_recon, reduce, T, a, s);
     return false;
 }
 

@@ -1,0 +1,173 @@
+// dslash_mrhs.cuh -- the stencil applied to a tile of T right-hand sides at
+// once (Sec. 1, block solvers: the link traffic is shared by the tile, which
+// turns the matrix-vector stencil into a matrix-matrix one and raises its
+// arithmetic intensity T-fold).
+//
+// One thread per output site and tile: each of the 16 links is loaded once
+// (scaled to its true value, since that cost is now shared by T products) and
+// applied to the T neighbour spinors.  Right-hand side t of the tile lives in
+// the field at in + (t0 + t) * field_bytes.  Per right-hand side: its own xpay
+// coefficient and, when reducing, Re<y_t, out_t> and |out_t|^2, whose totals
+// drive the batched solver's per-RHS scalar recurrences.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "codecs.cuh"
+#include "dslash.cuh"
+#include "finish.cuh"
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace hisq {
+
+constexpr int kMrhsBlock = 128;
+
+template <int GF, int RECON, typename real>
+__device__ __forceinline__ void load_link_scaled(const char *base, size_t pstride, int li, real U[18], real scale,
+                                                 real sign12)
+{
+    Link<GF, RECON>::load(base, pstride, li, U);
+    if constexpr (LinkScaled<GF>::value) {
+#pragma unroll
+        for (int k = 0; k < RECON; k++) U[k] *= scale;
+    }
+    if constexpr (RECON == 12) rebuild_row2(U, sign12);
+}
+
+template <int GF, int SF, typename real, int LREC, int T, bool RED>
+__global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMArgs a)
+{
+    if (a.active_any != nullptr && *(volatile const int *)a.active_any == 0) return;
+    const Geom &g = a.g;
+    const int vh = g.vh;
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    const int po = a.out_parity, pi = 1 - po;
+    const size_t pstride = (size_t)8 * vh * 16;
+    constexpr bool kScaled = LinkScaled<GF>::value;
+    const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.fat_scale_d : (real)a.gv.fat_scale_f) : real(1);
+    const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
+    double rv[2 * T];
+#pragma unroll
+    for (int k = 0; k < 2 * T; k++) rv[k] = 0.0;
+
+    if (cb < vh) {
+        int r = cb / g.xh;
+        const int xh = cb - r * g.xh;
+        const int y = r % g.L[1];
+        r /= g.L[1];
+        const int z = r % g.L[2];
+        const int t = r / g.L[2];
+        const int x = 2 * xh + ((y + z + t + po) & 1);
+        const int c[4] = {x, y, z, t};
+        const int lex = 2 * cb + (x & 1);
+        real acc[T][6];
+#pragma unroll
+        for (int j = 0; j < T; j++)
+#pragma unroll
+            for (int k = 0; k < 6; k++) acc[j][k] = 0;
+        int phase_sum = 0;
+
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int L = g.L[mu], st = g.stride[mu];
+            const int cp1 = wrap_coord(c[mu] + 1, L), cm1 = wrap_coord(c[mu] - 1, L);
+            const int cp3 = wrap_coord(c[mu] + 3, L), cm3 = wrap_coord(c[mu] - 3, L);
+            const int base = lex - c[mu] * st;
+            const int nb[4] = {(base + cp1 * st) >> 1, (base + cm1 * st) >> 1, (base + cp3 * st) >> 1,
+                               (base + cm3 * st) >> 1};
+            const real eta = (phase_sum & 1) ? real(-1) : real(1);
+            const bool flip_f = g.antiperiodic_t && mu == 3 && c[3] + 3 >= L;
+            const bool flip_b = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
+#pragma unroll
+            for (int term = 0; term < 4; term++) {
+                real U[18];
+                const bool fwd = term == 0 || term == 2;
+                const int li = ((fwd ? po : pi) * 4 + mu) * vh + (fwd ? cb : nb[term]);
+                if (term < 2)
+                    load_link_scaled<GF, 18>(a.gv.fat, pstride, li, U, fsc, real(1));
+                else
+                    load_link_scaled<GF, LREC>(a.gv.lng, pstride, li, U, lsc,
+                                               ((term == 2 ? flip_f : flip_b) ? -eta : eta));
+#pragma unroll
+                for (int j = 0; j < T; j++) {
+                    real s[6];
+                    Spinor<SF>::load(a.in + (size_t)(a.t0 + j) * a.field_bytes, vh, nb[term], s);
+                    if (fwd)
+                        mv_add(acc[j], U, s);
+                    else
+                        mv_adj_sub(acc[j], U, s);
+                }
+            }
+            phase_sum += c[mu];
+        }
+
+        const real sgn = (real)a.sign;
+#pragma unroll
+        for (int j = 0; j < T; j++) {
+            real o[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) o[k] = sgn * acc[j][k];
+            const size_t off = (size_t)(a.t0 + j) * a.field_bytes;
+            if (a.xpay) {
+                real yv[6];
+                Spinor<SF>::load(a.y + off, vh, cb, yv);
+                const real aa = (real)a.a[a.t0 + j];
+#pragma unroll
+                for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
+                if constexpr (RED) {
+#pragma unroll
+                    for (int k = 0; k < 6; k++) rv[2 * j] += (double)yv[k] * (double)o[k];
+                }
+            }
+            if constexpr (RED) {
+#pragma unroll
+                for (int k = 0; k < 6; k++) rv[2 * j + 1] += (double)o[k] * (double)o[k];
+            }
+            if (!Spinor<SF>::store(a.out + off, vh, cb, o)) atomicExch(a.err, 1);
+        }
+    }
+
+    if constexpr (RED) {
+        __shared__ double tot[2 * T];
+        if (reduce_grid<2 * T>(rv, a.red, tot) && threadIdx.x == 0)
+            run_batch_finisher(a.fin, tot, a.st, a.t0, T, a.slot);
+    }
+}
+
+template <int GF, int SF, typename real, int LREC, bool RED>
+void launch_mrhs_tile(int T, const DslashMArgs &a, cudaStream_t s)
+{
+    const int nb = (a.g.vh + kMrhsBlock - 1) / kMrhsBlock;
+    switch (T) {
+    case 16: dslash_mrhs_kernel<GF, SF, real, LREC, 16, RED><<<nb, kMrhsBlock, 0, s>>>(a); break;
+    case 8: dslash_mrhs_kernel<GF, SF, real, LREC, 8, RED><<<nb, kMrhsBlock, 0, s>>>(a); break;
+    case 4: dslash_mrhs_kernel<GF, SF, real, LREC, 4, RED><<<nb, kMrhsBlock, 0, s>>>(a); break;
+    case 2: dslash_mrhs_kernel<GF, SF, real, LREC, 2, RED><<<nb, kMrhsBlock, 0, s>>>(a); break;
+    default: dslash_mrhs_kernel<GF, SF, real, LREC, 1, RED><<<nb, kMrhsBlock, 0, s>>>(a); break;
+    }
+}
+
+// All nrhs right-hand sides in tiles of T (T divides nrhs; one launch per tile).
+template <int GF, int SF, typename real>
+bool launch_mrhs_t(int long_recon, bool reduce, int T, const DslashMArgs &args, cudaStream_t s)
+{
+    for (int t0 = 0; t0 < args.nrhs; t0 += T) {
+        DslashMArgs a = args;
+        a.t0 = t0;
+        if (long_recon == 12) {
+            if (reduce)
+                launch_mrhs_tile<GF, SF, real, 12, true>(T, a, s);
+            else
+                launch_mrhs_tile<GF, SF, real, 12, false>(T, a, s);
+        } else {
+            if (reduce)
+                launch_mrhs_tile<GF, SF, real, 18, true>(T, a, s);
+            else
+                launch_mrhs_tile<GF, SF, real, 18, false>(T, a, s);
+        }
+    }
+    return true;
+}
+
+}  // namespace hisq

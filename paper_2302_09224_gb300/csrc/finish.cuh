@@ -21,7 +21,7 @@ __device__ __forceinline__ void ms_stop(MSState *m, int reason)
     m->active = 0;
 }
 
-// Multi-shift finishers (Sec. 2.2; the shifted recurrences of Jegerlehner,
+// Multi-shift finishers (Sec. 3.2; the shifted recurrences of Jegerlehner,
 // hep-lat/9612014): r_i = zeta_i r with
 //   zeta_i' = zeta_i zeta_i^- a^- / (a b^- (zeta_i^- - zeta_i) + zeta_i^- a^- (1 + s_i a))
 //   alpha_i = a zeta_i'/zeta_i,  beta_i = b (zeta_i'/zeta_i)^2.
@@ -106,6 +106,7 @@ __device__ __forceinline__ void run_ms_finisher(int fin, const double *sums, MSS
 // sums: the grid totals of the reducing kernel; slot: ring slot of p.
 __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *state, int slot)
 {
+    if (state == nullptr || fin == FIN_NONE || fin == FIN_STORE) return;  // sums stay in RedBuf::result
     if (fin >= FIN_MS_ALPHA) {
         run_ms_finisher(fin, sums, static_cast<MSState *>(state));
         return;
@@ -124,7 +125,7 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
         st->alpha = alpha;
         st->alpha_ring[slot] = alpha;
     } else if (fin == FIN_CG_BETA) {
-        // sums = {|r_new|^2, Re<r_new, r_old>}; Polak-Ribiere beta (Sec. 2.1
+        // sums = {|r_new|^2, Re<r_new, r_old>}; Polak-Ribiere beta (Sec. 3.1
         // item 3) = r_new^+(r_new - r_old) / |r_old|^2, else Fletcher-Reeves
         const double rr_new = sums[0];
         const double num = st->pr ? rr_new - sums[1] : rr_new;
@@ -140,10 +141,10 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
         if (rr_new > st->rr_max) st->rr_max = rr_new;
         if (rr_new <= st->stop2)
             stop_iterating(st, REASON_CONVERGED);
-        else if (rr_new < st->delta2 * st->rr_max)  // |r| < delta max|r| (Sec. 2 footnote)
+        else if (rr_new < st->delta2 * st->rr_max)  // |r| < delta max|r| (Sec. 3 footnote)
             stop_iterating(st, REASON_RELIABLE);
     } else if (fin == FIN_CG_TRUE) {
-        // sums = {|r_hi|^2, Re<r_hi, p>, Im<r_hi, p>}.  Re-projection (Sec. 2.1
+        // sums = {|r_hi|^2, Re<r_hi, p>, Im<r_hi, p>}.  Re-projection (Sec. 3.1
         // item 2): p <- p - (<r_hi,p>/|r_hi|^2) r_hi, then Fletcher-Reeves
         // beta = |r_hi|^2/|r_old|^2 and p_new = r_hi + beta p, i.e.
         // p_new = (1 - beta c) r_hi + beta p with c = <r_hi,p>/|r_hi|^2.
@@ -166,6 +167,15 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
         st->active = 1;
         if (!isfinite(rr)) stop_iterating(st, REASON_BREAKDOWN);
     }
+}
+
+// Batched solver: the CG finisher for each active right-hand side of a tile
+// (stopped right-hand sides keep their state untouched).
+__device__ __forceinline__ void run_batch_finisher(int fin, const double *sums, CGState *st, int t0, int T, int slot)
+{
+    if (st == nullptr) return;
+    for (int j = 0; j < T; j++)
+        if (st[t0 + j].active) run_finisher(fin, sums + 2 * j, &st[t0 + j], slot);
 }
 
 }  // namespace hisq

@@ -62,7 +62,7 @@ Geom make_geom(const int dims[4], int antiperiodic_t);
 // ---------------------------------------------------------------------------
 // deterministic two-level reductions (last block finishes)
 // ---------------------------------------------------------------------------
-constexpr int kMaxRed = 8;          // values reduced per launch
+constexpr int kMaxRed = 32;         // values reduced per launch
 constexpr int kMaxRedBlocks = 1 << 16;
 
 struct RedBuf {
@@ -99,7 +99,7 @@ struct CGState {
 
 enum { REASON_NONE = 0, REASON_RELIABLE = 1, REASON_CONVERGED = 2, REASON_BREAKDOWN = 3 };
 
-// Multi-shift CG (Sec. 2.2): the base recurrence plus, per shift, the
+// Multi-shift CG (Sec. 3.2): the base recurrence plus, per shift, the
 // co-linearity factor zeta_i (r_i = zeta_i r) and its step sizes.
 constexpr int kMaxShift = 32;
 
@@ -163,6 +163,31 @@ struct DslashArgs {
     int slot;               // ring slot handed to the finisher
 };
 
+// A tile of right-hand sides for the batched stencil: right-hand side t lives
+// in the fields at in/out/y + t * field_bytes.
+constexpr int kMaxRHS = 16;
+
+struct DslashMArgs {
+    Geom g;
+    GaugeView gv;
+    int out_parity;
+    const char *in;
+    char *out;
+    const char *y;
+    size_t field_bytes;
+    double a[kMaxRHS];      // per right-hand side xpay coefficient
+    int sign;
+    int xpay;
+    int nrhs;
+    int t0;                 // first right-hand side of the tile (set by the launcher)
+    const int *active_any;  // skip when *active_any == 0 (null: always run)
+    int *err;
+    RedBuf red;
+    int fin;
+    CGState *st;            // per right-hand side states (st[t])
+    int slot;
+};
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -170,6 +195,15 @@ struct DslashArgs {
 // no kernel.
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a,
                    cudaStream_t s);
+// Batched stencil over all right-hand sides in tiles of T (T in {1,2,4,8,16},
+// dividing nrhs); false when the triplet has no batched kernel.
+bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, const DslashMArgs &a,
+                        cudaStream_t s);
+// Times each stencil launch shape on `a` (run as a plain pass: `a.out` is
+// overwritten) and keeps the fastest for this triplet and lattice.  Call
+// outside stream capture.
+void tune_dslash(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
+int stencil_config(int gf, int sf, int cf, int long_recon, const Geom &g);
 
 void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);
 void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s);

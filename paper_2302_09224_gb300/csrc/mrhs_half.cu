@@ -1,0 +1,9 @@
+// Batched-RHS stencil kernels for the FIX16 gauge / HALF spinor / float compute triplet.
+#include "dslash_mrhs.cuh"
+
+namespace hisq {
+bool launch_mrhs_half(int long_recon, bool reduce, int T, const DslashMArgs &a, cudaStream_t s)
+{
+    return launch_mrhs_t<G_FIX16, S_HALF, float>(long_recon, reduce, T, a, s);
+}
+}  // namespace hisq

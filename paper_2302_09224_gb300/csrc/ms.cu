@@ -1,4 +1,4 @@
-// ms.cu -- mixed-precision multi-shift CG with refinement (Sec. 2.2) and its
+// ms.cu -- mixed-precision multi-shift CG with refinement (Sec. 3.2) and its
 // C-ABI entry point.
 //
 // Stage 1 (sloppy triplet): one base recurrence on A = M_ee + sigma_0 (the
@@ -133,8 +133,8 @@ double format_eps(int sf)
     switch (sf) {
     case S_F32: return std::ldexp(1.0, -24);
     case S_HALF: return std::ldexp(1.0, -15);  // Sec. 2
-    case S_INT20: return std::ldexp(1.0, -19); // Sec. 3
-    case S_INT30: return std::ldexp(1.0, -29); // Sec. 3
+    case S_INT20: return std::ldexp(1.0, -19); // Sec. 4
+    case S_INT30: return std::ldexp(1.0, -29); // Sec. 4
     default: return std::ldexp(1.0, -52);
     }
 }
@@ -309,6 +309,8 @@ struct MSRun {
         if (cudaMallocHost(&mh, sizeof(MSState)) != cudaSuccess) return fail(c, HISQ_ENOMEM, "pinned host state");
         cudaMemsetAsync(ACC, 0, accb * ns, s);
         cudaMemsetAsync(X, 0, b48 * ns, s);
+        tune_stencil(c, g->geom, p.sloppy, gv_s, w_s, tmp_s, s);
+        tune_stencil(c, g->geom, prec_f64(), gv_d, (char *)ax64, (char *)tmp64, s);
         // r = p_i = b
         {
             LaunchScope ls(c, s, PROF_CONVERT, (48.0 + spinor_site_bytes(p.sloppy.spinor)) * vh);
@@ -405,7 +407,7 @@ struct MSRun {
         // FP64 true residual of every shift after the multi-shift stage (Table 3's r_sigma)
         std::vector<double> rs(ns);
         for (int i = 0; i < ns; i++) {
-            residual(i, FIN_NONE, nullptr);
+            residual(i, FIN_STORE, nullptr);
             double rr = 0;
             cudaMemcpyAsync(&rr, c->red.result, sizeof rr, cudaMemcpyDeviceToHost, s);
             if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "residual");

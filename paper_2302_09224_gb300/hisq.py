@@ -43,7 +43,7 @@ class hisq_prec(ctypes.Structure):
 
 
 def prec(name: str, long_recon: int = 12) -> hisq_prec:
-    """Named triplets of Sec. 3 (gauge / fermion / compute)."""
+    """Named triplets of Sec. 4 (gauge / fermion / compute)."""
     table = {
         "f64": (HISQ_GAUGE_F64, HISQ_SPINOR_F64, HISQ_COMPUTE_F64),
         "f32": (HISQ_GAUGE_F32, HISQ_SPINOR_F32, HISQ_COMPUTE_F32),

@@ -1,4 +1,4 @@
-"""GPU BiCGStab(l) (Sec. 5.1) on the full-lattice operator 2m + D against the oracle.
+"""GPU BiCGStab(l) (Sec. 6.1) on the full-lattice operator 2m + D against the oracle.
 
 * 2^4 and 4^4: the solution against the oracle's dense direct solve;
 * 8^4 and 8^3 x 16: the FP64 true residual of x recomputed by the CPU oracle

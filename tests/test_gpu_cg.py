@@ -1,4 +1,4 @@
-"""GPU CG (plain FP64 and stabilised mixed precision, Sec. 2.1) against the oracle.
+"""GPU CG (plain FP64 and stabilised mixed precision, Sec. 3.1) against the oracle.
 
 * 2^4 and 4^4: the solution against the oracle's dense direct solve;
 * larger lattices: the FP64 true residual of the returned x, recomputed by the

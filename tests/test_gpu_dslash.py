@@ -1,4 +1,4 @@
-"""GPU stencil against the FP64 oracle, per precision triplet (Sec. 3, Sec. 4.2).
+"""GPU stencil against the FP64 oracle, per precision triplet (Sec. 4, Sec. 5.2).
 
 For every triplet the C-ABI ``hisq_dslash`` (input rounded into the spinor
 format, links in the gauge format, arithmetic in the compute precision,
@@ -12,7 +12,7 @@ output repacked) is compared with
 
 on lattices that exercise a ragged last block, the 2^4 and 4^4 aliasing of the
 three-hop term, non-cubic extents and antiperiodic time.  The orderings the
-paper reports for the deviation (Sec. 4.2: 30-bit with FP64 compute about two
+paper reports for the deviation (Sec. 5.2: 30-bit with FP64 compute about two
 orders below FP32; 20-bit only modestly better than half) are checked too.
 """
 import numpy as np
@@ -121,7 +121,7 @@ def test_host_pointers_match_device(ctx):
 
 
 def test_deviation_orderings(ctx, orc):
-    """Sec. 4.2: 30-bit + FP64 ~100x below FP32; 30-bit + FP32 ~ FP32; 20-bit < half."""
+    """Sec. 5.2: 30-bit + FP64 ~100x below FP32; 30-bit + FP32 ~ FP32; 20-bit < half."""
     dims = (8, 8, 8, 8)
     fat, lng = lattice(dims, False)
     err = {}

@@ -1,4 +1,4 @@
-"""GPU multi-shift CG with refinement (Sec. 2.2) against the oracle.
+"""GPU multi-shift CG with refinement (Sec. 3.2) against the oracle.
 
 * 4^4: every shift's solution against a dense direct solve of M_ee + sigma_i;
 * 8^4 with twelve log-spaced shifts and log-spaced targets (the structure of

@@ -4,7 +4,7 @@
   (``tests/golden/*_vectors.txt``: Appendix A, Listing 4 for 20-bit;
   Sec. 2, Listing 1 for 16-bit; our stated reading of Listing 3 for 30-bit);
 * round-trip error within the format's epsilon (Sec. 2: 2^-15 relative to the
-  site maximum for the two's-complement 16-bit format; Sec. 3: about 2^-19
+  site maximum for the two's-complement 16-bit format; Sec. 4: about 2^-19
   for 20-bit and 2^-29 for 30-bit);
 * idempotence ``pack(unpack(pack(v))) == pack(v)`` and exact round trip of
   vectors that are already on the format's grid;
@@ -145,7 +145,7 @@ def test_int30_exact_grid(orc):
 
 
 def test_spinor_emulate_orders(orc):
-    """Format error ordering of Sec. 3: int30 << f32 < int20 < half."""
+    """Format error ordering of Sec. 4: int30 << f32 < int20 < half."""
     v = synth.spinor((4, 4, 4, 4), 7).numpy().reshape(-1, 6)
     err = {}
     for f in ("f32", "half", "int20", "int30"):

@@ -2,10 +2,10 @@
 
 * CG (textbook Hestenes-Stiefel) against a dense direct solve of M_ee by the
   oracle's own LU, itself cross-checked against numpy;
-* multi-shift CG (Sec. 2.2, co-linear shifted residuals) against dense solves
+* multi-shift CG (Sec. 3.2, co-linear shifted residuals) against dense solves
   per shift, the co-linearity invariant ``b - (A + s_i) x_i = zeta_i r`` and
   the single-shift case, which must reproduce CG;
-* BiCGStab(l) (Sec. 5.1) against a dense solve of the full ``2m + D`` and, at
+* BiCGStab(l) (Sec. 6.1) against a dense solve of the full ``2m + D`` and, at
   l = 1, against the textbook BiCGStab iterates written here from
   van der Vorst's recurrences (a different algorithm that coincides at l = 1).
 """

@@ -1,6 +1,6 @@
 """Pins of the oracle's HISQ stencil (CPU only).
 
-The stencil is only named in the paper (Sec. 1, Sec. 4.2); the oracle reads
+The stencil is only named in the paper (Sec. 1, Sec. 5.2); the oracle reads
 it as the one-hop fat plus three-hop Naik staggered operator with phased links.
 These tests fix that reading by properties a mistake would break:
 
