@@ -152,6 +152,35 @@ HISQ_API hisq_status hisq_dslash(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec p
                         const double *xpay_in, const double *in, double *out, int on_device,
                         void *stream);
 
+/* Sites per parity accepted by hisq_dslash_noalloc: 2^15, e.g. a 16^4 lattice
+ * (its fixed scratch is 3 x 48 B x 2 x 2^15 = 9 MiB plus 256 B). */
+#define HISQ_NOALLOC_MAX_SITES 32768
+
+/* hisq_dslash for callers that cannot allocate device memory.  The paper has
+ * no counterpart; it exists because some callers may not call cudaMalloc: an
+ * application whose own pool allocator has already reserved the GPU's memory
+ * (an allocation would fail or fragment that pool), or a long-running loop
+ * that must not allocate, since cudaMalloc and cudaFree synchronise the device
+ * and can fail partway through a run.  Same arguments and result as
+ * hisq_dslash with on_device = 1 (in, out, xpay_in are device pointers) but
+ * it allocates nothing: its scratch (the fields in the storage format and a
+ * non-finite counter) is one fixed device array of this library, which every
+ * GPU that loads the library holds until the process exits.
+ * Limits and rules:
+ *  - at most HISQ_NOALLOC_MAX_SITES sites per parity, else EINVAL;
+ *  - the gauge field must already hold its stored copy for `prec` (any earlier
+ *    hisq_dslash or solver call with that precision builds it), else EINVAL;
+ *  - the first call on a device looks up the scratch array's device address
+ *    once (cudaGetSymbolAddress); make that first call before any stream
+ *    capture;
+ *  - every call uses the same scratch array, which keeps the previous call's
+ *    contents (the counter is cleared at each call): calls whose work overlaps
+ *    on the GPU (several streams or host threads) race, so serialise them;
+ *  - the call synchronises `stream` before returning. */
+HISQ_API hisq_status hisq_dslash_noalloc(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec prec, int out_parity,
+                                         double a, const double *xpay_in, const double *in, double *out,
+                                         void *stream);
+
 /* Device bytes of one half-lattice (n sites) spinor field in format sfmt, in
  * this library's planar layout: the site record is split into 16-byte planes
  * [plane][site] followed by one narrower tail plane (F32 and INT30: 16 + 8 B;

@@ -172,6 +172,27 @@ static hisq_status get_copy(hisq_ctx *c, hisq_gauge *g, bool lng, int gf, int re
     return HISQ_OK;
 }
 
+hisq_status gauge_view_existing(hisq_ctx *c, const hisq_gauge *g, const hisq_prec &p, GaugeView *v)
+{
+    hisq_status st = check_prec(c, p);
+    if (st) return st;
+    v->fat = v->lng = nullptr;
+    for (auto &lc : g->fat_copies)
+        if (lc.gf == p.gauge && lc.recon == p.fat_recon) v->fat = lc.ptr;
+    for (auto &lc : g->lng_copies)
+        if (lc.gf == p.gauge && lc.recon == p.long_recon) v->lng = lc.ptr;
+    if (!v->fat || !v->lng)
+        return fail(c, HISQ_EINVAL,
+                    "the gauge field has no stored copy for this precision yet (any hisq_dslash or solver call "
+                    "with it builds one)");
+    const double qmax = p.gauge == G_FIX16 ? 32767.0 : 2147483647.0;
+    v->fat_scale_d = g->fat_max / qmax;
+    v->lng_scale_d = g->lng_max / qmax;
+    v->fat_scale_f = (float)v->fat_scale_d;
+    v->lng_scale_f = (float)v->lng_scale_d;
+    return HISQ_OK;
+}
+
 hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, GaugeView *v)
 {
     hisq_status st = check_prec(c, p);

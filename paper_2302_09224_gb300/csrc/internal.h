@@ -300,5 +300,7 @@ bool stream_capturing(cudaStream_t s);
 // A validated triplet: returns HISQ_OK and the device view of the gauge copy.
 hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, GaugeView *v);
 hisq_status check_prec(hisq_ctx *c, const hisq_prec &p);
+// The same view without building a missing copy (never allocates).
+hisq_status gauge_view_existing(hisq_ctx *c, const hisq_gauge *g, const hisq_prec &p, GaugeView *v);
 
 }  // namespace hisq

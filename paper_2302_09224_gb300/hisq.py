@@ -101,6 +101,7 @@ _SIGS = {
     "hisq_free_gauge": (None, [_P, _P]),
     "hisq_gauge_scale": (_D, [_P, _I]),
     "hisq_dslash": (_I, [_P, _P, hisq_prec, _I, _D, _P, _P, _P, _I, _P]),
+    "hisq_dslash_noalloc": (_I, [_P, _P, hisq_prec, _I, _D, _P, _P, _P, _P]),
     "hisq_spinor_bytes": (_SZ, [_I, _I64]),
     "hisq_spinor_pack": (_I, [_P, _I, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
     "hisq_spinor_unpack": (_I, [_P, _I, _I, _I64, _P, _P, _P]),
@@ -222,6 +223,15 @@ def hisq_gauge_scale(g, which: int) -> float:
 def hisq_dslash(ctx, g, p: hisq_prec, out_parity: int, a: float, xpay_in, x, out, on_device: bool, stream=None):
     _check(ctx, lib().hisq_dslash(ctx, g, p, int(out_parity), float(a), _ptr(xpay_in), _ptr(x), _ptr(out),
                                   int(bool(on_device)), _stream(stream)))
+
+
+HISQ_NOALLOC_MAX_SITES = 32768
+
+
+def hisq_dslash_noalloc(ctx, g, p: hisq_prec, out_parity: int, a: float, xpay_in, x, out, stream=None):
+    """hisq_dslash on device pointers without any device allocation (fixed scratch)."""
+    _check(ctx, lib().hisq_dslash_noalloc(ctx, g, p, int(out_parity), float(a), _ptr(xpay_in), _ptr(x),
+                                          _ptr(out), _stream(stream)))
 
 
 def hisq_spinor_bytes(sfmt: int, n: int) -> int:
