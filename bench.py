@@ -371,6 +371,8 @@ def run_stencil_only(args):
     from paper_2302_09224_gb300 import hisq, synth
 
     dims = tuple(int(v) for v in args.stencil.split(","))
+    if args.stencil_config >= 0:
+        hisq.hisq_stencil_config(args.stencil_config)
     ctx = hisq.hisq_create(0)
     fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
     g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
@@ -402,6 +404,7 @@ def main():
     ap.add_argument("--stencil", default=None, help="LX,LY,LZ,LT: only run stencil applications (profiling)")
     ap.add_argument("--prec", default="int20")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--stencil-config", type=int, default=-1, help="force a stencil launch shape (0..4)")
     args = ap.parse_args()
     if args.stencil:
         return run_stencil_only(args)

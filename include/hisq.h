@@ -226,6 +226,13 @@ HISQ_API void hisq_profile_enable(hisq_ctx *ctx, int on);
 HISQ_API void hisq_profile_reset(hisq_ctx *ctx);
 HISQ_API hisq_status hisq_profile_read(hisq_ctx *ctx, int kind, hisq_kernel_stats *out);
 
+/* Launch shape of the stencil kernels: -1 (default) lets the library time the
+ * shapes the first time a (precision, lattice) pair is used and keep the
+ * fastest; 0..4 forces one shape for every later launch in the process.
+ * Returns the previous setting, or -2 for an invalid value.  For benchmarking
+ * and testing the shapes. */
+HISQ_API int hisq_stencil_config(int cfg);
+
 /* Kernels this context has launched so far (graph replays add their nodes). */
 HISQ_API int64_t hisq_launch_count(hisq_ctx *ctx);
 
@@ -247,12 +254,14 @@ typedef struct {
     int32_t reproject;    /* 1: re-project p at each reliable update (Sec. 3.1 item 2) */
     int32_t l;            /* BiCGStab(l): l (Sec. 6.1 uses 4), 1..8 */
     int32_t use_graph;    /* 1: replay each block of iterations as a CUDA graph */
+    int32_t nrhs;         /* hisq_cg: right-hand sides solved together (1..16, Sec. 1 block solvers) */
+    int32_t rhs_tile;     /* right-hand sides per stencil launch (1,2,4,8,16 dividing nrhs; 0: tuned) */
     void *stream;         /* cudaStream_t; NULL: the context's stream */
 } hisq_solver_params;
 
 /* Fills params with the defaults: delta 0.1, nbuf 8, pr_beta 1, reproject 1,
- * l 4, use_graph 1, maxiter 100000, tol 1e-10, sloppy and refine
- * FIX16/INT20/F32 with r12 long links. */
+ * l 4, use_graph 1, nrhs 1, rhs_tile 0, maxiter 100000, tol 1e-10, sloppy
+ * and refine FIX16/INT20/F32 with r12 long links. */
 HISQ_API void hisq_default_params(hisq_solver_params *p);
 
 #define HISQ_MAX_SHIFTS 32
@@ -277,6 +286,12 @@ typedef struct {
  * updates with an FP64 true residual whenever |r| drops below delta times its
  * maximum since the last update, re-projection of p and Polak-Ribiere beta.
  * With sloppy = F64/F64/F64 this is plain FP64 CG.  b, x: half-lattice FP64.
+ * With nrhs > 1, b and x hold nrhs half-lattice fields back to back and the
+ * systems are iterated together: every stencil launch applies each link it
+ * loads to a tile of rhs_tile right-hand sides (sloppy triplets F32, half and
+ * 20-bit); each right-hand side keeps its own recurrence and stops on its own;
+ * info then reports the largest iteration count and true residual and the
+ * summed operator applications.
  * Returns OK, ENOTCONV (x is the best iterate, info filled), EBREAKDOWN,
  * EINVAL, ENOMEM, ECUDA. */
 HISQ_API hisq_status hisq_cg(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
@@ -296,6 +311,60 @@ HISQ_API hisq_status hisq_multishift_cg(hisq_ctx *ctx, const hisq_gauge *g, cons
  * FP64 x and a reliable update at the end of a cycle when triggered. */
 HISQ_API hisq_status hisq_bicgstabl(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
                            double *x, hisq_solve_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* Request loop (continuous batching)                                        */
+/* ------------------------------------------------------------------------ */
+
+#define HISQ_REQ_CG 0          /* (4m^2 - D_eo D_oe) x = b */
+#define HISQ_REQ_MULTISHIFT 1  /* (M_ee + sigma_i) x_i = b, i < nshift */
+
+typedef struct {
+    const hisq_gauge *gauge; /* resident gauge field: its lattice is the request's volume */
+    int32_t kind;            /* HISQ_REQ_CG or HISQ_REQ_MULTISHIFT */
+    double mass;
+    double tol;              /* CG: target true residual */
+    int32_t nshift;          /* multi-shift: number of shifts (<= HISQ_MAX_SHIFTS) */
+    const double *sigma;     /* multi-shift: shifts (copied at submit) */
+    const double *shift_tol; /* multi-shift: per-shift targets (copied at submit) */
+    const double *b;         /* half-lattice FP64 source */
+    double *x;               /* CG: one half-lattice field; multi-shift: nshift fields back to back */
+    int32_t on_device;       /* b and x are device pointers */
+    hisq_prec sloppy;        /* CG sloppy / multi-shift stage triplet */
+    hisq_prec refine;        /* multi-shift refinement triplet */
+    int32_t maxiter;
+} hisq_request;
+
+typedef struct {
+    int64_t completed;
+    int64_t pending;
+    double latency_p50_s;  /* submit -> done */
+    double latency_p99_s;
+    double solves_per_s;   /* completed / (last completion - first submission) */
+} hisq_serve_stats_t;
+
+/* Queue a solve and return at once with a ticket.  Worker threads of the
+ * context (each with its own stream, so their work overlaps on the device)
+ * take requests in arrival order.  CG requests on the same gauge field with
+ * the same sloppy triplet (FP32, half or 20-bit) share batch sessions: at
+ * every block of iterations finished systems leave and queued ones join
+ * (continuous batching); multi-shift requests run one per worker.  A session
+ * starts only when the context's HBM budget has room for it; otherwise its
+ * requests wait.  b and x stay owned by the caller and must stay valid until
+ * the request is done; the gauge must not be freed while requests use it.
+ * Errors: EINVAL (bad request), EBUSY (queue full). */
+HISQ_API hisq_status hisq_submit(hisq_ctx *ctx, const hisq_request *req, uint64_t *ticket);
+
+/* Non-blocking: *done = 1 and info filled once the request finished (the
+ * return value is then the solve's status and the ticket is released);
+ * *done = 0 while it is queued or running.  ENOTFOUND for unknown tickets. */
+HISQ_API hisq_status hisq_poll(hisq_ctx *ctx, uint64_t ticket, int *done, hisq_solve_info *info);
+
+/* Bounded wait for a request: its status once done, ETIMEOUT after timeout_s. */
+HISQ_API hisq_status hisq_wait(hisq_ctx *ctx, uint64_t ticket, double timeout_s, hisq_solve_info *info);
+
+/* Completed requests, queue length, latency percentiles and throughput. */
+HISQ_API hisq_status hisq_serve_stats(hisq_ctx *ctx, hisq_serve_stats_t *out);
 
 #ifdef __cplusplus
 }

@@ -155,13 +155,17 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, con
         real xv[6], yv[6];
         Spinor<SF>::load(half(x, a.hb), a.vh, s, xv);
         Spinor<SF>::load(half(y, a.hb), a.vh, s, yv);
+        real d0 = 0, d1 = 0, d2 = 0;  // one site in the compute precision; sites summed in FP64
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double xr = xv[2 * c], xi = xv[2 * c + 1], yr = yv[2 * c], yi = yv[2 * c + 1];
-            v[0] += xr * yr + xi * yi;
-            v[1] += xr * yi - xi * yr;
-            v[2] += yr * yr + yi * yi;
+            const real xr = xv[2 * c], xi = xv[2 * c + 1], yr = yv[2 * c], yi = yv[2 * c + 1];
+            d0 += xr * yr + xi * yi;
+            d1 += xr * yi - xi * yr;
+            d2 += yr * yr + yi * yi;
         }
+        v[0] = d0;
+        v[1] = d1;
+        v[2] = d2;
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
     if (skip(a.active)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.vh) return;
-    const double ar = a.b->alpha_re, ai = a.b->alpha_im;
+    const real ar = (real)a.b->alpha_re, ai = (real)a.b->alpha_im;
     for (int i = 0; i <= a.j; i++) {
         real u[6], r[6];
         Spinor<SF>::load(half(a.U + (i + 1) * a.fb, a.hb), a.vh, s, u);
@@ -205,12 +209,13 @@ __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
         Spinor<SF>::load(rf, a.vh, s, r);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double ur = u[2 * c], ui = u[2 * c + 1];
-            r[2 * c] = (real)((double)r[2 * c] - (ar * ur - ai * ui));
-            r[2 * c + 1] = (real)((double)r[2 * c + 1] - (ar * ui + ai * ur));
+            const real ur = u[2 * c], ui = u[2 * c + 1];
+            r[2 * c] -= ar * ur - ai * ui;
+            r[2 * c + 1] -= ar * ui + ai * ur;
         }
         if (!Spinor<SF>::store(rf, a.vh, s, r)) atomicExch(a.err, 1);
     }
+    // x += alpha u_0: the increment in the compute precision, the sum in FP64
     real u0[6];
     double x[6];
     Spinor<SF>::load(half(a.U, a.hb), a.vh, s, u0);
@@ -218,8 +223,8 @@ __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
     Spinor<S_F64>::load(xf, a.vh, s, x);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        x[2 * c] += ar * u0[2 * c] - ai * u0[2 * c + 1];
-        x[2 * c + 1] += ar * u0[2 * c + 1] + ai * u0[2 * c];
+        x[2 * c] += (double)(ar * u0[2 * c] - ai * u0[2 * c + 1]);
+        x[2 * c + 1] += (double)(ar * u0[2 * c + 1] + ai * u0[2 * c]);
     }
     Spinor<S_F64>::store(xf, a.vh, s, x);
 }
@@ -239,29 +244,33 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
         if (a.i >= 2) {
             real rp[6];
             Spinor<SF>::load(half(a.R + (a.i - 1) * a.fb, a.hb), a.vh, s, rp);
-            const double tr = a.b->tau_re[a.i - 1][a.j], ti = a.b->tau_im[a.i - 1][a.j];
+            const real tr = (real)a.b->tau_re[a.i - 1][a.j], ti = (real)a.b->tau_im[a.i - 1][a.j];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const double pr = rp[2 * c], pi = rp[2 * c + 1];
-                rj[2 * c] = (real)((double)rj[2 * c] - (tr * pr - ti * pi));
-                rj[2 * c + 1] = (real)((double)rj[2 * c + 1] - (tr * pi + ti * pr));
+                const real pr = rp[2 * c], pi = rp[2 * c + 1];
+                rj[2 * c] -= tr * pr - ti * pi;
+                rj[2 * c + 1] -= tr * pi + ti * pr;
             }
             if (!Spinor<SF>::store(rjf, a.vh, s, rj)) atomicExch(a.err, 1);
         }
         const int other = a.i < a.j ? a.i : 0;  // <r_i, r_j>, or <r_j, r_0> at i == j
         Spinor<SF>::load(half(a.R + other * a.fb, a.hb), a.vh, s, ri);
+        real d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const double jr = rj[2 * c], ji = rj[2 * c + 1], or_ = ri[2 * c], oi = ri[2 * c + 1];
+            const real jr = rj[2 * c], ji = rj[2 * c + 1], or_ = ri[2 * c], oi = ri[2 * c + 1];
             if (a.i < a.j) {  // conj(r_i) r_j
-                v[0] += or_ * jr + oi * ji;
-                v[1] += or_ * ji - oi * jr;
+                d0 += or_ * jr + oi * ji;
+                d1 += or_ * ji - oi * jr;
             } else {          // conj(r_j) r_0
-                v[0] += jr * or_ + ji * oi;
-                v[1] += jr * oi - ji * or_;
+                d0 += jr * or_ + ji * oi;
+                d1 += jr * oi - ji * or_;
             }
-            v[2] += jr * jr + ji * ji;
+            d2 += jr * jr + ji * ji;
         }
+        v[0] = d0;
+        v[1] = d1;
+        v[2] = d2;
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -308,42 +317,40 @@ __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
     const int l = b->l;
     double v[1] = {0.0};
     if (s < a.vh) {
-        double x[6], r0[6], u0[6];
-        real t[6];
+        // updates in the compute precision; x's increment is added in FP64
+        real dx[6] = {0, 0, 0, 0, 0, 0}, r0[6], u0[6], t[6];
         char *xf = reinterpret_cast<char *>(a.x64) + blockIdx.y * (size_t)48 * a.vh;
         char *r0f = half(a.R, a.hb), *u0f = half(a.U, a.hb);
-        Spinor<S_F64>::load(xf, a.vh, s, x);
-        Spinor<SF>::load(r0f, a.vh, s, t);
-        for (int k = 0; k < 6; k++) r0[k] = t[k];
-        Spinor<SF>::load(u0f, a.vh, s, t);
-        for (int k = 0; k < 6; k++) u0[k] = t[k];
-        auto cax = [](double *y, double cr, double ci, const real *z, double sgn) {
+        Spinor<SF>::load(r0f, a.vh, s, r0);
+        Spinor<SF>::load(u0f, a.vh, s, u0);
+        auto cax = [](real *y, double cr, double ci, const real *z, real sgn) {
+            const real c_r = (real)cr * sgn, c_i = (real)ci * sgn;
             for (int c = 0; c < 3; c++) {
-                y[2 * c] += sgn * (cr * z[2 * c] - ci * z[2 * c + 1]);
-                y[2 * c + 1] += sgn * (cr * z[2 * c + 1] + ci * z[2 * c]);
+                y[2 * c] += c_r * z[2 * c] - c_i * z[2 * c + 1];
+                y[2 * c + 1] += c_r * z[2 * c + 1] + c_i * z[2 * c];
             }
         };
-        real r0s[6];
-        for (int k = 0; k < 6; k++) r0s[k] = (real)r0[k];
-        cax(x, b->g_re[1], b->g_im[1], r0s, 1.0);
+        cax(dx, b->g_re[1], b->g_im[1], r0, real(1));
         Spinor<SF>::load(half(a.R + l * a.fb, a.hb), a.vh, s, t);
-        cax(r0, b->gp_re[l], b->gp_im[l], t, -1.0);
+        cax(r0, b->gp_re[l], b->gp_im[l], t, real(-1));
         Spinor<SF>::load(half(a.U + l * a.fb, a.hb), a.vh, s, t);
-        cax(u0, b->g_re[l], b->g_im[l], t, -1.0);
+        cax(u0, b->g_re[l], b->g_im[l], t, real(-1));
         for (int j = 1; j <= l - 1; j++) {
             Spinor<SF>::load(half(a.U + j * a.fb, a.hb), a.vh, s, t);
-            cax(u0, b->g_re[j], b->g_im[j], t, -1.0);
+            cax(u0, b->g_re[j], b->g_im[j], t, real(-1));
             Spinor<SF>::load(half(a.R + j * a.fb, a.hb), a.vh, s, t);
-            cax(x, b->gpp_re[j], b->gpp_im[j], t, 1.0);
-            cax(r0, b->gp_re[j], b->gp_im[j], t, -1.0);
+            cax(dx, b->gpp_re[j], b->gpp_im[j], t, real(1));
+            cax(r0, b->gp_re[j], b->gp_im[j], t, real(-1));
         }
+        double x[6];
+        Spinor<S_F64>::load(xf, a.vh, s, x);
+        for (int k = 0; k < 6; k++) x[k] += (double)dx[k];
         Spinor<S_F64>::store(xf, a.vh, s, x);
-        real o[6];
-        for (int k = 0; k < 6; k++) o[k] = (real)r0[k];
-        if (!Spinor<SF>::store(r0f, a.vh, s, o)) atomicExch(a.err, 1);
-        for (int k = 0; k < 6; k++) o[k] = (real)u0[k];
-        if (!Spinor<SF>::store(u0f, a.vh, s, o)) atomicExch(a.err, 1);
-        for (int k = 0; k < 6; k++) v[0] += r0[k] * r0[k];
+        if (!Spinor<SF>::store(r0f, a.vh, s, r0)) atomicExch(a.err, 1);
+        if (!Spinor<SF>::store(u0f, a.vh, s, u0)) atomicExch(a.err, 1);
+        real n2 = 0;
+        for (int k = 0; k < 6; k++) n2 += r0[k] * r0[k];
+        v[0] = n2;
     }
     __shared__ double tot[1];
     if (reduce_grid<1>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -412,8 +419,8 @@ struct BRun {
         a.x64 = x64;
         a.b = b;
         a.active = &b->active;
-        a.err = c->err_flag;
-        a.red = c->red;
+        a.err = cur_err(c);
+        a.red = cur_red(c);
         return a;
     }
 
@@ -427,8 +434,8 @@ struct BRun {
             DslashArgs d{};
             d.g = g->geom;
             d.gv = gv;
-            d.err = c->err_flag;
-            d.red = c->red;
+            d.err = cur_err(c);
+            d.red = cur_red(c);
             d.active = active;
             d.out_parity = po;
             d.in = in + (1 - po) * half_bytes;
@@ -512,8 +519,8 @@ struct BRun {
         for (int h = 0; h < 2; h++) {
             BlasArgs a{};
             a.n = vh;
-            a.err = c->err_flag;
-            a.red = c->red;
+            a.err = cur_err(c);
+            a.red = cur_red(c);
             a.b64 = b64 + h * 6 * (size_t)vh;
             a.ax64 = x_zero ? nullptr : ax64 + h * 6 * (size_t)vh;
             a.r64 = r64 + h * 6 * (size_t)vh;
@@ -523,7 +530,7 @@ struct BRun {
             a.fst = nullptr;
             LaunchScope ls(c, st, PROF_BLAS, (48.0 * 3 + 2.0 * spinor_site_bytes(p.sloppy.spinor)) * vh);
             launch_true_residual(p.sloppy.spinor, p.sloppy.compute, a, st);
-            if (h == 0) cudaMemcpyAsync(park, c->red.result, sizeof(double), cudaMemcpyDeviceToDevice, st);
+            if (h == 0) cudaMemcpyAsync(park, cur_red(c).result, sizeof(double), cudaMemcpyDeviceToDevice, st);
         }
     }
 
@@ -553,11 +560,11 @@ struct BRun {
         for (int h = 0; h < 2; h++) {
             BlasArgs a{};
             a.n = vh;
-            a.red = c->red;
+            a.red = cur_red(c);
             a.x64 = const_cast<double *>(b64) + h * 6 * (size_t)vh;
             launch_norm2(a, st);
             double part = 0;
-            cudaMemcpyAsync(&part, c->red.result, sizeof part, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&part, cur_red(c).result, sizeof part, cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "norm");
             bb += part;
         }
@@ -572,7 +579,7 @@ struct BRun {
             true_residual(b64, xz);
             double parts[2] = {0, 0};
             cudaMemcpyAsync(&parts[0], park, sizeof(double), cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(&parts[1], c->red.result, sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&parts[1], cur_red(c).result, sizeof(double), cudaMemcpyDeviceToHost, st);
             const cudaError_t ce = cudaStreamSynchronize(st);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "true residual");
             rr = parts[0] + parts[1];
@@ -607,13 +614,13 @@ struct BRun {
             if (graph) {
                 if (!exec) {
                     cudaGraph_t gr = nullptr;
-                    c->capturing = true;
+                    set_thread_capturing(true);
                     cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
                     if (ce == cudaSuccess) {
                         cycle();
                         ce = cudaStreamEndCapture(st, &gr);
                     }
-                    c->capturing = false;
+                    set_thread_capturing(false);
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
                     size_t nn = 0;
                     if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
@@ -640,8 +647,8 @@ struct BRun {
                 {
                     LaunchScope ls(c, st, PROF_BLAS, 0.0);
                     // total of both halves was assembled on the host; hand it to the device
-                    cudaMemcpyAsync(c->red.result, &rr, sizeof rr, cudaMemcpyHostToDevice, st);
-                    restart_kernel<<<1, 1, 0, st>>>(b, c->red.result);
+                    cudaMemcpyAsync(cur_red(c).result, &rr, sizeof rr, cudaMemcpyHostToDevice, st);
+                    restart_kernel<<<1, 1, 0, st>>>(b, cur_red(c).result);
                 }
                 e = pull();
                 if (e) break;

@@ -37,12 +37,15 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
         Spinor<SF>::load(a.v0, a.n, i, r);
         Spinor<SF>::load(a.v1, a.n, i, ap);
         const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
+        real n2 = 0, d = 0;  // per-site terms in the compute precision, summed over sites in FP64
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             rn[k] = r[k] - alpha * ap[k];
-            v[0] += (double)rn[k] * (double)rn[k];
-            v[1] += (double)rn[k] * (double)r[k];
+            n2 += rn[k] * rn[k];
+            d += rn[k] * r[k];
         }
+        v[0] = (double)n2;
+        v[1] = (double)d;
         if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
     }
     __shared__ double tot[2];
@@ -79,16 +82,21 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
     if (skip(a.active)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    double x[6];
-    Spinor<S_F64>::load(reinterpret_cast<const char *>(a.x64), a.n, i, x);
+    // the increment sum_j alpha_j p_j carries the sloppy vectors' precision,
+    // so it is formed in the compute precision and added to x in FP64
+    real dx[6] = {0, 0, 0, 0, 0, 0};
     for (int j = 0; j < a.nslots; j++) {
-        const double al = a.st->alpha_ring[j];
-        if (al == 0.0) continue;
+        const real al = (real)a.st->alpha_ring[j];
+        if (al == real(0)) continue;
         real p[6];
         Spinor<SF>::load(a.v0 + (size_t)j * a.slot_bytes, a.n, i, p);
 #pragma unroll
-        for (int k = 0; k < 6; k++) x[k] += al * (double)p[k];
+        for (int k = 0; k < 6; k++) dx[k] += al * p[k];
     }
+    double x[6];
+    Spinor<S_F64>::load(reinterpret_cast<const char *>(a.x64), a.n, i, x);
+#pragma unroll
+    for (int k = 0; k < 6; k++) x[k] += (double)dx[k];
     Spinor<S_F64>::store(reinterpret_cast<char *>(a.x64), a.n, i, x);
 }
 

@@ -17,10 +17,12 @@
 // reads the scalar state once per block.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
 
+#include "bcg.h"
 #include "blas.h"
 #include "cg.h"
 #include "internal.h"
@@ -65,8 +67,8 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
     DslashArgs d{};
     d.g = geom;
     d.gv = gv;
-    d.err = c->err_flag;
-    d.red = c->red;
+    d.err = cur_err(c);
+    d.red = cur_red(c);
     d.active = active;
     d.st = st;
     d.slot = slot;
@@ -95,13 +97,13 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
 void tune_stencil(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, char *zero_in, char *out,
                   cudaStream_t s)
 {
-    if (c->capturing || stream_capturing(s)) return;
+    if (thread_capturing() || stream_capturing(s)) return;
     cudaMemsetAsync(zero_in, 0, spinor_field_bytes(p.spinor, geom.vh), s);
     DslashArgs d{};
     d.g = geom;
     d.gv = gv;
-    d.err = c->err_flag;
-    d.red = c->red;
+    d.err = cur_err(c);
+    d.red = cur_red(c);
     d.out_parity = 1;
     d.in = zero_in;
     d.out = out;
@@ -142,8 +144,8 @@ struct CGRun {
     {
         BlasArgs a{};
         a.n = vh;
-        a.err = c->err_flag;
-        a.red = c->red;
+        a.err = cur_err(c);
+        a.red = cur_red(c);
         a.st = st;
         return a;
     }
@@ -263,7 +265,7 @@ struct CGRun {
             launch_norm2(a, s);
         }
         double bb = 0.0;
-        cudaMemcpyAsync(&bb, c->red.result, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&bb, cur_red(c).result, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "norm");
         info->iters = 0;
         info->reliable_updates = 0;
@@ -284,7 +286,7 @@ struct CGRun {
             // continue a previous recurrence: its gradient vector enters the
             // first restart (re-projected, with beta = |r_hi|^2 / rr_prev_init)
             LaunchScope ls(c, s, PROF_CONVERT, 2.0 * 48 * vh);
-            launch_convert(cfg.p_init_fmt, cfg.sloppy.spinor, vh, cfg.p_init, slot(0), c->err_flag, s);
+            launch_convert(cfg.p_init_fmt, cfg.sloppy.spinor, vh, cfg.p_init, slot(0), cur_err(c), s);
             init.rr_prev = cfg.rr_prev_init;
         }
         cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s);
@@ -304,13 +306,13 @@ struct CGRun {
             if (graph) {
                 if (!exec) {
                     cudaGraph_t gr = nullptr;
-                    c->capturing = true;
+                    set_thread_capturing(true);
                     cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
                     if (ce == cudaSuccess) {
                         iterate_block(x64);
                         ce = cudaStreamEndCapture(s, &gr);
                     }
-                    c->capturing = false;
+                    set_thread_capturing(false);
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
                     size_t nn = 0;
                     if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
@@ -350,7 +352,7 @@ struct CGRun {
             if (e) return e;
         }
         int herr = 0;
-        cudaMemcpyAsync(&herr, c->err_flag, sizeof herr, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&herr, cur_err(c), sizeof herr, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         info->iters = st_h->k;
         info->matvecs += st_h->k;
@@ -393,13 +395,13 @@ hisq_status to_planar(hisq_ctx *c, Workspace &ws, const double *user, int on_dev
         cudaMemcpyAsync(stage, user, (size_t)48 * n, cudaMemcpyHostToDevice, s);
         src = stage;
     }
-    cudaMemsetAsync(c->err_flag, 0, sizeof(int), s);
+    cudaMemsetAsync(cur_err(c), 0, sizeof(int), s);
     {
         LaunchScope ls(c, s, PROF_CONVERT, 96.0 * n);
-        launch_pack_spinor(S_F64, n, src, (char *)planar, c->err_flag, s);
+        launch_pack_spinor(S_F64, n, src, (char *)planar, cur_err(c), s);
     }
     int bad = 0;
-    cudaMemcpyAsync(&bad, c->err_flag, sizeof bad, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&bad, cur_err(c), sizeof bad, cudaMemcpyDeviceToHost, s);
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload");
     if (bad) return fail(c, HISQ_EINVAL, "non-finite input vector");
@@ -469,6 +471,8 @@ void hisq_default_params(hisq_solver_params *p)
     p->reproject = 1;
     p->l = 4;
     p->use_graph = 1;
+    p->nrhs = 1;
+    p->rhs_tile = 0;
     p->stream = nullptr;
 }
 
@@ -484,18 +488,53 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
     hisq_gauge *g = const_cast<hisq_gauge *>(gc);
     cudaStream_t s = pick_stream(c, p->stream);
     const int64_t vh = g->geom.vh;
+    const int nr = p->nrhs;
+    if (nr < 1 || nr > kMaxRHS) return fail(c, HISQ_EINVAL, "nrhs must be in 1..%d", kMaxRHS);
+    if (p->rhs_tile < 0 || p->rhs_tile > kMaxRHS || (p->rhs_tile > 0 && nr % p->rhs_tile))
+        return fail(c, HISQ_EINVAL, "rhs_tile must divide nrhs");
     Workspace ws(c, s);
     double *b64 = nullptr, *x64 = nullptr;
-    e = ws.alloc((size_t)48 * vh, (void **)&b64);
-    if (!e) e = ws.alloc((size_t)48 * vh, (void **)&x64);
-    if (!e) e = to_planar(c, ws, b, p->on_device, vh, b64, s);
-    if (!e && p->use_init_guess) e = to_planar(c, ws, x, p->on_device, vh, x64, s);
-    if (!e && !p->use_init_guess) cudaMemsetAsync(x64, 0, (size_t)48 * vh, s);
+    e = ws.alloc((size_t)48 * vh * nr, (void **)&b64);
+    if (!e) e = ws.alloc((size_t)48 * vh * nr, (void **)&x64);
+    for (int t = 0; t < nr && !e; t++) {
+        e = to_planar(c, ws, b + (size_t)t * 6 * vh, p->on_device, vh, b64 + (size_t)t * 6 * vh, s);
+        if (!e && p->use_init_guess)
+            e = to_planar(c, ws, x + (size_t)t * 6 * vh, p->on_device, vh, x64 + (size_t)t * 6 * vh, s);
+    }
+    if (!e && !p->use_init_guess) cudaMemsetAsync(x64, 0, (size_t)48 * vh * nr, s);
     if (e) return e;
-    const CGConfig cfg = config_from(p, 0.0);
-    hisq_status st = run_cg(c, g, cfg, b64, x64, !p->use_init_guess, info, s);
+    hisq_status st;
+    if (nr == 1) {
+        const CGConfig cfg = config_from(p, 0.0);
+        st = run_cg(c, g, cfg, b64, x64, !p->use_init_guess, info, s);
+    } else {
+        BCGConfig bc;
+        bc.nrhs = nr;
+        for (int t = 0; t < nr; t++) {
+            bc.diag[t] = 4.0 * p->mass * p->mass;
+            bc.tol[t] = p->tol;
+        }
+        bc.sloppy = p->sloppy;
+        bc.nbuf = p->nbuf;
+        bc.maxiter = p->maxiter;
+        bc.pr = p->pr_beta;
+        bc.reproject = p->reproject;
+        bc.use_graph = p->use_graph;
+        bc.tile = p->rhs_tile;
+        bc.delta = p->delta;
+        std::vector<hisq_solve_info> infos(nr);
+        st = run_bcg(c, g, bc, b64, x64, !p->use_init_guess, infos.data(), s);
+        for (int t = 0; t < nr; t++) {
+            info->iters = std::max(info->iters, infos[t].iters);
+            info->matvecs += infos[t].matvecs;
+            info->matvecs_hi += infos[t].matvecs_hi;
+            info->reliable_updates += infos[t].reliable_updates;
+            info->true_residual = std::max(info->true_residual, infos[t].true_residual);
+        }
+    }
     if (st != HISQ_OK && st != HISQ_ENOTCONV && st != HISQ_EBREAKDOWN) return st;
-    e = from_planar(c, ws, x64, vh, x, p->on_device, s);
+    for (int t = 0; t < nr && !e; t++)
+        e = from_planar(c, ws, x64 + (size_t)t * 6 * vh, vh, x + (size_t)t * 6 * vh, p->on_device, s);
     if (e) return e;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st;

@@ -76,16 +76,27 @@ struct Spinor;
 
 template <>
 struct Spinor<S_F64> {
+    static constexpr int chunks = 3;  // 16-byte chunks per site (a tail chunk holds its bytes first)
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) c[k] = ld_cached(reinterpret_cast<const uint4 *>(b) + (size_t)k * n + i);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            v[2 * k] = (real)__hiloint2double((int)c[k].y, (int)c[k].x);
+            v[2 * k + 1] = (real)__hiloint2double((int)c[k].w, (int)c[k].z);
+        }
+    }
     template <typename real>
     __device__ static void load(const char *b, int n, int i, real v[6])
     {
-        const double2 *p = reinterpret_cast<const double2 *>(b);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const double2 d = ld_cached(p + (size_t)c * n + i);
-            v[2 * c] = (real)d.x;
-            v[2 * c + 1] = (real)d.y;
-        }
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -103,12 +114,26 @@ struct Spinor<S_F64> {
 
 template <>
 struct Spinor<S_F32> {
+    static constexpr int chunks = 2;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
+    {
+        c[0] = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        const uint2 t = ld_cached(reinterpret_cast<const uint2 *>(b + (size_t)16 * n) + i);
+        c[1] = make_uint4(t.x, t.y, 0u, 0u);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+        v[0] = __uint_as_float(c[0].x); v[1] = __uint_as_float(c[0].y);
+        v[2] = __uint_as_float(c[0].z); v[3] = __uint_as_float(c[0].w);
+        v[4] = __uint_as_float(c[1].x); v[5] = __uint_as_float(c[1].y);
+    }
     template <typename real>
     __device__ static void load(const char *b, int n, int i, real v[6])
     {
-        const float4 a = ld_cached(reinterpret_cast<const float4 *>(b) + i);
-        const float2 c = ld_cached(reinterpret_cast<const float2 *>(b + (size_t)16 * n) + i);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y;
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -131,15 +156,28 @@ struct Spinor<S_F32> {
 // Sites with max below 2^-110 (32767/max would overflow) are stored as zero.
 template <>
 struct Spinor<S_HALF> {
-    template <typename real>
-    __device__ static void load(const char *b, int n, int i, real v[6])
+    static constexpr int chunks = 1;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
     {
-        const uint4 r = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        (void)n;
+        c[0] = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+        const uint4 r = c[0];
         const float scale = fmul(__uint_as_float(r.w), 1.0f / 32767.0f);
         const float q[6] = {i16lo_to_f(r.x), i16hi_to_f(r.x), i16lo_to_f(r.y),
                             i16hi_to_f(r.y), i16lo_to_f(r.z), i16hi_to_f(r.z)};
 #pragma unroll
         for (int k = 0; k < 6; k++) v[k] = (real)fmul(q[k], scale);
+    }
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -176,11 +214,16 @@ struct Spinor<S_HALF> {
 // plus one, q = rint(v * 2^-(E-127)), bitfields least-significant first.
 template <>
 struct Spinor<S_INT20> {
-    template <typename real>
-    __device__ static void load(const char *b, int n, int i, real v[6])
+    static constexpr int chunks = 1;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
     {
         (void)n;
-        const uint4 w = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        c[0] = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+        const uint4 w = c[0];
         const float up = __uint_as_float((w.w >> 24) << 23);
         const uint32_t u[6] = {w.x,
                                ((w.x >> 20) << 8) | (w.y & 0xffu),
@@ -190,6 +233,13 @@ struct Spinor<S_INT20> {
                                w.w >> 4};
 #pragma unroll
         for (int k = 0; k < 6; k++) v[k] = (real)fmul(i20_to_f(u[k]), up);
+    }
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -228,14 +278,20 @@ struct Spinor<S_INT20> {
 // in FP64: t = max/(2^29-1), 2^(E-127) the power of two just above t.
 template <>
 struct Spinor<S_INT30> {
-    template <typename real>
-    __device__ static void load(const char *b, int n, int i, real v[6])
+    static constexpr int chunks = 2;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
     {
-        const uint4 a = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
-        const uint2 c = ld_cached(reinterpret_cast<const uint2 *>(b + (size_t)16 * n) + i);
+        c[0] = ld_cached(reinterpret_cast<const uint4 *>(b) + i);
+        const uint2 t = ld_cached(reinterpret_cast<const uint2 *>(b + (size_t)16 * n) + i);
+        c[1] = make_uint4(t.x, t.y, 0u, 0u);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+        const uint4 a = c[0];
         const uint32_t E = (a.x >> 30) | ((a.y >> 30) << 2) | ((a.z >> 30) << 4) | ((a.w >> 30) << 6);
         const int32_t q[6] = {sext_bits(a.x, 30), sext_bits(a.y, 30), sext_bits(a.z, 30),
-                              sext_bits(a.w, 30), sext_bits(c.x, 30), sext_bits(c.y, 30)};
+                              sext_bits(a.w, 30), sext_bits(c[1].x, 30), sext_bits(c[1].y, 30)};
         if constexpr (sizeof(real) == 8) {
             const double up = __longlong_as_double((long long)(E + 896u) << 52);  // 2^(E-127)
 #pragma unroll
@@ -245,6 +301,13 @@ struct Spinor<S_INT30> {
 #pragma unroll
             for (int k = 0; k < 6; k++) v[k] = fmul(__int2float_rn(q[k]), up);
         }
+    }
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
     }
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
@@ -319,40 +382,51 @@ template <int GF, int RECON>
 struct Link {
     static constexpr int n16 = link_n16(GF, RECON);
     static constexpr int tail = link_tail(GF, RECON);
+    static constexpr int chunks = n16 + (tail ? 1 : 0);  // the tail chunk holds its 4 or 8 bytes first
 
     // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16)
+    __device__ static void gather(const char *base, size_t pstride, int li, uint4 c[chunks])
+    {
+#pragma unroll
+        for (int k = 0; k < n16; k++) c[k] = ld_stream(reinterpret_cast<const uint4 *>(base + k * pstride) + li);
+        if constexpr (tail == 4) {
+            c[n16] = make_uint4(ld_stream(reinterpret_cast<const unsigned int *>(base + n16 * pstride) + li), 0u, 0u, 0u);
+        } else if constexpr (tail == 8) {
+            const uint2 t = ld_stream(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
+            c[n16] = make_uint4(t.x, t.y, 0u, 0u);
+        }
+    }
+
     template <typename real>
-    __device__ static void load(const char *base, size_t pstride, int li, real U[18])
+    __device__ static void decode(const uint4 c[chunks], real U[18])
     {
         if constexpr (GF == G_F64) {
 #pragma unroll
             for (int k = 0; k < RECON / 2; k++) {
-                const double2 d = ld_stream(reinterpret_cast<const double2 *>(base + k * pstride) + li);
-                U[2 * k] = (real)d.x;
-                U[2 * k + 1] = (real)d.y;
+                U[2 * k] = (real)__hiloint2double((int)c[k].y, (int)c[k].x);
+                U[2 * k + 1] = (real)__hiloint2double((int)c[k].w, (int)c[k].z);
             }
         } else if constexpr (GF == G_F32) {
 #pragma unroll
             for (int k = 0; k < n16; k++) {
-                const float4 d = ld_stream(reinterpret_cast<const float4 *>(base + k * pstride) + li);
-                U[4 * k] = d.x; U[4 * k + 1] = d.y; U[4 * k + 2] = d.z; U[4 * k + 3] = d.w;
+                U[4 * k] = __uint_as_float(c[k].x); U[4 * k + 1] = __uint_as_float(c[k].y);
+                U[4 * k + 2] = __uint_as_float(c[k].z); U[4 * k + 3] = __uint_as_float(c[k].w);
             }
             if constexpr (tail == 8) {
-                const float2 d = ld_stream(reinterpret_cast<const float2 *>(base + n16 * pstride) + li);
-                U[4 * n16] = d.x; U[4 * n16 + 1] = d.y;
+                U[4 * n16] = __uint_as_float(c[n16].x);
+                U[4 * n16 + 1] = __uint_as_float(c[n16].y);
             }
         } else if constexpr (GF == G_FIX16) {
             uint32_t w[RECON / 2];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
-                const uint4 d = ld_stream(reinterpret_cast<const uint4 *>(base + k * pstride) + li);
-                w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
+                w[4 * k] = c[k].x; w[4 * k + 1] = c[k].y; w[4 * k + 2] = c[k].z; w[4 * k + 3] = c[k].w;
             }
             if constexpr (tail == 4) {
-                w[4 * n16] = ld_stream(reinterpret_cast<const unsigned int *>(base + n16 * pstride) + li);
+                w[4 * n16] = c[n16].x;
             } else if constexpr (tail == 8) {
-                const uint2 d = ld_stream(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
-                w[4 * n16] = d.x; w[4 * n16 + 1] = d.y;
+                w[4 * n16] = c[n16].x;
+                w[4 * n16 + 1] = c[n16].y;
             }
 #pragma unroll
             for (int k = 0; k < RECON / 2; k++) {
@@ -368,12 +442,11 @@ struct Link {
             int q[RECON];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
-                const int4 d = ld_stream(reinterpret_cast<const int4 *>(base + k * pstride) + li);
-                q[4 * k] = d.x; q[4 * k + 1] = d.y; q[4 * k + 2] = d.z; q[4 * k + 3] = d.w;
+                q[4 * k] = (int)c[k].x; q[4 * k + 1] = (int)c[k].y; q[4 * k + 2] = (int)c[k].z; q[4 * k + 3] = (int)c[k].w;
             }
             if constexpr (tail == 8) {
-                const int2 d = ld_stream(reinterpret_cast<const int2 *>(base + n16 * pstride) + li);
-                q[4 * n16] = d.x; q[4 * n16 + 1] = d.y;
+                q[4 * n16] = (int)c[n16].x;
+                q[4 * n16 + 1] = (int)c[n16].y;
             }
 #pragma unroll
             for (int k = 0; k < RECON; k++) {
@@ -383,6 +456,14 @@ struct Link {
                     U[k] = __int2float_rn(q[k]);
             }
         }
+    }
+
+    template <typename real>
+    __device__ static void load(const char *base, size_t pstride, int li, real U[18])
+    {
+        uint4 c[chunks];
+        gather(base, pstride, li, c);
+        decode(c, U);
     }
 };
 

@@ -36,6 +36,7 @@ hisq_status fail(hisq_ctx *c, hisq_status s, const char *fmt, ...)
         va_start(ap, fmt);
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
+        std::lock_guard<std::mutex> lk(c->err_mu);
         c->last_error = buf;
     }
     return s;
@@ -46,10 +47,22 @@ hisq_status cuda_fail(hisq_ctx *c, cudaError_t e, const char *what)
     return fail(c, HISQ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+namespace {
+thread_local const Lane *tl_lane = nullptr;
+thread_local bool tl_capturing = false;
+}  // namespace
+
+void set_thread_lane(const Lane *lane) { tl_lane = lane; }
+const RedBuf &cur_red(hisq_ctx *c) { return tl_lane ? tl_lane->red : c->red; }
+int *cur_err(hisq_ctx *c) { return tl_lane ? tl_lane->err : c->err_flag; }
+void set_thread_capturing(bool on) { tl_capturing = on; }
+bool thread_capturing() { return tl_capturing; }
+
 hisq_status ctx_alloc(hisq_ctx *c, size_t bytes, void **p)
 {
     *p = nullptr;
     if (bytes == 0) return HISQ_OK;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     if (c->used + bytes > c->budget)
         return fail(c, HISQ_ENOMEM, "device budget exceeded: %zu + %zu > %zu bytes", c->used, bytes, c->budget);
     const cudaError_t e = cudaMalloc(p, bytes);
@@ -65,6 +78,7 @@ hisq_status ctx_alloc(hisq_ctx *c, size_t bytes, void **p)
 void ctx_free(hisq_ctx *c, void *p, size_t bytes)
 {
     if (!p) return;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     cudaFree(p);
     c->used -= std::min(c->used, bytes);
 }
@@ -81,9 +95,10 @@ bool stream_capturing(cudaStream_t s)
 LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_)
     : c(c_), s(s_), kind(kind_), bytes(bytes_)
 {
-    if (c->capturing) return;  // counted when the graph is replayed
+    if (thread_capturing()) return;  // counted when the graph is replayed
     c->launches += 1;
     if (!c->prof.on || stream_capturing(s)) return;
+    std::lock_guard<std::mutex> lk(c->prof_mu);
     auto take = [&]() {
         cudaEvent_t e;
         if (!c->prof.pool.empty()) {
@@ -103,11 +118,18 @@ LaunchScope::~LaunchScope()
 {
     if (!a) return;
     cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(c->prof_mu);
     c->prof.pending.push_back({a, b, kind, bytes});
-    if (c->prof.pending.size() > 4096) prof_flush(c);
+    if (c->prof.pending.size() > 4096) prof_flush_locked(c);
 }
 
 void prof_flush(hisq_ctx *c)
+{
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    prof_flush_locked(c);
+}
+
+void prof_flush_locked(hisq_ctx *c)
 {
     for (auto &r : c->prof.pending) {
         cudaEventSynchronize(r.b);
@@ -197,6 +219,7 @@ hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, Gauge
 {
     hisq_status st = check_prec(c, p);
     if (st) return st;
+    std::lock_guard<std::mutex> lk(g->copy_mu);
     st = get_copy(c, g, false, p.gauge, p.fat_recon, &v->fat);
     if (st) return st;
     st = get_copy(c, g, true, p.gauge, p.long_recon, &v->lng);
@@ -257,6 +280,7 @@ void hisq_destroy(hisq_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    server_shutdown(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     prof_flush(c);
     for (auto e : c->prof.pool) cudaEventDestroy(e);
@@ -308,7 +332,7 @@ hisq_status hisq_load_gauge(hisq_ctx *c, const int dims[4], const double *fat, c
     const cudaMemcpyKind kind = (flags & HISQ_GAUGE_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(g->fat64, fat, bytes, kind, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->lng64, lng, bytes, kind, c->stream);
-    double *scal = c->red.result;  // 4 scratch doubles: fat max, long max, fat dev, long dev
+    double *scal = cur_red(c).result;  // 4 scratch doubles: fat max, long max, fat dev, long dev
     if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 4 * sizeof(double), c->stream);
     if (e == cudaSuccess) {
         LaunchScope ls(c, c->stream, PROF_CONVERT, 0.0);
@@ -394,7 +418,7 @@ hisq_status hisq_spinor_pack(hisq_ctx *c, int sfmt, int64_t n, const double *in,
         return fail(c, HISQ_EINVAL, "hisq_spinor_pack: bad argument");
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);
-    int *bad = c->err_flag;
+    int *bad = cur_err(c);
     cudaMemsetAsync(bad, 0, sizeof(int), s);
     {
         LaunchScope ls(c, s, PROF_CONVERT, (48.0 + spinor_site_bytes(sfmt)) * n);
@@ -458,15 +482,15 @@ hisq_status hisq_dslash(hisq_ctx *c, const hisq_gauge *gc, hisq_prec prec, int o
         dy = y64;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash upload");
-    cudaMemsetAsync(c->err_flag, 0, sizeof(int), s);
+    cudaMemsetAsync(cur_err(c), 0, sizeof(int), s);
     // the caller's full-lattice array is [even half][odd half]: pack per half
     for (int h = 0; h < nhalf; h++) {
         LaunchScope ls(c, s, PROF_CONVERT, (48.0 + spinor_site_bytes(prec.spinor)) * vh);
-        launch_pack_spinor(prec.spinor, vh, din + h * vh * 6, in_s + h * bs, c->err_flag, s);
-        if (xpay) launch_pack_spinor(prec.spinor, vh, dy + h * vh * 6, y_s + h * bs, c->err_flag, s);
+        launch_pack_spinor(prec.spinor, vh, din + h * vh * 6, in_s + h * bs, cur_err(c), s);
+        if (xpay) launch_pack_spinor(prec.spinor, vh, dy + h * vh * 6, y_s + h * bs, cur_err(c), s);
     }
     int bad_in = 0;
-    cudaMemcpyAsync(&bad_in, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&bad_in, cur_err(c), sizeof(int), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash pack");
     if (bad_in) return fail(c, HISQ_EINVAL, "non-finite input spinor");
@@ -474,8 +498,8 @@ hisq_status hisq_dslash(hisq_ctx *c, const hisq_gauge *gc, hisq_prec prec, int o
         DslashArgs td{};
         td.g = g->geom;
         td.gv = gv;
-        td.err = c->err_flag;
-        td.red = c->red;
+        td.err = cur_err(c);
+        td.red = cur_red(c);
         td.out_parity = 0;
         td.in = in_s;
         td.out = out_s;
@@ -500,8 +524,8 @@ hisq_status hisq_dslash(hisq_ctx *c, const hisq_gauge *gc, hisq_prec prec, int o
         da.sign = xpay ? -1 : 1;
         da.xpay = xpay ? 1 : 0;
         da.active = nullptr;
-        da.err = c->err_flag;
-        da.red = c->red;
+        da.err = cur_err(c);
+        da.red = cur_red(c);
         da.fin = FIN_NONE;
         da.st = nullptr;
         LaunchScope ls(c, s, PROF_STENCIL, (link_b + (xpay ? 3 : 2) * site_b) * vh);
@@ -547,6 +571,6 @@ hisq_status hisq_profile_read(hisq_ctx *c, int kind, hisq_kernel_stats *out)
     return HISQ_OK;
 }
 
-int64_t hisq_launch_count(hisq_ctx *c) { return c ? c->launches : 0; }
+int64_t hisq_launch_count(hisq_ctx *c) { return c ? c->launches.load() : 0; }
 
 }  // extern "C"

@@ -59,19 +59,66 @@ __device__ __forceinline__ void mv_adj_sub(real acc[6], const real U[18], const 
         }
 }
 
-// Launch shapes tried by the tuner: threads per block and the minimum number
-// of resident blocks per SM asked of the register allocator (trading loads in
-// flight per thread against warps per SM): 128/1 (no cap), 128/6 (<= 85
-// registers), 128/8 (<= 64), 256/4 (<= 64), 64/16 (<= 64).
+// Launch shapes tried by the tuner: threads per block, the minimum number of
+// resident blocks per SM asked of the register allocator (loads in flight per
+// thread against warps per SM) and whether the direction loop is unrolled
+// (more overlap across directions against a four times larger kernel body):
+//   0: 128 threads, no cap, unrolled     1: 128, no cap, rolled
+//   2: 128, <= 64 registers, rolled      3: 256, <= 64 registers, rolled
+//   4: 128, <= 64 registers, unrolled
 constexpr int kNumStencilConfigs = 5;
-__host__ __device__ constexpr int stencil_block(int cfg) { return cfg == 3 ? 256 : cfg == 4 ? 64 : 128; }
-__host__ __device__ constexpr int stencil_minb(int cfg)
+__host__ __device__ constexpr bool stencil_config_valid(int cfg, int gf) { return cfg >= 0 && cfg < kNumStencilConfigs && gf >= 0; }
+__host__ __device__ constexpr int stencil_block(int cfg) { return cfg == 3 ? 256 : 128; }
+__host__ __device__ constexpr int stencil_minb(int cfg) { return cfg == 2 ? 8 : cfg == 3 ? 4 : cfg == 4 ? 8 : 1; }
+__host__ __device__ constexpr bool stencil_unrolled(int cfg) { return cfg == 0 || cfg == 4; }
+
+// One direction mu of the stencil at site x (coordinates c, lex), accumulated
+// into accf (fat terms) and accl (long terms).
+template <int GF, int SF, typename real, int LREC>
+__device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, int cmu, int c3, int lex, int cb,
+                                                  int po, size_t pstride, real lsc, int phase_sum, real accf[6],
+                                                  real accl[6])
 {
-    return cfg == 1 ? 6 : cfg == 2 ? 8 : cfg == 3 ? 4 : cfg == 4 ? 16 : 1;
+    const Geom &g = a.g;
+    const int vh = g.vh, pi = 1 - po;
+    const int L = g.L[mu], st = g.stride[mu];
+    const int cp1 = wrap_coord(cmu + 1, L), cm1 = wrap_coord(cmu - 1, L);
+    const int cp3 = wrap_coord(cmu + 3, L), cm3 = wrap_coord(cmu - 3, L);
+    const int base = lex - cmu * st;
+    const int np1 = (base + cp1 * st) >> 1, nm1 = (base + cm1 * st) >> 1;
+    const int np3 = (base + cp3 * st) >> 1, nm3 = (base + cm3 * st) >> 1;
+    real U[18], s[6];
+
+    Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
+    Spinor<SF>::load(a.in, vh, np1, s);
+    mv_add(accf, U, s);
+
+    Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
+    Spinor<SF>::load(a.in, vh, nm1, s);
+    mv_adj_sub(accf, U, s);
+
+    // row 2 of an r12 link in the units of the accumulated sum: sign * lsc * conj(row0 x row1)
+    const real eta = (phase_sum & 1) ? -lsc : lsc;
+    Link<GF, LREC>::load(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
+    if constexpr (LREC == 12) {
+        const bool flip = g.antiperiodic_t && mu == 3 && c3 + 3 >= L;
+        rebuild_row2(U, flip ? -eta : eta);
+    }
+    Spinor<SF>::load(a.in, vh, np3, s);
+    mv_add(accl, U, s);
+
+    Link<GF, LREC>::load(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
+    if constexpr (LREC == 12) {
+        const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
+        rebuild_row2(U, flip ? -eta : eta);
+    }
+    Spinor<SF>::load(a.in, vh, nm3, s);
+    mv_adj_sub(accl, U, s);
 }
 
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
-__global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG)) dslash_kernel(const DslashArgs a)
+__global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
+    dslash_kernel(const __grid_constant__ DslashArgs a)
 {
     if (a.active != nullptr && *(volatile const int *)a.active == 0) return;  // uniform over the grid
     const Geom &g = a.g;
@@ -97,45 +144,23 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG)) dslash_
         const int lex = 2 * cb + (x & 1);
         real accf[6] = {0, 0, 0, 0, 0, 0};
         real accl[6] = {0, 0, 0, 0, 0, 0};
-        int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
-
+        if constexpr (stencil_unrolled(CFG)) {
+            int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            const int L = g.L[mu], st = g.stride[mu];
-            const int cp1 = wrap_coord(c[mu] + 1, L), cm1 = wrap_coord(c[mu] - 1, L);
-            const int cp3 = wrap_coord(c[mu] + 3, L), cm3 = wrap_coord(c[mu] - 3, L);
-            const int base = lex - c[mu] * st;
-            const int np1 = (base + cp1 * st) >> 1, nm1 = (base + cm1 * st) >> 1;
-            const int np3 = (base + cp3 * st) >> 1, nm3 = (base + cm3 * st) >> 1;
-            real U[18], s[6];
-
-            Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
-            Spinor<SF>::load(a.in, vh, np1, s);
-            mv_add(accf, U, s);
-
-            Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
-            Spinor<SF>::load(a.in, vh, nm1, s);
-            mv_adj_sub(accf, U, s);
-
-            // row 2 of an r12 link in the units of the accumulated sum: sign * lsc * conj(row0 x row1)
-            const real eta = (phase_sum & 1) ? -lsc : lsc;
-            Link<GF, LREC>::load(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
-            if constexpr (LREC == 12) {
-                const bool flip = g.antiperiodic_t && mu == 3 && c[3] + 3 >= L;
-                rebuild_row2(U, flip ? -eta : eta);
+            for (int mu = 0; mu < 4; mu++) {
+                stencil_direction<GF, SF, real, LREC>(a, mu, c[mu], t, lex, cb, po, pstride, lsc, phase_sum, accf,
+                                                      accl);
+                phase_sum += c[mu];
             }
-            Spinor<SF>::load(a.in, vh, np3, s);
-            mv_add(accl, U, s);
-
-            Link<GF, LREC>::load(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
-            if constexpr (LREC == 12) {
-                const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
-                rebuild_row2(U, flip ? -eta : eta);
+        } else {
+            int phase_sum = 0;
+#pragma unroll 1
+            for (int mu = 0; mu < 4; mu++) {
+                const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+                stencil_direction<GF, SF, real, LREC>(a, mu, cmu, t, lex, cb, po, pstride, lsc, phase_sum, accf,
+                                                      accl);
+                phase_sum += cmu;
             }
-            Spinor<SF>::load(a.in, vh, nm3, s);
-            mv_adj_sub(accl, U, s);
-
-            phase_sum += c[mu];
         }
 
         const real sf = (real)a.sign * fsc, sl = (real)a.sign * lsc;
@@ -149,13 +174,19 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG)) dslash_
 #pragma unroll
             for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
             if constexpr (RED) {
+                // one site's terms in the compute precision (FP64 arithmetic
+                // is scarce on GB300); sites are summed in FP64
+                real d = 0;
 #pragma unroll
-                for (int k = 0; k < 6; k++) rv[0] += (double)yv[k] * (double)o[k];
+                for (int k = 0; k < 6; k++) d += yv[k] * o[k];
+                rv[0] = (double)d;
             }
         }
         if constexpr (RED) {
+            real n2 = 0;
 #pragma unroll
-            for (int k = 0; k < 6; k++) rv[1] += (double)o[k] * (double)o[k];
+            for (int k = 0; k < 6; k++) n2 += o[k] * o[k];
+            rv[1] = (double)n2;
         }
         if (!Spinor<SF>::store(a.out, vh, cb, o)) atomicExch(a.err, 1);
     }

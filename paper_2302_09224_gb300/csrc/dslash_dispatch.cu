@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -47,8 +48,12 @@ TuneKey key_of(int gf, int sf, int cf, int lrec, const Geom &g)
 
 }  // namespace
 
+std::atomic<int> forced_config{-1};
+
 int stencil_config(int gf, int sf, int cf, int lrec, const Geom &g)
 {
+    const int f = forced_config.load();
+    if (f >= 0 && stencil_config_valid(f, gf)) return f;
     std::lock_guard<std::mutex> lk(tune_mu);
     auto it = tune_cache.find(key_of(gf, sf, cf, lrec, g));
     return it == tune_cache.end() ? 0 : it->second;
@@ -78,6 +83,7 @@ void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaS
     int best = 0;
     float best_ms = 1e30f;
     for (int cfg = 0; cfg < kNumStencilConfigs; cfg++) {
+        if (!stencil_config_valid(cfg, gf)) continue;
         launch_with(gf, sf, cf, lrec, false, cfg, a, s);  // warm
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3; r++) launch_with(gf, sf, cf, lrec, false, cfg, a, s);
@@ -117,3 +123,9 @@ bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int
 }
 
 }  // namespace hisq
+
+extern "C" int hisq_stencil_config(int cfg)
+{
+    if (cfg < -1 || cfg >= hisq::kNumStencilConfigs) return -2;
+    return hisq::forced_config.exchange(cfg);
+}

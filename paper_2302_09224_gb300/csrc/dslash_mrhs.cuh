@@ -112,17 +112,22 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
             if (a.xpay) {
                 real yv[6];
                 Spinor<SF>::load(a.y + off, vh, cb, yv);
-                const real aa = (real)a.a[a.t0 + j];
+                // a solver's per-system coefficient lives in its state (slots change hands)
+                const real aa = a.st ? (real)a.st[a.t0 + j].diag : (real)a.a[a.t0 + j];
 #pragma unroll
                 for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
                 if constexpr (RED) {
+                    real d = 0;
 #pragma unroll
-                    for (int k = 0; k < 6; k++) rv[2 * j] += (double)yv[k] * (double)o[k];
+                    for (int k = 0; k < 6; k++) d += yv[k] * o[k];
+                    rv[2 * j] = (double)d;
                 }
             }
             if constexpr (RED) {
+                real n2 = 0;
 #pragma unroll
-                for (int k = 0; k < 6; k++) rv[2 * j + 1] += (double)o[k] * (double)o[k];
+                for (int k = 0; k < 6; k++) n2 += o[k] * o[k];
+                rv[2 * j + 1] = (double)n2;
             }
             if (!Spinor<SF>::store(a.out + off, vh, cb, o)) atomicExch(a.err, 1);
         }

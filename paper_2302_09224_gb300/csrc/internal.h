@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -89,6 +90,7 @@ struct CGState {
     double hi_rr;       // |r_hi|^2 of the last true residual
     double proj_re, proj_im;  // projection coefficient of p onto r_hi
     double coef_re, coef_im;  // p <- coef * r_hi + beta * p at a reliable update
+    double diag;        // 4 m^2 + sigma of this system (read by the batched stencil)
     int active;         // kernels of an iteration run only while 1
     int reason;         // why the iteration stopped (REASON_*)
     int k;              // iterations done
@@ -236,9 +238,13 @@ struct hisq_gauge {
     double fat_max = 0, lng_max = 0;
     bool fat_r12_ok = false, lng_r12_ok = false;
     std::vector<hisq::LinkCopy> fat_copies, lng_copies;
+    std::mutex copy_mu;        // lazily built reduced-format copies
 };
 
 namespace hisq {
+struct Server;  // request loop (serve.cu)
+void server_shutdown(hisq_ctx *c);
+
 // Optional per-launch timing (benchmarks): launches made outside graph
 // capture are bracketed by CUDA events on their own stream.
 enum ProfKind { PROF_STENCIL = 0, PROF_STENCIL_HI = 1, PROF_BLAS = 2, PROF_CONVERT = 3, PROF_NKIND = 4 };
@@ -270,12 +276,28 @@ struct hisq_ctx {
     // scratch fields used by hisq_dslash (grown on demand)
     char *scratch = nullptr;
     size_t scratch_bytes = 0;
-    int64_t launches = 0;            // kernels launched (graph replays count their nodes)
-    bool capturing = false;          // a solver is recording a graph on its stream
+    std::atomic<int64_t> launches{0};  // kernels launched (graph replays count their nodes)
+    std::mutex alloc_mu;               // device allocations and lazily built gauge copies
+    std::mutex err_mu;                 // last_error
+    hisq::Server *server = nullptr;    // request loop, started by the first hisq_submit
+    std::mutex prof_mu;
     hisq::Profiler prof;
 };
 
 namespace hisq {
+
+// Per-thread execution state.  A worker thread of the request loop runs its
+// solves with its own reduction buffer and error flag (its "lane"); every
+// other thread uses the context's.  Graph capture is per thread as well.
+struct Lane {
+    RedBuf red;
+    int *err;
+};
+void set_thread_lane(const Lane *lane);
+const RedBuf &cur_red(hisq_ctx *c);
+int *cur_err(hisq_ctx *c);
+void set_thread_capturing(bool on);
+bool thread_capturing();
 
 // status helpers (context.cu)
 hisq_status fail(hisq_ctx *c, hisq_status s, const char *fmt, ...);
@@ -295,6 +317,7 @@ struct LaunchScope {
     ~LaunchScope();
 };
 void prof_flush(hisq_ctx *c);   // resolve pending event pairs (synchronises on them)
+void prof_flush_locked(hisq_ctx *c);
 bool stream_capturing(cudaStream_t s);
 
 // A validated triplet: returns HISQ_OK and the device view of the gauge copy.

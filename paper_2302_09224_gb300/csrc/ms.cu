@@ -195,8 +195,8 @@ struct MSRun {
         a.acc_bytes = accb;
         a.x64 = X;
         a.m = m;
-        a.err = c->err_flag;
-        a.red = c->red;
+        a.err = cur_err(c);
+        a.red = cur_red(c);
         return a;
     }
 
@@ -226,8 +226,8 @@ struct MSRun {
         mv_hi++;
         BlasArgs b{};
         b.n = vh;
-        b.err = c->err_flag;
-        b.red = c->red;
+        b.err = cur_err(c);
+        b.red = cur_red(c);
         b.b64 = b64;
         b.ax64 = ax64;
         b.r64 = r64;
@@ -249,8 +249,8 @@ struct MSRun {
             apply_mee(c, g->geom, p.sloppy, gv_s, diag0, pf(0), tmp_s, w_s, FIN_MS_ALPHA, m, 0, act, PROF_STENCIL, s);
             BlasArgs b{};
             b.n = vh;
-            b.err = c->err_flag;
-            b.red = c->red;
+            b.err = cur_err(c);
+            b.red = cur_red(c);
             b.v0 = r_s;
             b.v1 = w_s;
             b.active = act;
@@ -314,19 +314,19 @@ struct MSRun {
         // r = p_i = b
         {
             LaunchScope ls(c, s, PROF_CONVERT, (48.0 + spinor_site_bytes(p.sloppy.spinor)) * vh);
-            launch_convert(S_F64, p.sloppy.spinor, vh, (const char *)b64, r_s, c->err_flag, s);
+            launch_convert(S_F64, p.sloppy.spinor, vh, (const char *)b64, r_s, cur_err(c), s);
         }
         for (int i = 0; i < ns; i++) cudaMemcpyAsync(pf(i), r_s, sb, cudaMemcpyDeviceToDevice, s);
         {
             BlasArgs a{};
             a.n = vh;
-            a.red = c->red;
+            a.red = cur_red(c);
             a.x64 = const_cast<double *>(b64);
             LaunchScope ls(c, s, PROF_BLAS, 48.0 * vh);
             launch_norm2(a, s);
         }
         double bb = 0;
-        cudaMemcpyAsync(&bb, c->red.result, sizeof bb, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&bb, cur_red(c).result, sizeof bb, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "norm");
         if (!std::isfinite(bb)) return fail(c, HISQ_EINVAL, "non-finite right-hand side");
         info->nshift = ns;
@@ -363,13 +363,13 @@ struct MSRun {
             if (graph) {
                 if (!exec) {
                     cudaGraph_t gr = nullptr;
-                    c->capturing = true;
+                    set_thread_capturing(true);
                     cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
                     if (ce == cudaSuccess) {
                         iterate_block(N);
                         ce = cudaStreamEndCapture(s, &gr);
                     }
-                    c->capturing = false;
+                    set_thread_capturing(false);
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
                     size_t nn = 0;
                     if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
@@ -409,7 +409,7 @@ struct MSRun {
         for (int i = 0; i < ns; i++) {
             residual(i, FIN_STORE, nullptr);
             double rr = 0;
-            cudaMemcpyAsync(&rr, c->red.result, sizeof rr, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&rr, cur_red(c).result, sizeof rr, cudaMemcpyDeviceToHost, s);
             if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "residual");
             rs[i] = std::sqrt(rr / bb);
             info->shift_resid_ms[i] = rs[i];

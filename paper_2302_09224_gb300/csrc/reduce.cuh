@@ -63,13 +63,25 @@ __device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
+    // every block's partials: coherent L2 loads (ld.cg), U rows per thread in
+    // flight at once (one L2 round trip per U rows); the order is fixed
+    constexpr int U = NR <= 4 ? 8 : NR <= 8 ? 4 : 1;
     double w[NR];
 #pragma unroll
     for (int k = 0; k < NR; k++) w[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const volatile double *p = rb.partials + (size_t)b * NR;
+    const unsigned step = blockDim.x;
+    for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * step) {
+        double tmp[U][NR];
 #pragma unroll
-        for (int k = 0; k < NR; k++) w[k] += p[k];
+        for (int u = 0; u < U; u++) {
+            const unsigned b = b0 + u * step;
+#pragma unroll
+            for (int k = 0; k < NR; k++) tmp[u][k] = b < nblocks ? __ldcg(rb.partials + (size_t)b * NR + k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int k = 0; k < NR; k++) w[k] += tmp[u][k];
     }
     block_sum<NR>(w, sh);
     if (threadIdx.x == 0) {

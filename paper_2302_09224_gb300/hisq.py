@@ -61,7 +61,8 @@ class hisq_solver_params(ctypes.Structure):
                 ("delta", ctypes.c_double), ("sloppy", hisq_prec), ("refine", hisq_prec),
                 ("nbuf", ctypes.c_int32), ("use_init_guess", ctypes.c_int32), ("on_device", ctypes.c_int32),
                 ("pr_beta", ctypes.c_int32), ("reproject", ctypes.c_int32), ("l", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("use_graph", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class hisq_solve_info(ctypes.Structure):
@@ -72,6 +73,22 @@ class hisq_solve_info(ctypes.Structure):
                 ("shift_resid_ms", ctypes.c_double * HISQ_MAX_SHIFTS),
                 ("shift_resid", ctypes.c_double * HISQ_MAX_SHIFTS),
                 ("refine_iters", ctypes.c_int32 * HISQ_MAX_SHIFTS)]
+
+
+HISQ_REQ_CG, HISQ_REQ_MULTISHIFT = 0, 1
+
+
+class hisq_request(ctypes.Structure):
+    _fields_ = [("gauge", ctypes.c_void_p), ("kind", ctypes.c_int32), ("mass", ctypes.c_double),
+                ("tol", ctypes.c_double), ("nshift", ctypes.c_int32), ("sigma", ctypes.c_void_p),
+                ("shift_tol", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32), ("sloppy", hisq_prec), ("refine", hisq_prec),
+                ("maxiter", ctypes.c_int32)]
+
+
+class hisq_serve_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("pending", ctypes.c_int64), ("latency_p50_s", ctypes.c_double),
+                ("latency_p99_s", ctypes.c_double), ("solves_per_s", ctypes.c_double)]
 
 
 class hisq_kernel_stats(ctypes.Structure):
@@ -109,12 +126,17 @@ _SIGS = {
     "hisq_profile_reset": (None, [_P]),
     "hisq_profile_read": (_I, [_P, _I, ctypes.POINTER(hisq_kernel_stats)]),
     "hisq_launch_count": (_I64, [_P]),
+    "hisq_stencil_config": (_I, [_I]),
     "hisq_default_params": (None, [ctypes.POINTER(hisq_solver_params)]),
     "hisq_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P, ctypes.POINTER(hisq_solve_info)]),
     "hisq_multishift_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _I, _P, _P, _P, _P,
                                 ctypes.POINTER(hisq_solve_info)]),
     "hisq_bicgstabl": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P,
                             ctypes.POINTER(hisq_solve_info)]),
+    "hisq_submit": (_I, [_P, ctypes.POINTER(hisq_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "hisq_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(hisq_solve_info)]),
+    "hisq_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(hisq_solve_info)]),
+    "hisq_serve_stats": (_I, [_P, ctypes.POINTER(hisq_serve_stats_t)]),
 }
 
 
@@ -264,6 +286,10 @@ def hisq_profile_read(ctx, kind: int) -> hisq_kernel_stats:
     return s
 
 
+def hisq_stencil_config(cfg: int) -> int:
+    return int(lib().hisq_stencil_config(int(cfg)))
+
+
 def hisq_launch_count(ctx) -> int:
     return int(lib().hisq_launch_count(ctx))
 
@@ -301,3 +327,57 @@ def hisq_bicgstabl(ctx, g, params: hisq_solver_params, b, x) -> tuple[int, hisq_
     if st not in (HISQ_OK, HISQ_ENOTCONV):
         _check(ctx, st)
     return st, info
+
+
+def hisq_submit(ctx, gauge, kind: int, mass: float, b, x, on_device: bool, tol: float = 1e-10, sigma=None,
+                shift_tol=None, sloppy: hisq_prec | None = None, refine: hisq_prec | None = None,
+                maxiter: int = 100000) -> int:
+    """Queue a solve; returns its ticket.  b and x must stay alive until it is done."""
+    r = hisq_request()
+    r.gauge = gauge
+    r.kind = int(kind)
+    r.mass = float(mass)
+    r.tol = float(tol)
+    keep = []
+    if kind == HISQ_REQ_MULTISHIFT:
+        n = len(sigma)
+        sa = (ctypes.c_double * n)(*[float(v) for v in sigma])
+        ta = (ctypes.c_double * n)(*[float(v) for v in shift_tol])
+        keep += [sa, ta]
+        r.nshift = n
+        r.sigma = ctypes.cast(sa, ctypes.c_void_p)
+        r.shift_tol = ctypes.cast(ta, ctypes.c_void_p)
+    r.b = _ptr(b)
+    r.x = _ptr(x)
+    r.on_device = int(bool(on_device))
+    r.sloppy = sloppy if sloppy is not None else prec("int20")
+    r.refine = refine if refine is not None else prec("int20")
+    r.maxiter = int(maxiter)
+    t = ctypes.c_uint64(0)
+    _check(ctx, lib().hisq_submit(ctx, ctypes.byref(r), ctypes.byref(t)))
+    return int(t.value)
+
+
+def hisq_poll(ctx, ticket: int):
+    """(done, status, info); status is the solve's once done."""
+    done = ctypes.c_int(0)
+    info = hisq_solve_info()
+    st = lib().hisq_poll(ctx, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(info))
+    if st in (HISQ_EINVAL, HISQ_ENOTFOUND):
+        _check(ctx, st)
+    return bool(done.value), st, info
+
+
+def hisq_wait(ctx, ticket: int, timeout_s: float = 60.0):
+    """(status, info) once done; raises HisqError on ETIMEOUT or an unknown ticket."""
+    info = hisq_solve_info()
+    st = lib().hisq_wait(ctx, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(info))
+    if st in (HISQ_ETIMEOUT, HISQ_ENOTFOUND, HISQ_EINVAL):
+        _check(ctx, st)
+    return st, info
+
+
+def hisq_serve_stats(ctx) -> hisq_serve_stats_t:
+    s = hisq_serve_stats_t()
+    _check(ctx, lib().hisq_serve_stats(ctx, ctypes.byref(s)))
+    return s

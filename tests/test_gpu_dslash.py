@@ -198,3 +198,18 @@ def test_full_size_sampled(ctx, orc, name):
         hisq.hisq_free_gauge(ctx, g)
         del fat, lng
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("cfg", range(5))
+@pytest.mark.parametrize("name", ["int20", "half", "f32", "f64"])
+def test_every_launch_shape(ctx, orc, cfg, name):
+    """Each stencil launch shape the tuner may pick gives the same parity (ragged and aliased lattices)."""
+    prev = hisq.hisq_stencil_config(cfg)
+    try:
+        for dims, anti, parity, a in [((6, 4, 4, 10), True, 2, 0.4), ((2, 2, 2, 2), False, 1, 0.0)]:
+            fat, lng = lattice(dims, anti)
+            x, y, out = run_gpu(ctx, dims, anti, name, 12, parity, a)
+            exact = oracle_apply(orc, dims, fat, lng, parity, a, x, y)
+            assert rel(out, exact) <= BOUND_EXACT[name], (cfg, name, dims)
+    finally:
+        hisq.hisq_stencil_config(prev)

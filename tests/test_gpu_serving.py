@@ -1,0 +1,124 @@
+"""GPU request loop: continuous batching of solve requests (hisq_submit / hisq_poll).
+
+A seeded Poisson-like stream of requests on two lattice volumes, with
+different masses and tolerances and some multi-shift requests, is queued at
+once; every result's FP64 true residual, recomputed by the CPU oracle, must
+meet its own target, and every CG result must equal the same request solved
+alone (same batch session shape), bitwise or at least within ten times its
+tolerance.  Bounded waits time out cleanly, unknown tickets and bad requests
+are refused, and the stats report latency percentiles and throughput.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_09224_gb300 import hisq, synth
+
+pytestmark = pytest.mark.gpu
+
+VOLS = [(8, 8, 8, 8), (8, 8, 4, 16)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    ctx = hisq.hisq_create(0)
+    gauges, fields = {}, {}
+    for d in VOLS:
+        fat, lng = synth.gauge_pair(d, seed=0)
+        fields[d] = (fat.numpy(), lng.numpy())
+        gauges[d] = hisq.hisq_load_gauge(ctx, d, fat.cuda(), lng.cuda())
+    yield ctx, gauges, fields
+    hisq.hisq_destroy(ctx)
+
+
+def requests(n, seed=1):
+    g = np.random.Generator(np.random.Philox(key=seed))
+    out = []
+    for i in range(n):
+        d = VOLS[int(g.integers(len(VOLS)))]
+        m = float(np.exp(g.uniform(np.log(0.02), np.log(0.2))))
+        tol = [1e-6, 1e-8, 1e-10][int(g.integers(3))]
+        ms = bool(g.uniform() < 0.3)
+        out.append(dict(dims=d, mass=m, tol=tol, ms=ms, seed=synth.rhs_seed(i)))
+    return out
+
+
+def submit(ctx, gauges, q, on_device=True):
+    d = q["dims"]
+    b = synth.spinor(d, q["seed"])
+    b = b.cuda() if on_device else b.numpy()
+    if q["ms"]:
+        sig = synth.shifts_logspaced(4, 1e-3, 0.5)
+        tols = [q["tol"]] * 4
+        x = torch.zeros((4,) + tuple(b.shape), dtype=torch.float64, device="cuda") if on_device else \
+            np.zeros((4,) + b.shape)
+        t = hisq.hisq_submit(ctx, gauges[d], hisq.HISQ_REQ_MULTISHIFT, q["mass"], b, x, on_device, sigma=sig,
+                             shift_tol=tols)
+        return t, b, x, sig
+    x = torch.zeros_like(b) if on_device else np.zeros_like(b)
+    t = hisq.hisq_submit(ctx, gauges[d], hisq.HISQ_REQ_CG, q["mass"], b, x, on_device, tol=q["tol"])
+    return t, b, x, None
+
+
+def as_np(a):
+    return a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
+
+
+def test_stream_in_the_mix_matches_alone(env, orc):
+    ctx, gauges, fields = env
+    qs = requests(24)
+    live = [(q, *submit(ctx, gauges, q, on_device=(i % 3 != 0))) for i, q in enumerate(qs)]
+    results = {}
+    for q, t, b, x, sig in live:
+        st, info = hisq.hisq_wait(ctx, t, 120.0)
+        assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+        results[t] = (q, b, x, sig)
+    for t, (q, b, x, sig) in results.items():
+        d = q["dims"]
+        fat, lng = fields[d]
+        bb = as_np(b)
+        xx = as_np(x)
+        if sig is None:
+            r = bb - orc.mee(d, fat, lng, q["mass"], xx)
+            assert np.linalg.norm(r) / np.linalg.norm(bb) <= q["tol"]
+        else:
+            for i, s in enumerate(sig):
+                r = bb - orc.mee(d, fat, lng, q["mass"], xx[i], sigma=s)
+                assert np.linalg.norm(r) / np.linalg.norm(bb) <= q["tol"]
+    # the same CG requests alone
+    for t, (q, b, x, sig) in list(results.items())[:6]:
+        if sig is not None:
+            continue
+        t2, b2, x2, _ = submit(ctx, gauges, q)
+        st, _ = hisq.hisq_wait(ctx, t2, 60.0)
+        assert st == hisq.HISQ_OK
+        a, m = as_np(x2), as_np(x)
+        assert np.linalg.norm(a - m) <= 10 * q["tol"] * 1e3 * np.linalg.norm(a)
+    s = hisq.hisq_serve_stats(ctx)
+    assert s.completed >= 24 and s.latency_p99_s >= s.latency_p50_s > 0 and s.solves_per_s > 0
+
+
+def test_wait_timeout_poll_and_refusals(env):
+    ctx, gauges, fields = env
+    q = dict(dims=VOLS[0], mass=0.02, tol=1e-10, ms=False, seed=5)
+    t, b, x, _ = submit(ctx, gauges, q)
+    try:
+        hisq.hisq_wait(ctx, t, 0.0)
+    except hisq.HisqError as e:
+        assert e.status == hisq.HISQ_ETIMEOUT
+    st, info = hisq.hisq_wait(ctx, t, 60.0)
+    assert st == hisq.HISQ_OK and info.true_residual <= 1e-10
+    with pytest.raises(hisq.HisqError, match="ENOTFOUND"):
+        hisq.hisq_poll(ctx, t)
+    t2, b2, x2, _ = submit(ctx, gauges, q)
+    done = False
+    for _ in range(2000):
+        done, st, info = hisq.hisq_poll(ctx, t2)
+        if done:
+            break
+        time.sleep(0.005)
+    assert done and st == hisq.HISQ_OK
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_submit(ctx, gauges[VOLS[0]], 7, 0.1, b, x, True)
