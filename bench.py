@@ -388,6 +388,34 @@ def run_stencil_only(args):
     return 0
 
 
+def run_solve_only(args):
+    """One short mixed-precision CG solve on a small lattice (the small case for ncu captures of the solver's kernels)."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims = tuple(int(v) for v in args.solve.split(","))
+    if args.stencil_config >= 0:
+        hisq.hisq_stencil_config(args.stencil_config)
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    del fat, lng
+    b = synth.spinor(dims, synth.rhs_seed(0), device="cuda")
+    x = torch.zeros_like(b)
+    p = hisq.hisq_default_params()
+    p.mass, p.tol, p.delta, p.on_device = MASS, TOL, DELTA, 1
+    p.sloppy = hisq.prec(args.prec, 12)
+    p.maxiter = args.maxiter
+    st, info = hisq.hisq_cg(ctx, g, p, b, x)
+    torch.cuda.synchronize()
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    print(json.dumps({"solve": list(dims), "prec": args.prec, "maxiter": args.maxiter,
+                      "status": hisq.STATUS_NAMES.get(st, st), "iters": info.iters}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,9 +433,13 @@ def main():
     ap.add_argument("--prec", default="int20")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--stencil-config", type=int, default=-1, help="force a stencil launch shape (0..4)")
+    ap.add_argument("--solve", default=None, help="LX,LY,LZ,LT: only one short CG solve (profiling)")
+    ap.add_argument("--maxiter", type=int, default=20)
     args = ap.parse_args()
     if args.stencil:
         return run_stencil_only(args)
+    if args.solve:
+        return run_solve_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -53,9 +53,9 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) b_r_update_kernel(BBArgs a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[2 * kMaxRHS];
+    real v[2 * kMaxRHS];
 #pragma unroll
-    for (int k = 0; k < 2 * kMaxRHS; k++) v[k] = 0.0;
+    for (int k = 0; k < 2 * kMaxRHS; k++) v[k] = 0;
     if (i < a.n) {
 #pragma unroll
         for (int t = 0; t < kMaxRHS; t++) {
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kBlock) b_r_update_kernel(BBArgs a)
                 d += rn * r[k];
                 r[k] = rn;
             }
-            v[2 * t] = (double)n2;
-            v[2 * t + 1] = (double)d;
+            v[2 * t] = n2;
+            v[2 * t + 1] = d;
             if (!Spinor<SF>::store(rf, a.n, i, r)) atomicExch(a.err, 1);
         }
     }
@@ -176,7 +176,7 @@ int tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
         for (int T = 1; T <= 16; T *= 2) {
-            if (nrhs % T) continue;
+            if (nrhs % T || !red_fits(geom.vh, kMrhsBlock, 2 * T)) continue;
             launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, d, s);
             cudaEventRecord(e0, s);
             for (int r = 0; r < 2; r++) launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, d, s);
@@ -374,6 +374,8 @@ hisq_status BatchSession::setup()
     diag.assign(nr, 0.0);
     T = cfg.tile > 0 ? cfg.tile : tune_tile(c, g->geom, cfg.sloppy, gv_s, nr, ap_s, tmp_s, fb, s);
     if (nr % T) return fail(c, HISQ_EINVAL, "RHS tile %d does not divide nrhs %d", T, nr);
+    if (!red_fits(vh, kMrhsBlock, 2 * T) || !red_fits(vh, kBlock, 2 * kMaxRHS))
+        return fail(c, HISQ_EINVAL, "lattice too large for a batched reduction over a tile of %d", T);
     tune_stencil(c, g->geom, prec_f64(), gv_d, (char *)ax64, (char *)tmp64, s);
     cudaMemsetAsync(ring, 0, fb * nr * N, s);
     cudaMemsetAsync(r_s, 0, fb * nr, s);

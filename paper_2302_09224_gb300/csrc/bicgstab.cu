@@ -150,12 +150,12 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, con
 {
     if (skip(a.active)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {0.0, 0.0, 0.0};
+    real v[3] = {0, 0, 0};
     if (s < a.vh) {
         real xv[6], yv[6];
         Spinor<SF>::load(half(x, a.hb), a.vh, s, xv);
         Spinor<SF>::load(half(y, a.hb), a.vh, s, yv);
-        real d0 = 0, d1 = 0, d2 = 0;  // one site in the compute precision; sites summed in FP64
+        real d0 = 0, d1 = 0, d2 = 0;  // one site in the compute precision (see reduce_grid)
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const real xr = xv[2 * c], xi = xv[2 * c + 1], yr = yv[2 * c], yi = yv[2 * c + 1];
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
 {
     if (skip(a.active)) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {0.0, 0.0, 0.0};
+    real v[3] = {0, 0, 0};
     if (s < a.vh) {
         real rj[6], ri[6];
         char *rjf = half(a.R + a.j * a.fb, a.hb);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const BState *b = a.b;
     const int l = b->l;
-    double v[1] = {0.0};
+    real v[1] = {0};
     if (s < a.vh) {
         // updates in the compute precision; x's increment is added in FP64
         real dx[6] = {0, 0, 0, 0, 0, 0}, r0[6], u0[6], t[6];
@@ -692,6 +692,7 @@ extern "C" hisq_status hisq_bicgstabl(hisq_ctx *c, const hisq_gauge *gc, const h
     hisq_gauge *g = const_cast<hisq_gauge *>(gc);
     cudaStream_t s = pick_stream(c, p->stream);
     const int64_t vh = g->geom.vh;
+    if (!solver_red_fits(vh)) return fail(c, HISQ_EINVAL, "lattice too large for the solvers' reductions");
     Workspace ws(c, s);
     double *b64 = nullptr, *x64 = nullptr;
     e = ws.alloc((size_t)96 * vh, (void **)&b64);

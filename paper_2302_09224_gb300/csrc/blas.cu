@@ -1,6 +1,7 @@
 // blas.cu -- fused BLAS-1 kernels of the stabilised mixed-precision CG
 // (Sec. 3.1), each a single pass over its vectors in the sloppy storage
-// format with the reduction it needs fused in (deterministic, FP64):
+// format with the reduction it needs fused in (deterministic; see reduce_grid
+// for the precision of each stage):
 //   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta)
 //   p_update      p' <- r + beta p       (into the next ring slot)
 //   x_flush       x_hi <- x_hi + sum_j alpha_j p_j   (buffered gradient vectors)
@@ -30,22 +31,22 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 {
     if (skip(a.active)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[2] = {0.0, 0.0};
-    if (i < a.n) {
+    real v[2] = {0, 0};
+    const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
+    // one wave of blocks loops over the sites (see wave_blocks)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         real r[6], ap[6], rn[6];
         Spinor<SF>::load(a.v0, a.n, i, r);
         Spinor<SF>::load(a.v1, a.n, i, ap);
-        const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
-        real n2 = 0, d = 0;  // per-site terms in the compute precision, summed over sites in FP64
+        real n2 = 0, d = 0;  // in the compute precision; reduce_grid sums the threads
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             rn[k] = r[k] - alpha * ap[k];
             n2 += rn[k] * rn[k];
             d += rn[k] * r[k];
         }
-        v[0] = (double)n2;
-        v[1] = (double)d;
+        v[0] += n2;
+        v[1] += d;
         if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
     }
     __shared__ double tot[2];
@@ -191,9 +192,32 @@ int nblk(int n) { return (n + kBlock - 1) / kBlock; }
         }                                                                                   \
     } while (0)
 
+namespace {
+
+template <int SF, typename real>
+void r_update_t(const BlasArgs &a, cudaStream_t s)
+{
+    static const int wave = wave_blocks(r_update_kernel<SF, real>, kBlock);
+    const int nb = nblk(a.n) < wave ? nblk(a.n) : wave;
+    r_update_kernel<SF, real><<<nb, kBlock, 0, s>>>(a);
+}
+
+}  // namespace
+
 void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, r_update_kernel, nblk(a.n), kBlock, 0, s);
+    switch (sf) {
+    case S_F64: r_update_t<S_F64, double>(a, s); break;
+    case S_F32: r_update_t<S_F32, float>(a, s); break;
+    case S_HALF: r_update_t<S_HALF, float>(a, s); break;
+    case S_INT20: r_update_t<S_INT20, float>(a, s); break;
+    case S_INT30:
+        if (cf == HISQ_COMPUTE_F64)
+            r_update_t<S_INT30, double>(a, s);
+        else
+            r_update_t<S_INT30, float>(a, s);
+        break;
+    }
 }
 
 void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)

@@ -490,6 +490,7 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
     const int64_t vh = g->geom.vh;
     const int nr = p->nrhs;
     if (nr < 1 || nr > kMaxRHS) return fail(c, HISQ_EINVAL, "nrhs must be in 1..%d", kMaxRHS);
+    if (!solver_red_fits(vh)) return fail(c, HISQ_EINVAL, "lattice too large for the solvers' reductions");
     if (p->rhs_tile < 0 || p->rhs_tile > kMaxRHS || (p->rhs_tile > 0 && nr % p->rhs_tile))
         return fail(c, HISQ_EINVAL, "rhs_tile must divide nrhs");
     Workspace ws(c, s);

@@ -15,6 +15,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "codecs.cuh"
 #include "finish.cuh"
 #include "internal.h"
@@ -59,6 +61,70 @@ __device__ __forceinline__ void mv_adj_sub(real acc[6], const real U[18], const 
         }
 }
 
+// Accumulator of one field's terms at a site.  The generic form keeps the
+// six reals of the colour vector.  For FP32 compute it keeps, per colour row
+// i, the pair sums P_i = sum (Re U, Im U) * (Re s, Re s) and Q_i = sum (Re U,
+// Im U) * (Im s, Im s) on the packed FP32 pipe (one __ffma2_rn per two
+// products, halving the issue slots of the complex matrix-vector products);
+// the colour vector is then (P.x - Q.y, P.y + Q.x).  A subtracted adjoint term
+// U^+ s uses the broadcasts (-Re s, Re s) and (-Im s, Im s) on the transposed
+// element, which lands its real and imaginary parts in the same two sums.
+template <typename real>
+struct SiteAccScalar {
+    real a[6];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) a[k] = 0;
+    }
+    __device__ __forceinline__ void add(const real U[18], const real s[6]) { mv_add(a, U, s); }
+    __device__ __forceinline__ void adj_sub(const real U[18], const real s[6]) { mv_adj_sub(a, U, s); }
+    __device__ __forceinline__ real get(int k) const { return a[k]; }
+};
+
+struct SiteAccPacked {
+    float2 P[3], Q[3];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++) P[i] = Q[i] = make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void add(const float U[18], const float s[6])
+    {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float2 br = make_float2(s[2 * j], s[2 * j]), bi = make_float2(s[2 * j + 1], s[2 * j + 1]);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float2 u = make_float2(U[2 * (3 * i + j)], U[2 * (3 * i + j) + 1]);
+                P[i] = __ffma2_rn(u, br, P[i]);
+                Q[i] = __ffma2_rn(u, bi, Q[i]);
+            }
+        }
+    }
+    __device__ __forceinline__ void adj_sub(const float U[18], const float s[6])
+    {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float2 br = make_float2(-s[2 * j], s[2 * j]), bi = make_float2(-s[2 * j + 1], s[2 * j + 1]);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float2 u = make_float2(U[2 * (3 * j + i)], U[2 * (3 * j + i) + 1]);  // element U_ji
+                P[i] = __ffma2_rn(u, br, P[i]);
+                Q[i] = __ffma2_rn(u, bi, Q[i]);
+            }
+        }
+    }
+    __device__ __forceinline__ float get(int k) const
+    {
+        const int i = k >> 1;
+        return (k & 1) ? P[i].y + Q[i].x : P[i].x - Q[i].y;
+    }
+};
+
+template <typename real>
+using SiteAcc = std::conditional_t<std::is_same<real, float>::value, SiteAccPacked, SiteAccScalar<real>>;
+
 // Launch shapes tried by the tuner: threads per block, the minimum number of
 // resident blocks per SM asked of the register allocator (loads in flight per
 // thread against warps per SM) and whether the direction loop is unrolled
@@ -73,12 +139,15 @@ __host__ __device__ constexpr int stencil_minb(int cfg) { return cfg == 2 ? 8 : 
 __host__ __device__ constexpr bool stencil_unrolled(int cfg) { return cfg == 0 || cfg == 4; }
 
 // One direction mu of the stencil at site x (coordinates c, lex), accumulated
-// into accf (fat terms) and accl (long terms).
+// into acc.  Fixed-point links are applied unscaled and the sum is kept in
+// units of the fat scale: a long term's spinor is multiplied by lsc/fsc (one
+// accumulator for both fields keeps registers for loads in flight).
 template <int GF, int SF, typename real, int LREC>
 __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, int cmu, int c3, int lex, int cb,
-                                                  int po, size_t pstride, real lsc, int phase_sum, real accf[6],
-                                                  real accl[6])
+                                                  int po, size_t pstride, real lsc, real ratio, int phase_sum,
+                                                  SiteAcc<real> &acc)
 {
+    constexpr bool kScaled = LinkScaled<GF>::value;
     const Geom &g = a.g;
     const int vh = g.vh, pi = 1 - po;
     const int L = g.L[mu], st = g.stride[mu];
@@ -91,13 +160,13 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
 
     Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
     Spinor<SF>::load(a.in, vh, np1, s);
-    mv_add(accf, U, s);
+    acc.add(U, s);
 
     Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
     Spinor<SF>::load(a.in, vh, nm1, s);
-    mv_adj_sub(accf, U, s);
+    acc.adj_sub(U, s);
 
-    // row 2 of an r12 link in the units of the accumulated sum: sign * lsc * conj(row0 x row1)
+    // row 2 of an r12 link in the units of rows 0 and 1: sign * lsc * conj(row0 x row1)
     const real eta = (phase_sum & 1) ? -lsc : lsc;
     Link<GF, LREC>::load(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
     if constexpr (LREC == 12) {
@@ -105,7 +174,10 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
         rebuild_row2(U, flip ? -eta : eta);
     }
     Spinor<SF>::load(a.in, vh, np3, s);
-    mv_add(accl, U, s);
+    if constexpr (kScaled)
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] *= ratio;
+    acc.add(U, s);
 
     Link<GF, LREC>::load(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
     if constexpr (LREC == 12) {
@@ -113,87 +185,101 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
         rebuild_row2(U, flip ? -eta : eta);
     }
     Spinor<SF>::load(a.in, vh, nm3, s);
-    mv_adj_sub(accl, U, s);
+    if constexpr (kScaled)
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] *= ratio;
+    acc.adj_sub(U, s);
 }
 
+// One output site cb: the stencil, the optional xpay, the store and, when
+// reducing, this site's Re<y, out> and |out|^2 added to rv (in the compute
+// precision; reduce_grid sums the threads).
+template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
+__device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t pstride, real fsc, real lsc,
+                                             real ratio, real rv[2])
+{
+    const Geom &g = a.g;
+    const int vh = g.vh;
+    const int po = a.out_parity;
+    int r = cb / g.xh;
+    const int xh = cb - r * g.xh;
+    const int y = r % g.L[1];
+    r /= g.L[1];
+    const int z = r % g.L[2];
+    const int t = r / g.L[2];
+    const int x = 2 * xh + ((y + z + t + po) & 1);
+    const int c[4] = {x, y, z, t};
+    const int lex = 2 * cb + (x & 1);
+    SiteAcc<real> acc;
+    acc.zero();
+    if constexpr (stencil_unrolled(CFG)) {
+        int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            stencil_direction<GF, SF, real, LREC>(a, mu, c[mu], t, lex, cb, po, pstride, lsc, ratio, phase_sum, acc);
+            phase_sum += c[mu];
+        }
+    } else {
+        int phase_sum = 0;
+#pragma unroll 1
+        for (int mu = 0; mu < 4; mu++) {
+            const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+            stencil_direction<GF, SF, real, LREC>(a, mu, cmu, t, lex, cb, po, pstride, lsc, ratio, phase_sum, acc);
+            phase_sum += cmu;
+        }
+    }
+
+    const real sf = (real)a.sign * fsc;
+    real o[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) o[k] = sf * acc.get(k);
+    if (a.xpay) {
+        real yv[6];
+        Spinor<SF>::load(a.y, vh, cb, yv);
+        const real aa = (real)a.a;
+#pragma unroll
+        for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
+        if constexpr (RED) {
+            real d = 0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) d += yv[k] * o[k];
+            rv[0] += d;
+        }
+    }
+    if constexpr (RED) {
+        real n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) n2 += o[k] * o[k];
+        rv[1] += n2;
+    }
+    if (!Spinor<SF>::store(a.out, vh, cb, o)) atomicExch(a.err, 1);
+}
+
+// A plain pass runs one thread per site.  A reducing pass runs one wave of
+// blocks (every block resident at once) over the sites with a grid-stride
+// loop: the end of a reducing block (block sum, partial store, fence, counter)
+// is then paid once per resident block instead of once per 128 sites.
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)
 {
     if (a.active != nullptr && *(volatile const int *)a.active == 0) return;  // uniform over the grid
-    const Geom &g = a.g;
-    const int vh = g.vh;
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    const int po = a.out_parity, pi = 1 - po;
+    const int vh = a.g.vh;
     const size_t pstride = (size_t)8 * vh * 16;
-    double rv[2] = {0.0, 0.0};
     constexpr bool kScaled = LinkScaled<GF>::value;
-    // fixed-point links are accumulated unscaled, one sum per field
+    // fixed-point links are applied unscaled, the sum kept in units of the fat scale
     const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.fat_scale_d : (real)a.gv.fat_scale_f) : real(1);
     const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
-
-    if (cb < vh) {
-        int r = cb / g.xh;
-        const int xh = cb - r * g.xh;
-        const int y = r % g.L[1];
-        r /= g.L[1];
-        const int z = r % g.L[2];
-        const int t = r / g.L[2];
-        const int x = 2 * xh + ((y + z + t + po) & 1);
-        const int c[4] = {x, y, z, t};
-        const int lex = 2 * cb + (x & 1);
-        real accf[6] = {0, 0, 0, 0, 0, 0};
-        real accl[6] = {0, 0, 0, 0, 0, 0};
-        if constexpr (stencil_unrolled(CFG)) {
-            int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                stencil_direction<GF, SF, real, LREC>(a, mu, c[mu], t, lex, cb, po, pstride, lsc, phase_sum, accf,
-                                                      accl);
-                phase_sum += c[mu];
-            }
-        } else {
-            int phase_sum = 0;
-#pragma unroll 1
-            for (int mu = 0; mu < 4; mu++) {
-                const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
-                stencil_direction<GF, SF, real, LREC>(a, mu, cmu, t, lex, cb, po, pstride, lsc, phase_sum, accf,
-                                                      accl);
-                phase_sum += cmu;
-            }
-        }
-
-        const real sf = (real)a.sign * fsc, sl = (real)a.sign * lsc;
-        real o[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) o[k] = sf * accf[k] + sl * accl[k];
-        if (a.xpay) {
-            real yv[6];
-            Spinor<SF>::load(a.y, vh, cb, yv);
-            const real aa = (real)a.a;
-#pragma unroll
-            for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
-            if constexpr (RED) {
-                // one site's terms in the compute precision (FP64 arithmetic
-                // is scarce on GB300); sites are summed in FP64
-                real d = 0;
-#pragma unroll
-                for (int k = 0; k < 6; k++) d += yv[k] * o[k];
-                rv[0] = (double)d;
-            }
-        }
-        if constexpr (RED) {
-            real n2 = 0;
-#pragma unroll
-            for (int k = 0; k < 6; k++) n2 += o[k] * o[k];
-            rv[1] = (double)n2;
-        }
-        if (!Spinor<SF>::store(a.out, vh, cb, o)) atomicExch(a.err, 1);
-    }
-
+    const real ratio = lsc / fsc;
+    real rv[2] = {0, 0};
     if constexpr (RED) {
+        for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < vh; cb += gridDim.x * blockDim.x)
+            stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
         __shared__ double tot[2];
         if (reduce_grid<2>(rv, a.red, tot) && threadIdx.x == 0) run_finisher(a.fin, tot, a.st, a.slot);
+    } else {
+        const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+        if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
     }
 }
 
@@ -201,7 +287,13 @@ template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 void launch_cfg(const DslashArgs &a, cudaStream_t s)
 {
     constexpr int B = stencil_block(CFG);
-    dslash_kernel<GF, SF, real, LREC, RED, CFG><<<(a.g.vh + B - 1) / B, B, 0, s>>>(a);
+    auto kern = dslash_kernel<GF, SF, real, LREC, RED, CFG>;
+    int nb = (a.g.vh + B - 1) / B;
+    if constexpr (RED) {
+        static const int wave = wave_blocks(kern, B);  // one device model per process
+        nb = nb < wave ? nb : wave;
+    }
+    kern<<<nb, B, 0, s>>>(a);
 }
 
 template <int GF, int SF, typename real, int LREC, bool RED>

@@ -37,43 +37,53 @@ bool launch_with(int gf, int sf, int cf, int lrec, bool red, int cfg, const Dsla
     return false;
 }
 
-using TuneKey = std::array<int, 8>;
+using TuneKey = std::array<int, 9>;
 std::mutex tune_mu;
 std::map<TuneKey, int> tune_cache;
 
-TuneKey key_of(int gf, int sf, int cf, int lrec, const Geom &g)
+TuneKey key_of(int gf, int sf, int cf, int lrec, bool red, const Geom &g)
 {
-    return {gf, sf, cf, lrec, g.L[0], g.L[1], g.L[2], g.L[3]};
+    return {gf, sf, cf, lrec, red ? 1 : 0, g.L[0], g.L[1], g.L[2], g.L[3]};
 }
 
 }  // namespace
 
 std::atomic<int> forced_config{-1};
 
-int stencil_config(int gf, int sf, int cf, int lrec, const Geom &g)
+int stencil_config(int gf, int sf, int cf, int lrec, bool red, const Geom &g)
 {
     const int f = forced_config.load();
     if (f >= 0 && stencil_config_valid(f, gf)) return f;
     std::lock_guard<std::mutex> lk(tune_mu);
-    auto it = tune_cache.find(key_of(gf, sf, cf, lrec, g));
+    auto it = tune_cache.find(key_of(gf, sf, cf, lrec, red, g));
     return it == tune_cache.end() ? 0 : it->second;
 }
 
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
 {
-    return launch_with(gf, sf, cf, long_recon, reduce, stencil_config(gf, sf, cf, long_recon, a.g), a, s);
+    return launch_with(gf, sf, cf, long_recon, reduce, stencil_config(gf, sf, cf, long_recon, reduce, a.g), a, s);
 }
 
-void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaStream_t s)
+namespace {
+
+// Times every launch shape of one kernel variant; the reducing variant (whose
+// register budget differs) is timed as the solvers use it, with xpay and both
+// sums, and with no finisher.
+void tune_variant(int gf, int sf, int cf, int lrec, bool red, const DslashArgs &args, cudaStream_t s)
 {
-    const TuneKey key = key_of(gf, sf, cf, lrec, args.g);
+    const TuneKey key = key_of(gf, sf, cf, lrec, red, args.g);
     {
         std::lock_guard<std::mutex> lk(tune_mu);
         if (tune_cache.count(key)) return;
     }
-    DslashArgs a = args;  // a plain pass: no finisher, no skip flag
+    DslashArgs a = args;
     a.fin = FIN_NONE;
     a.active = nullptr;
+    if (red) {
+        a.xpay = 1;
+        a.y = a.out;
+        a.a = 1.0;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -84,9 +94,9 @@ void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaS
     float best_ms = 1e30f;
     for (int cfg = 0; cfg < kNumStencilConfigs; cfg++) {
         if (!stencil_config_valid(cfg, gf)) continue;
-        launch_with(gf, sf, cf, lrec, false, cfg, a, s);  // warm
+        launch_with(gf, sf, cf, lrec, red, cfg, a, s);  // warm
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; r++) launch_with(gf, sf, cf, lrec, false, cfg, a, s);
+        for (int r = 0; r < 3; r++) launch_with(gf, sf, cf, lrec, red, cfg, a, s);
         cudaEventRecord(e1, s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
@@ -100,6 +110,15 @@ void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaS
     (void)cudaGetLastError();
     std::lock_guard<std::mutex> lk(tune_mu);
     tune_cache[key] = best;
+}
+
+}  // namespace
+
+void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaStream_t s)
+{
+    if (const int f = forced_config.load(); f >= 0 && stencil_config_valid(f, gf)) return;  // shape fixed by the caller
+    tune_variant(gf, sf, cf, lrec, false, args, s);
+    if (args.red.partials != nullptr && args.red.counter != nullptr) tune_variant(gf, sf, cf, lrec, true, args, s);
 }
 
 }  // namespace hisq

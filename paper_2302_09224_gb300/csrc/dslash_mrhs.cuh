@@ -21,8 +21,6 @@
 
 namespace hisq {
 
-constexpr int kMrhsBlock = 128;
-
 template <int GF, int RECON, typename real>
 __device__ __forceinline__ void load_link_scaled(const char *base, size_t pstride, int li, real U[18], real scale,
                                                  real sign12)
@@ -47,9 +45,9 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
     constexpr bool kScaled = LinkScaled<GF>::value;
     const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.fat_scale_d : (real)a.gv.fat_scale_f) : real(1);
     const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
-    double rv[2 * T];
+    real rv[2 * T];
 #pragma unroll
-    for (int k = 0; k < 2 * T; k++) rv[k] = 0.0;
+    for (int k = 0; k < 2 * T; k++) rv[k] = 0;
 
     if (cb < vh) {
         int r = cb / g.xh;
@@ -61,11 +59,11 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
         const int x = 2 * xh + ((y + z + t + po) & 1);
         const int c[4] = {x, y, z, t};
         const int lex = 2 * cb + (x & 1);
-        real acc[T][6];
+        // packed FP32 accumulators hold twice the registers: used up to 8 per thread
+        using Acc = std::conditional_t<(T <= 8), SiteAcc<real>, SiteAccScalar<real>>;
+        Acc acc[T];
 #pragma unroll
-        for (int j = 0; j < T; j++)
-#pragma unroll
-            for (int k = 0; k < 6; k++) acc[j][k] = 0;
+        for (int j = 0; j < T; j++) acc[j].zero();
         int phase_sum = 0;
 
 #pragma unroll
@@ -94,9 +92,9 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
                     real s[6];
                     Spinor<SF>::load(a.in + (size_t)(a.t0 + j) * a.field_bytes, vh, nb[term], s);
                     if (fwd)
-                        mv_add(acc[j], U, s);
+                        acc[j].add(U, s);
                     else
-                        mv_adj_sub(acc[j], U, s);
+                        acc[j].adj_sub(U, s);
                 }
             }
             phase_sum += c[mu];
@@ -107,7 +105,7 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
         for (int j = 0; j < T; j++) {
             real o[6];
 #pragma unroll
-            for (int k = 0; k < 6; k++) o[k] = sgn * acc[j][k];
+            for (int k = 0; k < 6; k++) o[k] = sgn * acc[j].get(k);
             const size_t off = (size_t)(a.t0 + j) * a.field_bytes;
             if (a.xpay) {
                 real yv[6];
@@ -120,14 +118,14 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
                     real d = 0;
 #pragma unroll
                     for (int k = 0; k < 6; k++) d += yv[k] * o[k];
-                    rv[2 * j] = (double)d;
+                    rv[2 * j] = d;
                 }
             }
             if constexpr (RED) {
                 real n2 = 0;
 #pragma unroll
                 for (int k = 0; k < 6; k++) n2 += o[k] * o[k];
-                rv[2 * j + 1] = (double)n2;
+                rv[2 * j + 1] = n2;
             }
             if (!Spinor<SF>::store(a.out + off, vh, cb, o)) atomicExch(a.err, 1);
         }
@@ -157,6 +155,7 @@ void launch_mrhs_tile(int T, const DslashMArgs &a, cudaStream_t s)
 template <int GF, int SF, typename real>
 bool launch_mrhs_t(int long_recon, bool reduce, int T, const DslashMArgs &args, cudaStream_t s)
 {
+    if (reduce && !red_fits(args.g.vh, kMrhsBlock, 2 * T)) return false;
     for (int t0 = 0; t0 < args.nrhs; t0 += T) {
         DslashMArgs a = args;
         a.t0 = t0;

@@ -67,10 +67,22 @@ constexpr int kMaxRed = 32;         // values reduced per launch
 constexpr int kMaxRedBlocks = 1 << 16;
 
 struct RedBuf {
-    double *partials;        // [kMaxRedBlocks][kMaxRed]
+    double *partials;        // kMaxRedBlocks * kMaxRed values: nr per block of a launch
     unsigned int *counter;   // zero between launches
     double *result;          // [kMaxRed] written by the last block
 };
+
+// Whether a reducing launch over n sites (blocks of `block` threads, gy grid
+// rows, nr values per block) fits the partials buffer.
+inline bool red_fits(int64_t n, int block, int nr, int gy = 1)
+{
+    return ((n + block - 1) / block) * gy * nr <= (int64_t)kMaxRedBlocks * kMaxRed;
+}
+
+// The single-RHS solvers' reducing launches: the stencil (blocks of 128 or
+// more, 2 values), the BLAS kernels (256, 3) and BiCGStab(l)'s two-parity
+// grids (256, 3, 2 rows).  Holds up to Vh = 2^27 sites.
+inline bool solver_red_fits(int64_t vh) { return red_fits(vh, 128, 2) && red_fits(vh, 256, 3, 2); }
 
 // ---------------------------------------------------------------------------
 // solver scalar state kept on the device (one per solve)
@@ -168,6 +180,7 @@ struct DslashArgs {
 // A tile of right-hand sides for the batched stencil: right-hand side t lives
 // in the fields at in/out/y + t * field_bytes.
 constexpr int kMaxRHS = 16;
+constexpr int kMrhsBlock = 128;  // threads per block of the batched stencil
 
 struct DslashMArgs {
     Geom g;
@@ -205,7 +218,7 @@ bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int
 // overwritten) and keeps the fastest for this triplet and lattice.  Call
 // outside stream capture.
 void tune_dslash(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
-int stencil_config(int gf, int sf, int cf, int long_recon, const Geom &g);
+int stencil_config(int gf, int sf, int cf, int long_recon, bool reduce, const Geom &g);
 
 void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);
 void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s);

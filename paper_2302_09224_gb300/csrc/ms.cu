@@ -477,6 +477,7 @@ extern "C" hisq_status hisq_multishift_cg(hisq_ctx *c, const hisq_gauge *gc, con
     hisq_gauge *g = const_cast<hisq_gauge *>(gc);
     cudaStream_t s = pick_stream(c, p->stream);
     const int64_t vh = g->geom.vh;
+    if (!solver_red_fits(vh)) return fail(c, HISQ_EINVAL, "lattice too large for the solvers' reductions");
     // ascending shifts: the smallest is the base system
     std::vector<int> ord(nshift);
     std::iota(ord.begin(), ord.end(), 0);

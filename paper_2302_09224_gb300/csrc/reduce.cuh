@@ -1,4 +1,4 @@
-// reduce.cuh -- deterministic FP64 reductions fused into producing kernels.
+// reduce.cuh -- deterministic reductions fused into producing kernels.
 //
 // Each block reduces its threads' values with a fixed shuffle/shared-memory
 // tree and writes one partial per value; the last block to finish (detected
@@ -14,8 +14,8 @@
 
 namespace hisq {
 
-template <int NR>
-__device__ __forceinline__ void warp_sum(double v[NR])
+template <int NR, typename T>
+__device__ __forceinline__ void warp_sum(T v[NR])
 {
 #pragma unroll
     for (int k = 0; k < NR; k++)
@@ -23,13 +23,13 @@ __device__ __forceinline__ void warp_sum(double v[NR])
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
 }
 
-// Sum over the block; the result is valid in thread 0 only.
-template <int NR>
-__device__ __forceinline__ void block_sum(double v[NR], double (*sh)[NR])
+// Sum over the block in the values' own type; valid in thread 0 only.
+template <int NR, typename T>
+__device__ __forceinline__ void block_sum(T v[NR], T (*sh)[NR])
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
-    warp_sum<NR>(v);
+    warp_sum<NR, T>(v);
     __syncthreads();  // sh may be reused from a previous call
     if (lane == 0)
 #pragma unroll
@@ -37,25 +37,67 @@ __device__ __forceinline__ void block_sum(double v[NR], double (*sh)[NR])
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; k++) v[k] = lane < nw ? sh[lane][k] : 0.0;
-        warp_sum<NR>(v);
+        for (int k = 0; k < NR; k++) v[k] = lane < nw ? sh[lane][k] : T(0);
+        warp_sum<NR, T>(v);
     }
+}
+
+// An unevaluated FP32 pair hi + lo (about 44 significant bits) and its sum by
+// Knuth's error-free TwoSum: every step a plain FP32 add (no contraction), so
+// the FP32 pipe carries the cross-block sum instead of the narrow FP64 pipe.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fadd_rn(s, -a.hi);
+    float e = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -bb)), __fadd_rn(b.hi, -bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    return {hi, __fadd_rn(e, -__fadd_rn(hi, -s))};
+}
+
+template <int NR>
+__device__ __forceinline__ void warp_sum_ff(FF v[NR])
+{
+#pragma unroll
+    for (int k = 0; k < NR; k++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const FF o = {__shfl_down_sync(0xffffffffu, v[k].hi, off), __shfl_down_sync(0xffffffffu, v[k].lo, off)};
+            v[k] = ff_add(v[k], o);
+        }
 }
 
 // Returns true in every thread of the last block, with the grid totals in
 // `tot` (shared memory).  All threads of every block must call it.  Grids may
 // be two-dimensional (blocks are numbered x fastest).
-template <int NR>
-__device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
+//
+// FP64 values (FP64 compute) are summed in FP64 throughout.  FP32 values (one
+// thread's sites formed in the FP32 compute precision) are summed in FP32 up
+// to the block, each block storing one FP32 partial; the last block sums the
+// partials in the FP32 pair arithmetic above and returns hi + lo in FP64.  On
+// GB300 the FP64 pipe issues a small fraction of the FP32 rate, so FP64
+// arithmetic in every block (or a long FP64 chain in the last one) dominated
+// the short reducing kernels.
+template <int NR, typename T>
+__device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
 {
-    __shared__ double sh[32][NR];
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "float or double");
+    __shared__ T sh[32][NR];
     __shared__ int is_last;
     const unsigned nblocks = gridDim.x * gridDim.y;
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum<NR>(v, sh);
+    T *part = reinterpret_cast<T *>(rb.partials);
+    T v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) v[k] = vin[k];
+    block_sum<NR, T>(v, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; k++) rb.partials[(size_t)bid * NR + k] = v[k];
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = v[k];
         __threadfence();
         const unsigned prev = atomicAdd(rb.counter, 1u);
         is_last = (prev == nblocks - 1);
@@ -66,34 +108,83 @@ __device__ bool reduce_grid(double v[NR], const RedBuf &rb, double *tot)
     // every block's partials: coherent L2 loads (ld.cg), U rows per thread in
     // flight at once (one L2 round trip per U rows); the order is fixed
     constexpr int U = NR <= 4 ? 8 : NR <= 8 ? 4 : 1;
-    double w[NR];
-#pragma unroll
-    for (int k = 0; k < NR; k++) w[k] = 0.0;
     const unsigned step = blockDim.x;
-    for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * step) {
-        double tmp[U][NR];
+    if constexpr (sizeof(T) == 8) {
+        double w[NR];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const unsigned b = b0 + u * step;
+        for (int k = 0; k < NR; k++) w[k] = 0.0;
+        for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * step) {
+            double tmp[U][NR];
 #pragma unroll
-            for (int k = 0; k < NR; k++) tmp[u][k] = b < nblocks ? __ldcg(rb.partials + (size_t)b * NR + k) : 0.0;
+            for (int u = 0; u < U; u++) {
+                const unsigned b = b0 + u * step;
+#pragma unroll
+                for (int k = 0; k < NR; k++) tmp[u][k] = b < nblocks ? __ldcg(part + (size_t)b * NR + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int k = 0; k < NR; k++) w[k] += tmp[u][k];
         }
+        block_sum<NR, double>(w, sh);
+        if (threadIdx.x == 0)
 #pragma unroll
-        for (int u = 0; u < U; u++)
+            for (int k = 0; k < NR; k++) tot[k] = w[k];
+    } else {
+        FF w[NR];
 #pragma unroll
-            for (int k = 0; k < NR; k++) w[k] += tmp[u][k];
+        for (int k = 0; k < NR; k++) w[k] = {0.0f, 0.0f};
+        for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * step) {
+            float tmp[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const unsigned b = b0 + u * step;
+#pragma unroll
+                for (int k = 0; k < NR; k++) tmp[u][k] = b < nblocks ? __ldcg(part + (size_t)b * NR + k) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int k = 0; k < NR; k++) w[k] = ff_add(w[k], FF{tmp[u][k], 0.0f});
+        }
+        __shared__ FF shf[32][NR];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int nw = (blockDim.x + 31) >> 5;
+        warp_sum_ff<NR>(w);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NR; k++) shf[wid][k] = w[k];
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; k++) w[k] = lane < nw ? shf[lane][k] : FF{0.0f, 0.0f};
+            warp_sum_ff<NR>(w);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < NR; k++) tot[k] = (double)w[k].hi + (double)w[k].lo;
+        }
     }
-    block_sum<NR>(w, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NR; k++) {
-            tot[k] = w[k];
-            rb.result[k] = w[k];
-        }
+        for (int k = 0; k < NR; k++) rb.result[k] = tot[k];
         *rb.counter = 0u;
     }
     __syncthreads();
     return true;
+}
+
+// Blocks of one full wave of a kernel on the current device: the grid of a
+// reducing kernel that loops over its sites, so that the end of a reducing
+// block (block sum, partial store, fence, counter) is paid once per resident
+// block rather than once per block of sites.
+template <typename K>
+int wave_blocks(K kernel, int block)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
 }
 
 }  // namespace hisq
