@@ -36,6 +36,8 @@ MASS = 0.01
 TOL = 1e-10
 DELTA = 0.1
 SLOPPY = "int20"
+# the stencil's flop convention (16 complex 3x3 matrix-vector products of 66 flop plus 15 six-real adds)
+FLOP_PER_SITE = 16 * 66 + 15 * 6
 WORKLOAD = ("mixed-precision even/odd CG to 1e-10 (16-bit gauge / 20-bit fermion / FP32 sloppy, r12 long links, "
             "FP64 x, true residuals and reductions, delta 0.1) on a 32^3x64 lattice, m=0.01, seeded near-identity "
             "SU(3) links (eps 0.3, fat x0.8, staggered phases), Gaussian source")
@@ -229,7 +231,7 @@ def run_ours(args):
     x = torch.zeros_like(b)
     stream = torch.cuda.Stream(device=dev)
 
-    def params(name, delta, on_device=1, graph=0):
+    def params(name, delta, on_device=1, graph=1):
         p = hisq.hisq_default_params()
         p.mass, p.tol, p.delta, p.on_device = MASS, TOL, delta, on_device
         p.sloppy = hisq.prec(name, 12 if name != "f64" else 18)
@@ -277,24 +279,19 @@ def run_ours(args):
     total_bytes = sum_over_ranks(pg, bytes_per_step * args.steps, dev)
     value = total_bytes / (ms_max / 1e3) / 1e9
 
-    # oracle check of the returned solution (FP64 true residual on the CPU)
-    true_res_oracle = None
+    # the CPU baseline: the oracle's FP64 CG on the host cores, a bounded sample (rank 0, N = 1 only)
     cpu = None
-    if rank == 0:
+    if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
         oracle.build()
         fat_h, lng_h, b_h = fat.cpu().numpy(), lng.cpu().numpy(), b.cpu().numpy()
-        xs = x.cpu().numpy()
-        r = b_h - oracle.mee(DIMS, fat_h, lng_h, MASS, xs)
-        true_res_oracle = float(np.linalg.norm(r) / np.linalg.norm(b_h))
-        if world == 1 and not args.no_cpu:
-            dt, it, cores = oracle_sample(fat_h, lng_h, b_h, args.ref_iters)
-            per_iter = dt / (it + 2)
-            cpu_step = per_iter * info.iters
-            cpu = {"value": bytes_per_step / cpu_step / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{args.ref_iters} FP64 CG iterations of the C oracle (OpenMP) on the full 32^3x64 "
-                             f"lattice, {dt:.1f} s, extrapolated to the GPU solve's {info.iters} iterations"}
+        dt, it, cores = oracle_sample(fat_h, lng_h, b_h, args.ref_iters)
+        per_iter = dt / (it + 2)
+        cpu_step = per_iter * info.iters
+        cpu = {"value": bytes_per_step / cpu_step / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.ref_iters} FP64 CG iterations of the C oracle (OpenMP) on the full 32^3x64 "
+                         f"lattice, {dt:.1f} s, extrapolated to the GPU solve's {info.iters} iterations"}
 
     # end to end through the ABI with host buffers
     bh = b.cpu().numpy()
@@ -310,7 +307,7 @@ def run_ours(args):
     e2e_value = sum_over_ranks(pg, bytes_per_step, dev) / e2e_s / 1e9
 
     # plain FP64 GPU CG on the same system (time-to-solution comparison)
-    p64 = params("f64", 0.0, graph=0)
+    p64 = params("f64", 0.0)
     x64 = torch.zeros_like(b)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
@@ -321,6 +318,47 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     fp64_s = f0.elapsed_time(f1) / 1e3
+
+    # the same solve with every other sloppy storage triplet of Sec. 4 (one warm-up solve each: the
+    # gauge copy in that format and the launch-shape tuning happen there), and BiCGStab(4) on the
+    # full M = 2m + D; each timed with events on the solver's stream
+    def timed(fn):
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        with torch.cuda.stream(stream):
+            res = fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return res, a0.elapsed_time(a1) / 1e3
+
+    formats = {}
+    if not args.no_formats:
+        for name in ("f32", "half", "int30f32", "int30"):
+            pf = params(name, DELTA)
+            xf = torch.zeros_like(b)
+            with torch.cuda.stream(stream):
+                hisq.hisq_cg(ctx, g, pf, b, xf)
+            xf.zero_()
+            (stf, inff), sec = timed(lambda: hisq.hisq_cg(ctx, g, pf, b, xf))
+            formats[name] = {"s": sec, "speedup_vs_fp64": fp64_s / sec, "iters": inff.iters,
+                             "reliable_updates": inff.reliable_updates, "true_residual": inff.true_residual,
+                             "status": hisq.STATUS_NAMES[stf]}
+        formats["int20"] = {"s": ms / args.steps / 1e3, "speedup_vs_fp64": fp64_s / (ms / args.steps / 1e3),
+                            "iters": infos[-1][1], "reliable_updates": infos[-1][3],
+                            "true_residual": infos[-1][2], "status": hisq.STATUS_NAMES[infos[-1][0]]}
+        bf = synth.spinor(DIMS, synth.rhs_seed(rank), full=True, device=dev)
+        xb = torch.zeros_like(bf)
+        pb = params(SLOPPY, DELTA)
+        pb.l = 4
+        with torch.cuda.stream(stream):
+            hisq.hisq_bicgstabl(ctx, g, pb, bf, xb)
+        xb.zero_()
+        (stb, infb), secb = timed(lambda: hisq.hisq_bicgstabl(ctx, g, pb, bf, xb))
+        formats["bicgstab4_int20_full_M"] = {"s": secb, "cycles": infb.iters, "matvecs": infb.matvecs,
+                                            "reliable_updates": infb.reliable_updates,
+                                            "true_residual": infb.true_residual, "status": hisq.STATUS_NAMES[stb]}
 
     peak, peak_kind = measured_peak()
     achieved = stencil.bytes / (stencil.ms / 1e3) / 1e9 if stencil.ms > 0 else 0.0
@@ -346,8 +384,10 @@ def run_ours(args):
                              "iters_custom": infos[-1][1], "iters_fp64": info64.iters,
                              "reliable_updates": infos[-1][3],
                              "true_residual_custom": infos[-1][2], "true_residual_fp64": info64.true_residual,
-                             "true_residual_oracle": true_res_oracle,
                              "status": [hisq.STATUS_NAMES[i[0]] for i in infos] + [hisq.STATUS_NAMES[st64]]},
+        "stencil_gflops": FLOP_PER_SITE * (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2) * stencil.launches
+                          / (stencil.ms / 1e3) / 1e9 if stencil.ms > 0 else 0.0,
+        "formats_time_to_solution": formats,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(bh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes), "s_per_step": e2e_s},
         "gpu_launches": int(sum_over_ranks(pg, launches, dev)),
@@ -416,6 +456,146 @@ def run_solve_only(args):
     return 0
 
 
+def run_multishift(args):
+    """12 shifts log-spaced in [1e-4, 1] on 32^3x64, base m = 0.005, per-shift targets 1e-10..1e-7: the
+    multi-shift stage (all shifts in one fused update kernel per iteration) plus refinement, per format."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims, m = (32, 32, 32, 64), 0.005
+    sig = synth.shifts_logspaced(12, 1e-4, 1.0)
+    tols = synth.shift_tolerances(12, 1e-10, 1e-7)
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    b = synth.spinor(dims, synth.rhs_seed(0), device="cuda")
+    res = {}
+    for name in args.formats.split(","):
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.delta, p.on_device = m, min(tols), DELTA, 1
+        p.sloppy = hisq.prec(name, 12 if name != "f64" else 18)
+        p.refine = hisq.prec(name, 12 if name != "f64" else 18)
+        p.maxiter = 100000
+        xs = [torch.zeros_like(b) for _ in sig]
+        hisq.hisq_multishift_cg(ctx, g, p, sig, tols, b, xs)  # warm-up: gauge copy, tuning
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = hisq.hisq_multishift_cg(ctx, g, p, sig, tols, b, xs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tr = list(info.shift_resid)[:12]  # FP64 true residuals computed on the GPU after refinement
+        res[name] = {"s": dt, "status": hisq.STATUS_NAMES[st], "iters_multishift": info.iters,
+                     "shift_iters": list(info.shift_iters)[:12], "refine_iters": list(info.refine_iters)[:12],
+                     "residual_after_multishift": list(info.shift_resid_ms)[:12], "true_residual": tr,
+                     "targets_met": all(r <= t for r, t in zip(tr, tols))}
+    print(json.dumps({"workload": "multi-shift CG, 12 shifts log-spaced 1e-4..1, 32^3x64, m=0.005, "
+                      "targets 1e-10..1e-7, refinement in the same format", "results": res}))
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
+def run_batched(args):
+    """16 right-hand sides on 48^3x96 (m = 0.002): one batched solve (autotuned RHS tile) against the same
+    16 systems solved one after another with the single-RHS solver."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims, m, nr = (48, 48, 48, 96), 0.002, 16
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    del fat, lng
+    torch.cuda.empty_cache()
+    b = torch.stack([synth.spinor(dims, synth.rhs_seed(k), device="cuda") for k in range(nr)]).contiguous()
+    res = {}
+    for name in args.formats.split(","):
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.delta, p.on_device = m, TOL, DELTA, 1
+        p.sloppy = hisq.prec(name, 12)
+        p.maxiter = 100000
+        p.nrhs = nr
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = hisq.hisq_cg(ctx, g, p, b, x)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        p1 = hisq.hisq_default_params()
+        p1.mass, p1.tol, p1.delta, p1.on_device = m, TOL, DELTA, 1
+        p1.sloppy = hisq.prec(name, 12)
+        p1.maxiter = 100000
+        x1 = torch.zeros_like(b[0])
+        iters1 = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(nr):
+            x1.zero_()
+            _, i1 = hisq.hisq_cg(ctx, g, p1, b[k], x1)
+            iters1.append(i1.iters)
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - t0
+        res[name] = {"batched_s": t_batch, "sequential_s": t_single, "speedup": t_single / t_batch,
+                     "status": hisq.STATUS_NAMES[st], "iters_max_batched": info.iters,
+                     "iters_single": iters1, "true_residual_max": info.true_residual}
+    print(json.dumps({"workload": "batched CG, 16 Gaussian RHS on 48^3x96, m=0.002, tol 1e-10, autotuned tile",
+                      "results": res}))
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
+def run_serve(args):
+    """A seeded Poisson stream (200 requests/s) of CG and 8-shift multi-shift requests over four lattice
+    volumes, masses log-uniform in [1e-3, 1e-1], tolerances {1e-6, 1e-8, 1e-10}, submitted at their arrival
+    times to the library's request loop; latency percentiles and throughput."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    reqs = synth.poisson_requests(args.requests, rate_hz=200.0, seed=1)
+    ctx = hisq.hisq_create(0)
+    gauges = {}
+    for d in sorted({r["dims"] for r in reqs}):
+        fat, lng = synth.gauge_pair(d, seed=0, device="cuda")
+        gauges[d] = hisq.hisq_load_gauge(ctx, d, fat, lng)
+        del fat, lng
+    live = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if r["t"] > now:
+            time.sleep(r["t"] - now)
+        b = synth.spinor(r["dims"], r["rhs_seed"], device="cuda")
+        if r["multishift"]:
+            xs = torch.zeros((len(r["shifts"]),) + tuple(b.shape), dtype=torch.float64, device="cuda")
+            t = hisq.hisq_submit(ctx, gauges[r["dims"]], hisq.HISQ_REQ_MULTISHIFT, r["mass"], b, xs, True,
+                                 sigma=r["shifts"], shift_tol=[r["tol"]] * len(r["shifts"]))
+        else:
+            xs = torch.zeros_like(b)
+            t = hisq.hisq_submit(ctx, gauges[r["dims"]], hisq.HISQ_REQ_CG, r["mass"], b, xs, True, tol=r["tol"])
+        live.append((t, b, xs))
+    statuses = {}
+    for t, b, xs in live:
+        st, _ = hisq.hisq_wait(ctx, t, 3600.0)
+        statuses[hisq.STATUS_NAMES[st]] = statuses.get(hisq.STATUS_NAMES[st], 0) + 1
+    wall = time.perf_counter() - t0
+    s = hisq.hisq_serve_stats(ctx)
+    print(json.dumps({"workload": f"serving: {args.requests} Poisson requests at 200/s (seed 1), volumes "
+                      "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts)",
+                      "completed": s.completed, "statuses": statuses, "latency_p50_s": s.latency_p50_s,
+                      "latency_p99_s": s.latency_p99_s, "solves_per_s": s.solves_per_s, "wall_s": wall}))
+    for g in gauges.values():
+        hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,21 +605,32 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per CPU sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--solve-iters", type=int, default=2100,
+    ap.add_argument("--no-formats", action="store_true", help="skip the other storage formats' solves")
+    ap.add_argument("--solve-iters", type=int, default=2866,
                     help="reference arm: iterations of one GPU solve (extrapolation unit)")
-    ap.add_argument("--solve-bytes", type=float, default=2.6e12,
+    ap.add_argument("--solve-bytes", type=float, default=3.605e12,
                     help="reference arm: algorithmic bytes of one GPU solve")
     ap.add_argument("--stencil", default=None, help="LX,LY,LZ,LT: only run stencil applications (profiling)")
     ap.add_argument("--prec", default="int20")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--stencil-config", type=int, default=-1, help="force a stencil launch shape (0..4)")
     ap.add_argument("--solve", default=None, help="LX,LY,LZ,LT: only one short CG solve (profiling)")
+    ap.add_argument("--workload", default="solve", choices=["solve", "multishift", "batched", "serve"],
+                    help="solve: the headline line; the others print their own measurement line")
+    ap.add_argument("--formats", default="int20,half", help="sloppy formats for --workload multishift/batched")
+    ap.add_argument("--requests", type=int, default=100, help="requests of --workload serve")
     ap.add_argument("--maxiter", type=int, default=20)
     args = ap.parse_args()
     if args.stencil:
         return run_stencil_only(args)
     if args.solve:
         return run_solve_only(args)
+    if args.workload == "multishift":
+        return run_multishift(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -461,7 +461,7 @@ hisq_status BatchSession::step()
             set_thread_capturing(false);
             if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
             size_t nn = 0;
-            if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
+            if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
             if (gr) cudaGraphDestroy(gr);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "batched CG graph capture");
             nodes = (int64_t)nn;

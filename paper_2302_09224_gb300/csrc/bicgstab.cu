@@ -623,7 +623,7 @@ struct BRun {
                     set_thread_capturing(false);
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
                     size_t nn = 0;
-                    if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
+                    if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
                     if (gr) cudaGraphDestroy(gr);
                     if (ce != cudaSuccess) return cuda_fail(c, ce, "BiCGStab graph capture");
                     nodes = (int64_t)nn;

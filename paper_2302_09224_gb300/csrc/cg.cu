@@ -230,6 +230,7 @@ struct CGRun {
         const int N = cfg.nbuf;
         const int *act = &st->active;
         for (int i = 0; i < N; i++) {
+            set_prof_tag(i);
             apply_mee(c, g->geom, cfg.sloppy, gv_s, diag, slot(i), tmp_s, ap_s, FIN_CG_ALPHA, st, i, act,
                       PROF_STENCIL, s);
             BlasArgs a = blas();
@@ -251,6 +252,7 @@ struct CGRun {
                 launch_p_update(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
             }
         }
+        set_prof_tag(-1);
     }
 
     hisq_status run(const double *b64, double *x64, bool x_zero, hisq_solve_info *info)
@@ -294,9 +296,11 @@ struct CGRun {
         if (e) return e;
         hisq_status status = HISQ_OK;
         bool done = st_h->hi_rr <= init.stop2;
-        const bool graph = cfg.use_graph && !c->prof.on;
+        // with the profiler on, the graph carries an event pair around each launch
+        const bool graph = cfg.use_graph;
         cudaGraphExec_t exec = nullptr;
         int64_t nodes = 0;
+        std::vector<Profiler::Rec> grecs;
         while (!done) {
             if (st_h->k >= cfg.maxiter) {
                 status = HISQ_ENOTCONV;
@@ -307,17 +311,22 @@ struct CGRun {
                 if (!exec) {
                     cudaGraph_t gr = nullptr;
                     set_thread_capturing(true);
+                    if (c->prof.on) set_graph_recorder(&grecs);
                     cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
                     if (ce == cudaSuccess) {
                         iterate_block(x64);
                         ce = cudaStreamEndCapture(s, &gr);
                     }
+                    set_graph_recorder(nullptr);
                     set_thread_capturing(false);
                     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
                     size_t nn = 0;
-                    if (ce == cudaSuccess) ce = cudaGraphGetNodes(gr, nullptr, &nn);
+                    if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
                     if (gr) cudaGraphDestroy(gr);
-                    if (ce != cudaSuccess) return cuda_fail(c, ce, "CG graph capture");
+                    if (ce != cudaSuccess) {
+                        prof_graph_release(c, grecs);
+                        return cuda_fail(c, ce, "CG graph capture");
+                    }
                     nodes = (int64_t)nn;
                 }
                 cudaGraphLaunch(exec, s);
@@ -327,6 +336,10 @@ struct CGRun {
             }
             e = pull_state();
             if (e) break;
+            if (graph)
+                prof_graph_account(c, grecs, st_h->k - k0);
+            else
+                prof_settle(c, st_h->k - k0);
             const int reason = st_h->reason;
             if (reason == REASON_BREAKDOWN) {
                 status = HISQ_EBREAKDOWN;
@@ -344,6 +357,7 @@ struct CGRun {
             }
         }
         if (exec) cudaGraphExecDestroy(exec);
+        prof_graph_release(c, grecs);
         if (e) return e;
         if (status != HISQ_OK) {
             // bring x up to date (an unfinished block's slots) and measure it

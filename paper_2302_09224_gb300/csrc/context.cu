@@ -50,7 +50,12 @@ hisq_status cuda_fail(hisq_ctx *c, cudaError_t e, const char *what)
 namespace {
 thread_local const Lane *tl_lane = nullptr;
 thread_local bool tl_capturing = false;
+thread_local int tl_prof_tag = -1;
+thread_local std::vector<Profiler::Rec> *tl_graph_rec = nullptr;
 }  // namespace
+
+void set_prof_tag(int tag) { tl_prof_tag = tag; }
+void set_graph_recorder(std::vector<Profiler::Rec> *rec) { tl_graph_rec = rec; }
 
 void set_thread_lane(const Lane *lane) { tl_lane = lane; }
 const RedBuf &cur_red(hisq_ctx *c) { return tl_lane ? tl_lane->red : c->red; }
@@ -93,11 +98,15 @@ bool stream_capturing(cudaStream_t s)
 }
 
 LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_)
-    : c(c_), s(s_), kind(kind_), bytes(bytes_)
+    : c(c_), s(s_), kind(kind_), bytes(bytes_), tag(tl_prof_tag)
 {
-    if (thread_capturing()) return;  // counted when the graph is replayed
-    c->launches += 1;
-    if (!c->prof.on || stream_capturing(s)) return;
+    if (thread_capturing()) {  // launches are counted when the graph is replayed
+        if (!c->prof.on || !tl_graph_rec) return;
+        in_graph = true;
+    } else {
+        c->launches += 1;
+        if (!c->prof.on || stream_capturing(s)) return;
+    }
     std::lock_guard<std::mutex> lk(c->prof_mu);
     auto take = [&]() {
         cudaEvent_t e;
@@ -111,16 +120,81 @@ LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_
     };
     a = take();
     b = take();
-    cudaEventRecord(a, s);
+    if (in_graph)
+        cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(a, s);
 }
 
 LaunchScope::~LaunchScope()
 {
     if (!a) return;
+    if (in_graph) {
+        cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+        tl_graph_rec->push_back({a, b, kind, bytes, tag});
+        return;
+    }
     cudaEventRecord(b, s);
     std::lock_guard<std::mutex> lk(c->prof_mu);
-    c->prof.pending.push_back({a, b, kind, bytes});
+    c->prof.pending.push_back({a, b, kind, bytes, tag});
     if (c->prof.pending.size() > 4096) prof_flush_locked(c);
+}
+
+cudaError_t graph_kernel_nodes(cudaGraph_t g, size_t *n)
+{
+    *n = 0;
+    size_t total = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &total);
+    if (e != cudaSuccess || total == 0) return e;
+    std::vector<cudaGraphNode_t> nodes(total);
+    e = cudaGraphGetNodes(g, nodes.data(), &total);
+    if (e != cudaSuccess) return e;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) *n += 1;
+    }
+    return cudaSuccess;
+}
+
+void prof_settle(hisq_ctx *c, int n_exec)
+{
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    auto &p = c->prof.pending;
+    size_t w = 0;
+    for (size_t i = 0; i < p.size(); i++) {
+        if (p[i].tag >= n_exec) {
+            c->prof.pool.push_back(p[i].a);
+            c->prof.pool.push_back(p[i].b);
+            continue;
+        }
+        p[i].tag = -1;
+        p[w++] = p[i];
+    }
+    p.resize(w);
+}
+
+void prof_graph_account(hisq_ctx *c, const std::vector<Profiler::Rec> &recs, int n_exec)
+{
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    for (const auto &r : recs) {
+        if (r.tag >= n_exec) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof.ms[r.kind] += ms;
+            c->prof.launches[r.kind] += 1;
+            c->prof.bytes[r.kind] += r.bytes;
+        }
+    }
+}
+
+void prof_graph_release(hisq_ctx *c, std::vector<Profiler::Rec> &recs)
+{
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    for (const auto &r : recs) {
+        c->prof.pool.push_back(r.a);
+        c->prof.pool.push_back(r.b);
+    }
+    recs.clear();
 }
 
 void prof_flush(hisq_ctx *c)

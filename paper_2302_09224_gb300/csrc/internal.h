@@ -267,6 +267,7 @@ struct Profiler {
         cudaEvent_t a, b;
         int kind;
         double bytes;
+        int tag;  // iteration within a solver's block (-1: always counted), see prof_settle
     };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
@@ -311,6 +312,10 @@ const RedBuf &cur_red(hisq_ctx *c);
 int *cur_err(hisq_ctx *c);
 void set_thread_capturing(bool on);
 bool thread_capturing();
+// Profiling tag of the launches that follow on this thread: the iteration
+// within a solver's block (-1: none).  Launches of iterations that the device
+// skipped (the block stopped early) are then left out of the statistics.
+void set_prof_tag(int tag);
 
 // status helpers (context.cu)
 hisq_status fail(hisq_ctx *c, hisq_status s, const char *fmt, ...);
@@ -325,13 +330,28 @@ struct LaunchScope {
     cudaStream_t s;
     int kind;
     double bytes;
+    int tag = -1;
+    bool in_graph = false;
     cudaEvent_t a = nullptr, b = nullptr;
     LaunchScope(hisq_ctx *c, cudaStream_t s, int kind, double bytes);
     ~LaunchScope();
 };
 void prof_flush(hisq_ctx *c);   // resolve pending event pairs (synchronises on them)
 void prof_flush_locked(hisq_ctx *c);
+// After a block of iterations of which n_exec ran: drop the pending records
+// tagged with a later iteration (launches that returned at once).
+void prof_settle(hisq_ctx *c, int n_exec);
+// Profiling inside a captured graph: while a recorder is set on the capturing
+// thread, launch scopes record their event pairs as graph nodes (external
+// event records) into it; after each replay of the graph and a synchronise,
+// prof_graph_account adds the pairs of the first n_exec iterations to the
+// statistics; prof_graph_release returns the events to the pool.
+void set_graph_recorder(std::vector<Profiler::Rec> *rec);
+void prof_graph_account(hisq_ctx *c, const std::vector<Profiler::Rec> &recs, int n_exec);
+void prof_graph_release(hisq_ctx *c, std::vector<Profiler::Rec> &recs);
 bool stream_capturing(cudaStream_t s);
+// Kernel nodes of a captured graph (the launches one replay makes).
+cudaError_t graph_kernel_nodes(cudaGraph_t g, size_t *n);
 
 // A validated triplet: returns HISQ_OK and the device view of the gauge copy.
 hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, GaugeView *v);
