@@ -219,19 +219,34 @@ typedef struct {
                            output spinors, xpay input) */
 } hisq_kernel_stats;
 
-/* While enabled, every launch made outside stream capture (solvers run their
- * iterations without graphs then) is bracketed by CUDA events on its own
- * stream and accumulated per class.  Reading synchronises on the events. */
+/* While enabled, every launch of a selected class is bracketed by CUDA events
+ * on its own stream and accumulated per class.  The CG solver keeps its
+ * graphs: the event pairs are then recorded as graph nodes and read after
+ * each block of iterations, and launches of iterations the device skipped
+ * (the block stopped early) are not counted; the other solvers run without
+ * graphs while profiling.  Reading synchronises on the events. */
 HISQ_API void hisq_profile_enable(hisq_ctx *ctx, int on);
 HISQ_API void hisq_profile_reset(hisq_ctx *ctx);
 HISQ_API hisq_status hisq_profile_read(hisq_ctx *ctx, int kind, hisq_kernel_stats *out);
+/* Classes that get event pairs: bit k selects class k (default all).  Each
+ * event pair costs some device time, so a caller timing a solve may select
+ * only the class it needs.  Unselected classes are not counted. */
+HISQ_API void hisq_profile_select(hisq_ctx *ctx, unsigned mask);
 
 /* Launch shape of the stencil kernels: -1 (default) lets the library time the
  * shapes the first time a (precision, lattice) pair is used and keep the
- * fastest; 0..4 forces one shape for every later launch in the process.
+ * fastest (separately for the plain pass and for the pass with the fused
+ * reduction); 0..4 forces one shape for every later launch in the process.
+ * hisq_stencil_config sets the plain pass and, unless
+ * hisq_stencil_config_reduce has set its own, the reducing pass too.
  * Returns the previous setting, or -2 for an invalid value.  For benchmarking
  * and testing the shapes. */
 HISQ_API int hisq_stencil_config(int cfg);
+HISQ_API int hisq_stencil_config_reduce(int cfg);
+/* The shape in use for triplet p on gauge g's lattice (plain pass, or the
+ * reducing pass if reduce != 0): the forced one, else the tuned one, else -1
+ * when that pair has not been tuned yet. */
+HISQ_API int hisq_stencil_config_in_use(const hisq_gauge *g, hisq_prec p, int reduce);
 
 /* Kernels this context has launched so far (graph replays add their nodes). */
 HISQ_API int64_t hisq_launch_count(hisq_ctx *ctx);

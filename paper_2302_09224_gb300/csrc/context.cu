@@ -100,12 +100,13 @@ bool stream_capturing(cudaStream_t s)
 LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_)
     : c(c_), s(s_), kind(kind_), bytes(bytes_), tag(tl_prof_tag)
 {
+    const bool sel = c->prof.on && ((c->prof.mask >> kind) & 1u);
     if (thread_capturing()) {  // launches are counted when the graph is replayed
-        if (!c->prof.on || !tl_graph_rec) return;
+        if (!sel || !tl_graph_rec) return;
         in_graph = true;
     } else {
         c->launches += 1;
-        if (!c->prof.on || stream_capturing(s)) return;
+        if (!sel || stream_capturing(s)) return;
     }
     std::lock_guard<std::mutex> lk(c->prof_mu);
     auto take = [&]() {
@@ -622,6 +623,13 @@ void hisq_profile_enable(hisq_ctx *c, int on)
     if (!c) return;
     if (!on) prof_flush(c);
     c->prof.on = on != 0;
+}
+
+void hisq_profile_select(hisq_ctx *c, unsigned mask)
+{
+    if (!c) return;
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    c->prof.mask = mask;
 }
 
 void hisq_profile_reset(hisq_ctx *c)

@@ -49,14 +49,34 @@ TuneKey key_of(int gf, int sf, int cf, int lrec, bool red, const Geom &g)
 }  // namespace
 
 std::atomic<int> forced_config{-1};
+std::atomic<int> forced_config_red{-1};
+
+namespace {
+
+int forced_for(bool red)
+{
+    const int fr = forced_config_red.load();
+    return red && fr >= 0 ? fr : forced_config.load();
+}
+
+}  // namespace
 
 int stencil_config(int gf, int sf, int cf, int lrec, bool red, const Geom &g)
 {
-    const int f = forced_config.load();
+    const int f = forced_for(red);
     if (f >= 0 && stencil_config_valid(f, gf)) return f;
     std::lock_guard<std::mutex> lk(tune_mu);
     auto it = tune_cache.find(key_of(gf, sf, cf, lrec, red, g));
     return it == tune_cache.end() ? 0 : it->second;
+}
+
+int stencil_config_in_use(int gf, int sf, int cf, int lrec, bool red, const Geom &g)
+{
+    const int f = forced_for(red);
+    if (f >= 0 && stencil_config_valid(f, gf)) return f;
+    std::lock_guard<std::mutex> lk(tune_mu);
+    auto it = tune_cache.find(key_of(gf, sf, cf, lrec, red, g));
+    return it == tune_cache.end() ? -1 : it->second;
 }
 
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a, cudaStream_t s)
@@ -71,6 +91,7 @@ namespace {
 // sums, and with no finisher.
 void tune_variant(int gf, int sf, int cf, int lrec, bool red, const DslashArgs &args, cudaStream_t s)
 {
+    if (const int f = forced_for(red); f >= 0 && stencil_config_valid(f, gf)) return;  // shape fixed by the caller
     const TuneKey key = key_of(gf, sf, cf, lrec, red, args.g);
     {
         std::lock_guard<std::mutex> lk(tune_mu);
@@ -116,7 +137,6 @@ void tune_variant(int gf, int sf, int cf, int lrec, bool red, const DslashArgs &
 
 void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaStream_t s)
 {
-    if (const int f = forced_config.load(); f >= 0 && stencil_config_valid(f, gf)) return;  // shape fixed by the caller
     tune_variant(gf, sf, cf, lrec, false, args, s);
     if (args.red.partials != nullptr && args.red.counter != nullptr) tune_variant(gf, sf, cf, lrec, true, args, s);
 }
@@ -142,6 +162,18 @@ bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int
 }
 
 }  // namespace hisq
+
+extern "C" int hisq_stencil_config_reduce(int cfg)
+{
+    if (cfg < -1 || cfg >= hisq::kNumStencilConfigs) return -2;
+    return hisq::forced_config_red.exchange(cfg);
+}
+
+extern "C" int hisq_stencil_config_in_use(const hisq_gauge *g, hisq_prec p, int reduce)
+{
+    if (!g) return -1;
+    return hisq::stencil_config_in_use(p.gauge, p.spinor, p.compute, p.long_recon, reduce != 0, g->geom);
+}
 
 extern "C" int hisq_stencil_config(int cfg)
 {

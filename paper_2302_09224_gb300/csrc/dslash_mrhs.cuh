@@ -33,6 +33,27 @@ __device__ __forceinline__ void load_link_scaled(const char *base, size_t pstrid
     if constexpr (RECON == 12) rebuild_row2(U, sign12);
 }
 
+// U <- -U^+ (a backward term's matrix, so that every term is accumulated as
+// acc += U s).
+template <typename real>
+__device__ __forceinline__ void neg_adjoint(real U[18])
+{
+    real V[18];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            V[2 * (3 * i + j)] = -U[2 * (3 * j + i)];
+            V[2 * (3 * i + j) + 1] = U[2 * (3 * j + i) + 1];
+        }
+#pragma unroll
+    for (int k = 0; k < 18; k++) U[k] = V[k];
+}
+
+// For tiles of 8 and 16 the loops over directions and over forward/backward
+// hops stay rolled (only the loop over the tile's right-hand sides is
+// unrolled): the kernel body then fits the instruction cache, which a fully
+// unrolled body of 16 x T matrix-vector products did not.
 template <int GF, int SF, typename real, int LREC, int T, bool RED>
 __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMArgs a)
 {
@@ -57,47 +78,63 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMAr
         const int z = r % g.L[2];
         const int t = r / g.L[2];
         const int x = 2 * xh + ((y + z + t + po) & 1);
-        const int c[4] = {x, y, z, t};
         const int lex = 2 * cb + (x & 1);
-        // packed FP32 accumulators hold twice the registers: used up to 8 per thread
-        using Acc = std::conditional_t<(T <= 8), SiteAcc<real>, SiteAccScalar<real>>;
+        // packed FP32 accumulators hold twice the registers: used up to 4 per thread
+        using Acc = std::conditional_t<(T <= 4), SiteAcc<real>, SiteAccScalar<real>>;
         Acc acc[T];
 #pragma unroll
         for (int j = 0; j < T; j++) acc[j].zero();
-        int phase_sum = 0;
-
-#pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
+        // one term: link of hop k (1 fat, 3 long) in direction dir, applied to
+        // the neighbour of every right-hand side of the tile
+        auto term = [&](int mu, int cmu, int hop, int dir, int base, real eta) {
             const int L = g.L[mu], st = g.stride[mu];
-            const int cp1 = wrap_coord(c[mu] + 1, L), cm1 = wrap_coord(c[mu] - 1, L);
-            const int cp3 = wrap_coord(c[mu] + 3, L), cm3 = wrap_coord(c[mu] - 3, L);
-            const int base = lex - c[mu] * st;
-            const int nb[4] = {(base + cp1 * st) >> 1, (base + cm1 * st) >> 1, (base + cp3 * st) >> 1,
-                               (base + cm3 * st) >> 1};
-            const real eta = (phase_sum & 1) ? real(-1) : real(1);
-            const bool flip_f = g.antiperiodic_t && mu == 3 && c[3] + 3 >= L;
-            const bool flip_b = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
-#pragma unroll
-            for (int term = 0; term < 4; term++) {
-                real U[18];
-                const bool fwd = term == 0 || term == 2;
-                const int li = ((fwd ? po : pi) * 4 + mu) * vh + (fwd ? cb : nb[term]);
-                if (term < 2)
-                    load_link_scaled<GF, 18>(a.gv.fat, pstride, li, U, fsc, real(1));
-                else
-                    load_link_scaled<GF, LREC>(a.gv.lng, pstride, li, U, lsc,
-                                               ((term == 2 ? flip_f : flip_b) ? -eta : eta));
-#pragma unroll
-                for (int j = 0; j < T; j++) {
-                    real s[6];
-                    Spinor<SF>::load(a.in + (size_t)(a.t0 + j) * a.field_bytes, vh, nb[term], s);
-                    if (fwd)
-                        acc[j].add(U, s);
-                    else
-                        acc[j].adj_sub(U, s);
-                }
+            const int k = hop ? 3 : 1;
+            const int cn = wrap_coord(dir ? cmu - k : cmu + k, L);
+            const int nb = (base + cn * st) >> 1;
+            const int li = ((dir ? pi : po) * 4 + mu) * vh + (dir ? nb : cb);
+            real U[18];
+            if (hop == 0) {
+                load_link_scaled<GF, 18>(a.gv.fat, pstride, li, U, fsc, real(1));
+            } else {
+                // the boundary sign belongs to the link's own site: x for the
+                // forward link, x - 3 mu for the backward one
+                const bool flip = g.antiperiodic_t && mu == 3 && (dir ? cn : cmu) + 3 >= L;
+                load_link_scaled<GF, LREC>(a.gv.lng, pstride, li, U, lsc, flip ? -eta : eta);
             }
-            phase_sum += c[mu];
+            if (dir) neg_adjoint(U);
+#pragma unroll
+            for (int j = 0; j < T; j++) {
+                real s[6];
+                Spinor<SF>::load(a.in + (size_t)(a.t0 + j) * a.field_bytes, vh, nb, s);
+                acc[j].add(U, s);
+            }
+        };
+        const int c[4] = {x, y, z, t};
+        int phase_sum = 0;
+        if constexpr (T <= 4) {
+            // small tiles: fully unrolled (index arithmetic folded at compile time)
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                const int base = lex - c[mu] * g.stride[mu];
+                const real eta = (phase_sum & 1) ? real(-1) : real(1);
+#pragma unroll
+                for (int q = 0; q < 4; q++) term(mu, c[mu], q >> 1, q & 1, base, eta);
+                phase_sum += c[mu];
+            }
+        } else {
+            // large tiles: directions and hops rolled so that the body fits the
+            // instruction cache
+#pragma unroll 1
+            for (int mu = 0; mu < 4; mu++) {
+                const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+                const int base = lex - cmu * g.stride[mu];
+                const real eta = (phase_sum & 1) ? real(-1) : real(1);
+#pragma unroll
+                for (int hop = 0; hop < 2; hop++)
+#pragma unroll 1
+                    for (int dir = 0; dir < 2; dir++) term(mu, cmu, hop, dir, base, eta);
+                phase_sum += cmu;
+            }
         }
 
         const real sgn = (real)a.sign;

@@ -219,6 +219,7 @@ bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int
 // outside stream capture.
 void tune_dslash(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
 int stencil_config(int gf, int sf, int cf, int long_recon, bool reduce, const Geom &g);
+int stencil_config_in_use(int gf, int sf, int cf, int long_recon, bool reduce, const Geom &g);
 
 void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);
 void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s);
@@ -263,6 +264,7 @@ void server_shutdown(hisq_ctx *c);
 enum ProfKind { PROF_STENCIL = 0, PROF_STENCIL_HI = 1, PROF_BLAS = 2, PROF_CONVERT = 3, PROF_NKIND = 4 };
 struct Profiler {
     bool on = false;
+    unsigned mask = ~0u;  // classes that get event pairs
     struct Rec {
         cudaEvent_t a, b;
         int kind;

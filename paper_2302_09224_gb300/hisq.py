@@ -124,9 +124,12 @@ _SIGS = {
     "hisq_spinor_unpack": (_I, [_P, _I, _I, _I64, _P, _P, _P]),
     "hisq_profile_enable": (None, [_P, _I]),
     "hisq_profile_reset": (None, [_P]),
+    "hisq_profile_select": (None, [_P, ctypes.c_uint]),
     "hisq_profile_read": (_I, [_P, _I, ctypes.POINTER(hisq_kernel_stats)]),
     "hisq_launch_count": (_I64, [_P]),
     "hisq_stencil_config": (_I, [_I]),
+    "hisq_stencil_config_reduce": (_I, [_I]),
+    "hisq_stencil_config_in_use": (_I, [_P, hisq_prec, _I]),
     "hisq_default_params": (None, [ctypes.POINTER(hisq_solver_params)]),
     "hisq_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P, ctypes.POINTER(hisq_solve_info)]),
     "hisq_multishift_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _I, _P, _P, _P, _P,
@@ -280,6 +283,10 @@ def hisq_profile_reset(ctx):
     lib().hisq_profile_reset(ctx)
 
 
+def hisq_profile_select(ctx, mask: int):
+    lib().hisq_profile_select(ctx, int(mask) & 0xFFFFFFFF)
+
+
 def hisq_profile_read(ctx, kind: int) -> hisq_kernel_stats:
     s = hisq_kernel_stats()
     _check(ctx, lib().hisq_profile_read(ctx, int(kind), ctypes.byref(s)))
@@ -288,6 +295,14 @@ def hisq_profile_read(ctx, kind: int) -> hisq_kernel_stats:
 
 def hisq_stencil_config(cfg: int) -> int:
     return int(lib().hisq_stencil_config(int(cfg)))
+
+
+def hisq_stencil_config_reduce(cfg: int) -> int:
+    return int(lib().hisq_stencil_config_reduce(int(cfg)))
+
+
+def hisq_stencil_config_in_use(g, p: hisq_prec, reduce: bool) -> int:
+    return int(lib().hisq_stencil_config_in_use(g, p, int(bool(reduce))))
 
 
 def hisq_launch_count(ctx) -> int:
