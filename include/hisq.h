@@ -271,11 +271,13 @@ typedef struct {
     int32_t use_graph;    /* 1: replay each block of iterations as a CUDA graph */
     int32_t nrhs;         /* hisq_cg: right-hand sides solved together (1..16, Sec. 1 block solvers) */
     int32_t rhs_tile;     /* right-hand sides per stencil launch (1,2,4,8,16 dividing nrhs; 0: tuned) */
+    int32_t rhs_kernel;   /* batched stencil kernel: 0 tuned, 1 registers, 2 staged neighbour loads
+                             (16-bit and 20-bit fermions only; EINVAL otherwise) */
     void *stream;         /* cudaStream_t; NULL: the context's stream */
 } hisq_solver_params;
 
 /* Fills params with the defaults: delta 0.1, nbuf 8, pr_beta 1, reproject 1,
- * l 4, use_graph 1, nrhs 1, rhs_tile 0, maxiter 100000, tol 1e-10, sloppy
+ * l 4, use_graph 1, nrhs 1, rhs_tile 0, rhs_kernel 0, maxiter 100000, tol 1e-10, sloppy
  * and refine FIX16/INT20/F32 with r12 long links. */
 HISQ_API void hisq_default_params(hisq_solver_params *p);
 

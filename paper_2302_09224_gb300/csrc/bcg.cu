@@ -142,22 +142,27 @@ __global__ void __launch_bounds__(kBlock) b_flush_kernel(BBArgs a)
         }                                                                                        \
     } while (0)
 
-using TileKey = std::array<int, 9>;
+using TileKey = std::array<int, 10>;
+struct TileChoice {
+    int T, variant;
+};
 std::mutex tile_mu;
-std::map<TileKey, int> tile_cache;
+std::map<TileKey, TileChoice> tile_cache;
 
-// The tile size T (dividing nrhs) with the fastest batched pass, timed once
-// per (triplet, nrhs, lattice) on zero fields.
-int tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, int nrhs, char *in, char *out,
-              size_t fb, cudaStream_t s)
+// The tile size T (dividing nrhs; only `fixed` if that is > 0) and kernel
+// variant with the fastest batched pass, timed once per (triplet, nrhs,
+// lattice) on zero fields.
+TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, int nrhs, int fixed,
+                     int kernel, char *in, char *out, size_t fb, cudaStream_t s)
 {
-    const TileKey key = {p.gauge, p.spinor, p.compute, p.long_recon, nrhs, geom.L[0], geom.L[1], geom.L[2], geom.L[3]};
+    const TileKey key = {p.gauge, p.spinor, p.compute, p.long_recon, nrhs, fixed * 4 + kernel, geom.L[0], geom.L[1],
+                         geom.L[2], geom.L[3]};
     {
         std::lock_guard<std::mutex> lk(tile_mu);
         auto it = tile_cache.find(key);
         if (it != tile_cache.end()) return it->second;
     }
-    int best = 1;
+    TileChoice best = {fixed > 0 ? fixed : 1, kernel == 2 ? 1 : 0};
     if (!thread_capturing() && !stream_capturing(s)) {
         cudaMemsetAsync(in, 0, fb * nrhs, s);
         DslashMArgs d{};
@@ -176,16 +181,19 @@ int tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
         for (int T = 1; T <= 16; T *= 2) {
-            if (nrhs % T || !red_fits(geom.vh, kMrhsBlock, 2 * T)) continue;
-            launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, d, s);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 2; r++) launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, d, s);
-            cudaEventRecord(e1, s);
-            float ms = 0.f;
-            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-                ms < best_ms) {
-                best_ms = ms;
-                best = T;
+            if (nrhs % T || (fixed > 0 && T != fixed) || !red_fits(geom.vh, kMrhsBlock, 2 * T)) continue;
+            for (int v = 0; v < 2; v++) {
+                if (kernel > 0 && v != kernel - 1) continue;
+                if (!launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, v, d, s)) continue;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 2; r++) launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, v, d, s);
+                cudaEventRecord(e1, s);
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                    ms < best_ms) {
+                    best_ms = ms;
+                    best = {T, v};
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -268,7 +276,8 @@ void BatchSession::stencil_pass(int parity_out, const char *in, char *out, const
     const double links = 8.0 * link_bytes(cfg.sloppy.gauge, 18) + 8.0 * link_bytes(cfg.sloppy.gauge, cfg.sloppy.long_recon);
     const double sb = (double)spinor_site_bytes(cfg.sloppy.spinor) * vh;
     LaunchScope ls(c, s, PROF_STENCIL, links * vh * (nr / T) + (y ? 3.0 : 2.0) * sb * nr);
-    launch_dslash_mrhs(cfg.sloppy.gauge, cfg.sloppy.spinor, cfg.sloppy.compute, cfg.sloppy.long_recon, red, T, d, s);
+    launch_dslash_mrhs(cfg.sloppy.gauge, cfg.sloppy.spinor, cfg.sloppy.compute, cfg.sloppy.long_recon, red, T, variant, d,
+                       s);
 }
 
 void BatchSession::iterate_block()
@@ -372,7 +381,9 @@ hisq_status BatchSession::setup()
     bb.assign(nr, 0.0);
     stop2.assign(nr, 0.0);
     diag.assign(nr, 0.0);
-    T = cfg.tile > 0 ? cfg.tile : tune_tile(c, g->geom, cfg.sloppy, gv_s, nr, ap_s, tmp_s, fb, s);
+    const TileChoice tc = tune_tile(c, g->geom, cfg.sloppy, gv_s, nr, cfg.tile, cfg.kernel, ap_s, tmp_s, fb, s);
+    T = tc.T;
+    variant = tc.variant;
     if (nr % T) return fail(c, HISQ_EINVAL, "RHS tile %d does not divide nrhs %d", T, nr);
     if (!red_fits(vh, kMrhsBlock, 2 * T) || !red_fits(vh, kBlock, 2 * kMaxRHS))
         return fail(c, HISQ_EINVAL, "lattice too large for a batched reduction over a tile of %d", T);

@@ -17,6 +17,7 @@ struct BCGConfig {
     hisq_prec sloppy{};
     int nbuf = 8, maxiter = 100000, pr = 1, reproject = 1, use_graph = 1;
     int tile = 0;               // RHS per stencil launch (0: tuned)
+    int kernel = 0;             // batched stencil: 0 tuned, 1 registers, 2 staged
     double delta = 0.1;
 };
 
@@ -32,7 +33,7 @@ struct BatchSession {
     BCGConfig cfg;
     cudaStream_t s;
     Workspace ws;
-    int vh, nr, N, T = 1;
+    int vh, nr, N, T = 1, variant = 0;
     size_t fb = 0;
     char *r_s = nullptr, *ap_s = nullptr, *tmp_s = nullptr, *ring = nullptr;
     double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *ax64 = nullptr, *tmp64 = nullptr;

@@ -487,6 +487,7 @@ void hisq_default_params(hisq_solver_params *p)
     p->use_graph = 1;
     p->nrhs = 1;
     p->rhs_tile = 0;
+    p->rhs_kernel = 0;
     p->stream = nullptr;
 }
 
@@ -507,6 +508,9 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
     if (!solver_red_fits(vh)) return fail(c, HISQ_EINVAL, "lattice too large for the solvers' reductions");
     if (p->rhs_tile < 0 || p->rhs_tile > kMaxRHS || (p->rhs_tile > 0 && nr % p->rhs_tile))
         return fail(c, HISQ_EINVAL, "rhs_tile must divide nrhs");
+    if (p->rhs_kernel < 0 || p->rhs_kernel > 2 ||
+        (p->rhs_kernel == 2 && p->sloppy.spinor != HISQ_SPINOR_HALF16 && p->sloppy.spinor != HISQ_SPINOR_INT20))
+        return fail(c, HISQ_EINVAL, "rhs_kernel must be 0, 1, or 2 with a 16- or 20-bit sloppy fermion");
     Workspace ws(c, s);
     double *b64 = nullptr, *x64 = nullptr;
     e = ws.alloc((size_t)48 * vh * nr, (void **)&b64);
@@ -536,6 +540,7 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
         bc.reproject = p->reproject;
         bc.use_graph = p->use_graph;
         bc.tile = p->rhs_tile;
+        bc.kernel = p->rhs_kernel;
         bc.delta = p->delta;
         std::vector<hisq_solve_info> infos(nr);
         st = run_bcg(c, g, bc, b64, x64, !p->use_init_guess, infos.data(), s);

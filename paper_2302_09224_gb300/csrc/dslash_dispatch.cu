@@ -145,19 +145,19 @@ void tune_dslash(int gf, int sf, int cf, int lrec, const DslashArgs &args, cudaS
 
 namespace hisq {
 
-bool launch_mrhs_f32(int, bool, int, const DslashMArgs &, cudaStream_t);
-bool launch_mrhs_half(int, bool, int, const DslashMArgs &, cudaStream_t);
-bool launch_mrhs_int20(int, bool, int, const DslashMArgs &, cudaStream_t);
+bool launch_mrhs_f32(int, bool, int, int, const DslashMArgs &, cudaStream_t);
+bool launch_mrhs_half(int, bool, int, int, const DslashMArgs &, cudaStream_t);
+bool launch_mrhs_int20(int, bool, int, int, const DslashMArgs &, cudaStream_t);
 
-bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, const DslashMArgs &a,
+bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, int variant, const DslashMArgs &a,
                         cudaStream_t s)
 {
     if (T != 1 && T != 2 && T != 4 && T != 8 && T != 16) return false;
     if (a.nrhs < 1 || a.nrhs > kMaxRHS || a.nrhs % T) return false;
     if (cf != HISQ_COMPUTE_F32) return false;
-    if (gf == G_F32 && sf == S_F32) return launch_mrhs_f32(long_recon, reduce, T, a, s);
-    if (gf == G_FIX16 && sf == S_HALF) return launch_mrhs_half(long_recon, reduce, T, a, s);
-    if (gf == G_FIX16 && sf == S_INT20) return launch_mrhs_int20(long_recon, reduce, T, a, s);
+    if (gf == G_F32 && sf == S_F32) return launch_mrhs_f32(long_recon, reduce, T, variant, a, s);
+    if (gf == G_FIX16 && sf == S_HALF) return launch_mrhs_half(long_recon, reduce, T, variant, a, s);
+    if (gf == G_FIX16 && sf == S_INT20) return launch_mrhs_int20(long_recon, reduce, T, variant, a, s);
     return false;
 }
 

@@ -211,8 +211,10 @@ struct DslashMArgs {
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a,
                    cudaStream_t s);
 // Batched stencil over all right-hand sides in tiles of T (T in {1,2,4,8,16},
-// dividing nrhs); false when the triplet has no batched kernel.
-bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, const DslashMArgs &a,
+// dividing nrhs), variant 0 (register kernel) or 1 (staged neighbour loads,
+// 16-byte spinor records only); false when the triplet or variant has no
+// batched kernel.
+bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int T, int variant, const DslashMArgs &a,
                         cudaStream_t s);
 // Times each stencil launch shape on `a` (run as a plain pass: `a.out` is
 // overwritten) and keeps the fastest for this triplet and lattice.  Call

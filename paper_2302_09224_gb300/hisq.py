@@ -62,7 +62,7 @@ class hisq_solver_params(ctypes.Structure):
                 ("nbuf", ctypes.c_int32), ("use_init_guess", ctypes.c_int32), ("on_device", ctypes.c_int32),
                 ("pr_beta", ctypes.c_int32), ("reproject", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("rhs_kernel", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class hisq_solve_info(ctypes.Structure):

@@ -93,3 +93,30 @@ def test_sixteen_rhs_and_invalid(ctx, orc):
         solve(ctx, dims, m, bs[:3], "half", tile=2)
     with pytest.raises(hisq.HisqError, match="EINVAL"):
         solve(ctx, dims, m, bs[:2], "int30", tile=1)
+
+
+@pytest.mark.parametrize("name", ["int20", "half"])
+@pytest.mark.parametrize("tile", [1, 2, 4, 8, 16])
+def test_register_and_staged_kernels(ctx, orc, name, tile):
+    """Both batched stencil kernels (registers; staged neighbour loads through
+    shared memory) at every tile size: every right-hand side meets the target
+    and the two kernels' solutions agree (same arithmetic in the same order).
+    The 6x4x4x8 lattice has a ragged last block (384 sites per parity)."""
+    dims, m = (6, 4, 4, 8), 0.08
+    bs = [synth.spinor(dims, synth.rhs_seed(k)).numpy() for k in range(16)]
+    sols = []
+    for kernel in (1, 2):
+        st, info, xs = solve(ctx, dims, m, bs, name, tile, rhs_kernel=kernel)
+        assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+        for b, x in zip(bs, xs):
+            assert true_res(orc, dims, m, b, x) <= 1e-10
+        sols.append(xs)
+    d = max(np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(*sols))
+    assert d <= 1e-9
+
+
+def test_staged_kernel_refuses_other_formats(ctx):
+    dims = (4, 4, 4, 8)
+    bs = [synth.spinor(dims, synth.rhs_seed(k)).numpy() for k in range(2)]
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        solve(ctx, dims, 0.1, bs, "f32", tile=2, rhs_kernel=2)
