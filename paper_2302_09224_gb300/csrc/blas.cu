@@ -27,27 +27,48 @@ __device__ __forceinline__ bool skip(const int *active)
     return active != nullptr && *(volatile const int *)active == 0;
 }
 
+// Sites per thread of the two per-iteration BLAS kernels: every load of a
+// thread's sites is issued before any of them is used (memory-level
+// parallelism for these short, latency-bound kernels).
+constexpr int kRSites = 2;
+constexpr int kPSites = 2;
+
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 {
     if (skip(a.active)) return;
+    constexpr int U = kRSites, C = Spinor<SF>::chunks;
     real v[2] = {0, 0};
     const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
-    // one wave of blocks loops over the sites (see wave_blocks)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        real r[6], ap[6], rn[6];
-        Spinor<SF>::load(a.v0, a.n, i, r);
-        Spinor<SF>::load(a.v1, a.n, i, ap);
-        real n2 = 0, d = 0;  // in the compute precision; reduce_grid sums the threads
+    // one wave of blocks loops over groups of U sites per thread (see wave_blocks)
+    for (int i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < a.n; i0 += gridDim.x * blockDim.x * U) {
+        uint4 cr[U][C], ca[U][C];
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            rn[k] = r[k] - alpha * ap[k];
-            n2 += rn[k] * rn[k];
-            d += rn[k] * r[k];
+        for (int u = 0; u < U; u++) {
+            const int i = i0 + u * blockDim.x;
+            if (i < a.n) {
+                Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
+                Spinor<SF>::gather(a.v1, a.n, i, ca[u]);
+            }
         }
-        v[0] += n2;
-        v[1] += d;
-        if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= a.n) continue;
+            real r[6], ap[6], rn[6];
+            Spinor<SF>::decode(cr[u], r);
+            Spinor<SF>::decode(ca[u], ap);
+            real n2 = 0, d = 0;  // in the compute precision; reduce_grid sums the threads
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                rn[k] = r[k] - alpha * ap[k];
+                n2 += rn[k] * rn[k];
+                d += rn[k] * r[k];
+            }
+            v[0] += n2;
+            v[1] += d;
+            if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
+        }
     }
     __shared__ double tot[2];
     if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) {
@@ -62,17 +83,31 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
 {
     if (skip(a.active)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a.clear_ring && i == 0)
+    constexpr int U = kPSites, C = Spinor<SF>::chunks;
+    const int i0 = blockIdx.x * blockDim.x * U + threadIdx.x;
+    if (a.clear_ring && i0 == 0)
         for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
-    if (i >= a.n) return;
-    real r[6], p[6];
-    Spinor<SF>::load(a.v0, a.n, i, r);
-    Spinor<SF>::load(a.v1, a.n, i, p);
+    uint4 cr[U][C], cp[U][C];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i < a.n) {
+            Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
+            Spinor<SF>::gather(a.v1, a.n, i, cp[u]);
+        }
+    }
     const real beta = (real)a.st->beta;
 #pragma unroll
-    for (int k = 0; k < 6; k++) p[k] = r[k] + beta * p[k];
-    if (!Spinor<SF>::store(a.v2, a.n, i, p)) atomicExch(a.err, 1);
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= a.n) continue;
+        real r[6], p[6];
+        Spinor<SF>::decode(cr[u], r);
+        Spinor<SF>::decode(cp[u], p);
+#pragma unroll
+        for (int k = 0; k < 6; k++) p[k] = r[k] + beta * p[k];
+        if (!Spinor<SF>::store(a.v2, a.n, i, p)) atomicExch(a.err, 1);
+    }
 }
 
 // x_hi += sum_{j < nslots} alpha_j p_j; slots are consecutive fields of
@@ -198,8 +233,8 @@ template <int SF, typename real>
 void r_update_t(const BlasArgs &a, cudaStream_t s)
 {
     static const int wave = wave_blocks(r_update_kernel<SF, real>, kBlock);
-    const int nb = nblk(a.n) < wave ? nblk(a.n) : wave;
-    r_update_kernel<SF, real><<<nb, kBlock, 0, s>>>(a);
+    const int need = (a.n + kBlock * kRSites - 1) / (kBlock * kRSites);
+    r_update_kernel<SF, real><<<need < wave ? need : wave, kBlock, 0, s>>>(a);
 }
 
 }  // namespace
@@ -222,7 +257,7 @@ void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 
 void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, nblk(a.n), kBlock, 0, s);
+    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, (a.n + kBlock * kPSites - 1) / (kBlock * kPSites), kBlock, 0, s);
 }
 
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)
