@@ -145,6 +145,13 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def aggregate(pg, ms, bytes_local, device):
+    """Whole-job figures of N replicas: the slowest rank's time and every rank's bytes (weak scaling)."""
+    ms_max = max_over_ranks(pg, ms, device)
+    total = sum_over_ranks(pg, bytes_local, device)
+    return ms_max, total / (ms_max / 1e3) / 1e9
+
+
 def barrier(pg):
     if pg is not None:
         pg.barrier()
@@ -281,9 +288,7 @@ def run_ours(args):
     hisq.hisq_profile_enable(ctx, False)
     hisq.hisq_profile_select(ctx, 0xFFFFFFFF)
     barrier(pg)
-    ms_max = max_over_ranks(pg, ms, dev)
-    total_bytes = sum_over_ranks(pg, bytes_per_step * args.steps, dev)
-    value = total_bytes / (ms_max / 1e3) / 1e9
+    ms_max, value = aggregate(pg, ms, bytes_per_step * args.steps, dev)
 
     # the CPU baseline: the oracle's FP64 CG on the host cores, a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -295,9 +300,22 @@ def run_ours(args):
         dt, it, cores = oracle_sample(fat_h, lng_h, b_h, args.ref_iters)
         per_iter = dt / (it + 2)
         cpu_step = per_iter * info.iters
+        # one stencil pass on all cores and on one thread, and one thread's CG iteration
+        xo = synth.spinor(DIMS, synth.rhs_seed(1)).numpy()
+        t0 = time.perf_counter()
+        oracle.dslash(DIMS, fat_h, lng_h, 0, xo)
+        pass_all = time.perf_counter() - t0
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.dslash(DIMS, fat_h, lng_h, 0, xo)
+        pass_one = time.perf_counter() - t0
+        dt1, it1, _ = oracle_sample(fat_h, lng_h, b_h, 1)
+        oracle.set_threads(cores)
         cpu = {"value": bytes_per_step / cpu_step / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"{args.ref_iters} FP64 CG iterations of the C oracle (OpenMP) on the full 32^3x64 "
-                         f"lattice, {dt:.1f} s, extrapolated to the GPU solve's {info.iters} iterations"}
+                         f"lattice, {dt:.1f} s, extrapolated to the GPU solve's {info.iters} iterations",
+               "cg_iteration_s": per_iter, "cg_iteration_s_1_thread": dt1 / (it1 + 2),
+               "stencil_pass_s": pass_all, "stencil_pass_s_1_thread": pass_one}
 
     # end to end through the ABI with host buffers
     bh = b.cpu().numpy()
