@@ -232,6 +232,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     force_shapes(args)
+    if args.fused:
+        hisq.hisq_mee_fused(1)
     ctx = hisq.hisq_create(local)
     fat, lng = synth.gauge_pair(DIMS, seed=0, device=dev)
     g = hisq.hisq_load_gauge(ctx, DIMS, fat, lng)
@@ -395,10 +397,12 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL, "delta": DELTA,
                    "sloppy": "fix16/int20/f32 r12", "l2": "no flush: every step streams >1 GB per iteration "
                    "(links 0.5 GB per stencil pass), far above the 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "m_ee": "one fused pass" if args.fused else "two stencil passes"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "dslash_kernel<FIX16, INT20, float, r12> (both passes of M_ee)",
+                     "kernel": ("mee_fused_kernel<FIX16, INT20, float, r12> (M_ee in one pass, links once)"
+                                if args.fused else "dslash_kernel<FIX16, INT20, float, r12> (both passes of M_ee)"),
                      "bytes_per_launch": per_launch_bytes, "launches": stencil.launches,
                      "launch_shapes": shapes,
                      "ms_per_launch": stencil.ms / max(1, stencil.launches)},
@@ -473,6 +477,8 @@ def run_solve_only(args):
 
     dims = tuple(int(v) for v in args.solve.split(","))
     force_shapes(args)
+    if args.fused:
+        hisq.hisq_mee_fused(1)
     ctx = hisq.hisq_create(0)
     fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
     g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
@@ -642,6 +648,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per CPU sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-formats", action="store_true", help="skip the other storage formats' solves")
+    ap.add_argument("--fused", action="store_true", help="M_ee as one fused pass (hisq_mee_fused)")
     ap.add_argument("--solve-iters", type=int, default=2866,
                     help="reference arm: iterations of one GPU solve (extrapolation unit)")
     ap.add_argument("--solve-bytes", type=float, default=3.605e12,

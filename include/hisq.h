@@ -242,6 +242,18 @@ HISQ_API void hisq_profile_select(hisq_ctx *ctx, unsigned mask);
  * Returns the previous setting, or -2 for an invalid value.  For benchmarking
  * and testing the shapes. */
 HISQ_API int hisq_stencil_config(int cfg);
+/* The normal operator M_ee as one fused pass (D_oe and D_eo swept over
+ * t-slices in one persistent kernel so that each link is read from HBM about
+ * once) instead of two stencil passes: 1 on, 0 off (default).  FP32-compute
+ * triplets, Lt <= 4096.  Returns the previous setting, or -2 for an invalid
+ * value.  Has no counterpart in the paper (a cache-blocking of its operator). */
+HISQ_API int hisq_mee_fused(int mode);
+/* Schedule of the fused pass: lag = t-slices between the last D_oe slice a
+ * D_eo slice reads and that D_eo slice in the work order (default 4; larger
+ * waits less, keeps more of the lattice in L2), blocks_per_sm = resident
+ * blocks asked per SM (0, the default: as many as fit).  Negative values leave
+ * a setting unchanged.  For benchmarking. */
+HISQ_API void hisq_mee_fused_shape(int lag, int blocks_per_sm);
 HISQ_API int hisq_stencil_config_reduce(int cfg);
 /* The shape in use for triplet p on gauge g's lattice (plain pass, or the
  * reducing pass if reduce != 0): the forced one, else the tuned one, else -1

@@ -76,21 +76,29 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
     d.in = in;
     d.out = tmp;
     d.sign = 1;
+    DslashArgs d2 = d;
+    d2.out_parity = 0;
+    d2.in = tmp;
+    d2.out = out;
+    d2.y = in;
+    d2.a = diag;
+    d2.sign = -1;
+    d2.xpay = 1;
+    d2.fin = fin;
+    if (mee_fused_available(p.gauge, p.spinor, p.compute, geom) && d2.red.sync != nullptr) {
+        // one pass: links once, plus the input, tmp and output spinors
+        const double links = 8.0 * link_bytes(p.gauge, 18) + 8.0 * link_bytes(p.gauge, p.long_recon);
+        LaunchScope ls(c, s, kind, (links + 3.0 * spinor_site_bytes(p.spinor)) * geom.vh);
+        MeeArgs m{d, d2};
+        if (launch_mee_fused(p.gauge, p.spinor, p.compute, p.long_recon, m, s)) return;
+    }
     {
         LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, false));
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, false, d, s);
     }
-    d.out_parity = 0;
-    d.in = tmp;
-    d.out = out;
-    d.y = in;
-    d.a = diag;
-    d.sign = -1;
-    d.xpay = 1;
-    d.fin = fin;
     {
         LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, true));
-        launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d, s);
+        launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d2, s);
     }
 }
 
@@ -373,6 +381,8 @@ struct CGRun {
         info->matvecs_hi += mv_hi;
         info->reliable_updates += ru;
         info->true_residual = std::sqrt(st_h->hi_rr / bb);
+        if (herr & 2)  // a bounded wait of the fused M_ee pass gave up: its results are not trusted
+            return fail(c, HISQ_ECUDA, "fused M_ee pass: a wait for earlier t-slices reached its limit");
         if (status == HISQ_ENOTCONV)
             fail(c, HISQ_ENOTCONV, "CG reached maxiter=%d with true residual %.3e", cfg.maxiter, info->true_residual);
         return status;

@@ -25,6 +25,7 @@ namespace hisq {
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+// (gather_coherent, after the Spinor codecs, reads a record through L2 only.)
 __device__ __forceinline__ int32_t sext_bits(uint32_t u, int bits)
 {
     const uint32_t m = 1u << (bits - 1);
@@ -385,21 +386,40 @@ struct LinkScaled {
     static constexpr bool value = GF == G_FIX16 || GF == G_FIX32;
 };
 
+// A spinor record read through L2 only (ld.global.cg): for fields that other
+// blocks of the same kernel write (the read-only path may not be used there).
+// Same planar layout as Spinor<SF>::gather.
+template <int SF>
+__device__ __forceinline__ void gather_coherent(const char *b, int n, int i, uint4 c[Spinor<SF>::chunks])
+{
+    constexpr int n16 = spinor_n16(SF), tail = spinor_tail(SF);
+#pragma unroll
+    for (int k = 0; k < n16; k++) c[k] = __ldcg(reinterpret_cast<const uint4 *>(b + (size_t)k * 16 * n) + i);
+    if constexpr (tail == 8) {
+        const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(b + (size_t)n16 * 16 * n) + i);
+        c[n16] = make_uint4(t.x, t.y, 0u, 0u);
+    }
+}
+
 template <int GF, int RECON>
 struct Link {
     static constexpr int n16 = link_n16(GF, RECON);
     static constexpr int tail = link_tail(GF, RECON);
     static constexpr int chunks = n16 + (tail ? 1 : 0);  // the tail chunk holds its 4 or 8 bytes first
 
-    // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16)
+    // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16).
+    // Links are read once per pass: evict-first loads, unless KEEP (a link
+    // that the same kernel applies again soon: normal priority in L2).
+    template <bool KEEP = false>
     __device__ static void gather(const char *base, size_t pstride, int li, uint4 c[chunks])
     {
+        auto ld = [](const auto *p) { return KEEP ? ld_cached(p) : ld_stream(p); };
 #pragma unroll
-        for (int k = 0; k < n16; k++) c[k] = ld_stream(reinterpret_cast<const uint4 *>(base + k * pstride) + li);
+        for (int k = 0; k < n16; k++) c[k] = ld(reinterpret_cast<const uint4 *>(base + k * pstride) + li);
         if constexpr (tail == 4) {
-            c[n16] = make_uint4(ld_stream(reinterpret_cast<const unsigned int *>(base + n16 * pstride) + li), 0u, 0u, 0u);
+            c[n16] = make_uint4(ld(reinterpret_cast<const unsigned int *>(base + n16 * pstride) + li), 0u, 0u, 0u);
         } else if constexpr (tail == 8) {
-            const uint2 t = ld_stream(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
+            const uint2 t = ld(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
             c[n16] = make_uint4(t.x, t.y, 0u, 0u);
         }
     }
@@ -465,11 +485,11 @@ struct Link {
         }
     }
 
-    template <typename real>
+    template <typename real, bool KEEP = false>
     __device__ static void load(const char *base, size_t pstride, int li, real U[18])
     {
         uint4 c[chunks];
-        gather(base, pstride, li, c);
+        gather<KEEP>(base, pstride, li, c);
         decode(c, U);
     }
 };

@@ -336,7 +336,8 @@ hisq_status hisq_create(int device, size_t hbm_budget, hisq_ctx **out)
     }
     c->budget = hbm_budget ? hbm_budget : (size_t)(0.9 * (double)fr);
     void *p = nullptr;
-    const size_t red_bytes = sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256;
+    const size_t red_bytes = sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256 +
+                             sizeof(unsigned) * kSyncWords;
     if (ctx_alloc(c, red_bytes, &p) != HISQ_OK) {
         hisq_destroy(c);
         return HISQ_ENOMEM;
@@ -345,6 +346,7 @@ hisq_status hisq_create(int device, size_t hbm_budget, hisq_ctx **out)
     c->red.result = c->red.partials + (size_t)kMaxRedBlocks * kMaxRed;
     c->red.counter = (unsigned *)(c->red.result + kMaxRed);
     c->err_flag = (int *)(c->red.counter + 16);
+    c->red.sync = c->red.counter + 64;  // 256 bytes past the counter
     cudaMemset(p, 0, red_bytes);
     cudaDeviceSynchronize();
     *out = c;

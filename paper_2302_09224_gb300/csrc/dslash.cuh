@@ -142,7 +142,19 @@ __host__ __device__ constexpr bool stencil_unrolled(int cfg) { return cfg == 0 |
 // into acc.  Fixed-point links are applied unscaled and the sum is kept in
 // units of the fat scale: a long term's spinor is multiplied by lsc/fsc (one
 // accumulator for both fields keeps registers for loads in flight).
-template <int GF, int SF, typename real, int LREC>
+template <typename real, int SF, bool COH>
+__device__ __forceinline__ void load_neighbour(const char *b, int n, int i, real s[6])
+{
+    if constexpr (COH) {
+        uint4 c[Spinor<SF>::chunks];
+        gather_coherent<SF>(b, n, i, c);
+        Spinor<SF>::decode(c, s);
+    } else {
+        Spinor<SF>::load(b, n, i, s);
+    }
+}
+
+template <int GF, int SF, typename real, int LREC, bool COH = false, bool KEEP = false>
 __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, int cmu, int c3, int lex, int cb,
                                                   int po, size_t pstride, real lsc, real ratio, int phase_sum,
                                                   SiteAcc<real> &acc)
@@ -158,33 +170,33 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     const int np3 = (base + cp3 * st) >> 1, nm3 = (base + cm3 * st) >> 1;
     real U[18], s[6];
 
-    Link<GF, 18>::load(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
-    Spinor<SF>::load(a.in, vh, np1, s);
+    Link<GF, 18>::template load<real, KEEP>(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, U);
+    load_neighbour<real, SF, COH>(a.in, vh, np1, s);
     acc.add(U, s);
 
-    Link<GF, 18>::load(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
-    Spinor<SF>::load(a.in, vh, nm1, s);
+    Link<GF, 18>::template load<real, KEEP>(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, U);
+    load_neighbour<real, SF, COH>(a.in, vh, nm1, s);
     acc.adj_sub(U, s);
 
     // row 2 of an r12 link in the units of rows 0 and 1: sign * lsc * conj(row0 x row1)
     const real eta = (phase_sum & 1) ? -lsc : lsc;
-    Link<GF, LREC>::load(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
+    Link<GF, LREC>::template load<real, KEEP>(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, U);
     if constexpr (LREC == 12) {
         const bool flip = g.antiperiodic_t && mu == 3 && c3 + 3 >= L;
         rebuild_row2(U, flip ? -eta : eta);
     }
-    Spinor<SF>::load(a.in, vh, np3, s);
+    load_neighbour<real, SF, COH>(a.in, vh, np3, s);
     if constexpr (kScaled)
 #pragma unroll
         for (int k = 0; k < 6; k++) s[k] *= ratio;
     acc.add(U, s);
 
-    Link<GF, LREC>::load(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
+    Link<GF, LREC>::template load<real, KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
     if constexpr (LREC == 12) {
         const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
         rebuild_row2(U, flip ? -eta : eta);
     }
-    Spinor<SF>::load(a.in, vh, nm3, s);
+    load_neighbour<real, SF, COH>(a.in, vh, nm3, s);
     if constexpr (kScaled)
 #pragma unroll
         for (int k = 0; k < 6; k++) s[k] *= ratio;
@@ -194,7 +206,7 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
 // One output site cb: the stencil, the optional xpay, the store and, when
 // reducing, this site's Re<y, out> and |out|^2 added to rv (in the compute
 // precision; reduce_grid sums the threads).
-template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
+template <int GF, int SF, typename real, int LREC, bool RED, int CFG, bool COH = false, bool KEEP = false>
 __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t pstride, real fsc, real lsc,
                                              real ratio, real rv[2])
 {
@@ -216,7 +228,8 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
         int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
 #pragma unroll
         for (int mu = 0; mu < 4; mu++) {
-            stencil_direction<GF, SF, real, LREC>(a, mu, c[mu], t, lex, cb, po, pstride, lsc, ratio, phase_sum, acc);
+            stencil_direction<GF, SF, real, LREC, COH, KEEP>(a, mu, c[mu], t, lex, cb, po, pstride, lsc, ratio,
+                                                             phase_sum, acc);
             phase_sum += c[mu];
         }
     } else {
@@ -224,7 +237,8 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
 #pragma unroll 1
         for (int mu = 0; mu < 4; mu++) {
             const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
-            stencil_direction<GF, SF, real, LREC>(a, mu, cmu, t, lex, cb, po, pstride, lsc, ratio, phase_sum, acc);
+            stencil_direction<GF, SF, real, LREC, COH, KEEP>(a, mu, cmu, t, lex, cb, po, pstride, lsc, ratio,
+                                                             phase_sum, acc);
             phase_sum += cmu;
         }
     }
@@ -322,6 +336,154 @@ bool launch_dslash_t(int long_recon, bool reduce, int cfg, const DslashArgs &a, 
         else
             launch_any<GF, SF, real, 18, false>(cfg, a, s);
     }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Fused M_ee pass.  Both stencil passes of M_ee = diag - D_eo D_oe read every
+// link of the lattice; run one after the other, the second reads them from
+// HBM again.  Here one persistent kernel (one wave of blocks) sweeps the
+// lattice in t-slices: D_oe of slice t into tmp, and D_eo of slice s as soon
+// as D_oe is complete on slices s-3..s+3 (the reach of the three-hop term).
+// The links D_eo(s) applies were read by D_oe a few slices earlier and are
+// still in L2, so the pass reads them from HBM about once.
+//
+// Work items (slice task, chunk of one site per thread) are handed out in a
+// fixed order by an atomic counter; a D_eo item only waits for D_oe items that
+// come earlier in that order, and D_oe items never wait, so every wait ends.
+// Each wait is also bounded: past the limit the kernel flags the error (bit 2
+// of the error word) and goes on, so a fault can cost results, never a hang.
+// The queue order puts D_eo(s) `lag` slices after the last D_oe slice it
+// reads (so that, with a wave of blocks in flight, those D_oe items have
+// mostly finished when it is taken), P = 6 + lag:
+//   Lt >= 7 + lag:  D_oe 0..P-1, then (D_oe i, D_eo i-3-lag) for i = P..Lt-1,
+//                   then D_eo 0, 1, 2, Lt-3-lag, ..., Lt-1;
+//   otherwise:      every D_oe slice, then every D_eo slice.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mee_task(int k, int Lt, int lag, int &kind, int &slice)
+{
+    const int P = 6 + lag;  // leading D_oe-only tasks
+    if (Lt < 7 + lag) {     // short lattice: every D_oe slice, then every D_eo slice
+        kind = k >= Lt;
+        slice = k - (kind ? Lt : 0);
+        return;
+    }
+    if (k < P) {
+        kind = 0;
+        slice = k;
+        return;
+    }
+    if (k < P + 2 * (Lt - P)) {  // pairs (D_oe i, D_eo i-3-lag), i = P..Lt-1
+        const int j = k - P, i = P + (j >> 1);
+        kind = j & 1;
+        slice = kind ? i - 3 - lag : i;
+        return;
+    }
+    const int m = k - P - 2 * (Lt - P);  // tail: D_eo 0, 1, 2 and Lt-3-lag..Lt-1
+    kind = 1;
+    slice = m < 3 ? m : Lt - 3 - lag + (m - 3);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr unsigned kMeeWaitPolls = 1u << 22;  // x >= 64 ns sleep: bounded well under a second
+
+template <int GF, int SF, typename real, int LREC, int CFG>
+__global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
+    mee_fused_kernel(const __grid_constant__ MeeArgs m)
+{
+    const DslashArgs &a1 = m.d1, &a2 = m.d2;
+    if (a2.active != nullptr && *(volatile const int *)a2.active == 0) return;  // uniform over the grid
+    const Geom &g = a1.g;
+    const int vh = g.vh, Lt = g.L[3];
+    const size_t pstride = (size_t)8 * vh * 16;
+    constexpr bool kScaled = LinkScaled<GF>::value;
+    const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a1.gv.fat_scale_d : (real)a1.gv.fat_scale_f) : real(1);
+    const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a1.gv.lng_scale_d : (real)a1.gv.lng_scale_f) : real(1);
+    const real ratio = lsc / fsc;
+    unsigned *work = a2.red.sync, *done = a2.red.sync + 32;
+    const int B = blockDim.x;
+    const int vs = vh / Lt;                // sites of one parity in a t-slice
+    const int nch = (vs + B - 1) / B;      // chunks per slice
+    const int nitems = 2 * Lt * nch;
+    real rv[2] = {0, 0};
+    __shared__ int item_sh;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int item = item_sh;
+        __syncthreads();  // item_sh is rewritten next round
+        if (item >= nitems) break;
+        const int task = item / nch, chunk = item - task * nch;
+        int kind, slice;
+        mee_task(task, Lt, m.lag, kind, slice);
+        const int off = chunk * B + (int)threadIdx.x;
+        const int cb = slice * vs + off;
+        if (kind == 0) {
+            // links stay in L2 for D_eo a few slices later
+            if (off < vs) stencil_site<GF, SF, real, LREC, false, CFG, false, true>(a1, cb, pstride, fsc, lsc, ratio, rv);
+            __syncthreads();  // every thread's tmp stores precede the release below
+            if (threadIdx.x == 0) red_release_add(done + slice, 1u);
+        } else {
+            if (threadIdx.x == 0) {
+                for (int d = -3; d <= 3; d++) {
+                    const int t = (slice + d + Lt) % Lt;
+                    unsigned polls = 0;
+                    while (ld_acquire(done + t) < (unsigned)nch) {
+                        if (++polls > kMeeWaitPolls) {
+                            atomicOr(a2.err, 2);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            __syncthreads();
+            // tmp is written by other blocks of this kernel: read through L2
+            if (off < vs) stencil_site<GF, SF, real, LREC, true, CFG, true>(a2, cb, pstride, fsc, lsc, ratio, rv);
+        }
+    }
+    __shared__ double tot[2];
+    if (reduce_grid<2>(rv, a2.red, tot)) {  // the last block: every item is finished
+        for (int t = threadIdx.x; t < Lt; t += B) done[t] = 0u;
+        if (threadIdx.x == 0) {
+            *work = 0u;
+            run_finisher(a2.fin, tot, a2.st, a2.slot);
+        }
+    }
+}
+
+template <int GF, int SF, typename real, int LREC, int CFG>
+void launch_mee_cfg(const MeeArgs &m, cudaStream_t s)
+{
+    constexpr int B = stencil_block(CFG);
+    auto kern = mee_fused_kernel<GF, SF, real, LREC, CFG>;
+    static const int wave = wave_blocks(kern, B);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = m.blocks_per_sm > 0 && m.blocks_per_sm * sms < wave ? m.blocks_per_sm * sms : wave;
+    kern<<<grid, B, 0, s>>>(m);
+}
+
+template <int GF, int SF, typename real>
+bool launch_mee_fused_t(int long_recon, int cfg, const MeeArgs &m, cudaStream_t s)
+{
+    // the unrolled 64-register shape only (the one the separate passes pick)
+    (void)cfg;
+    if (long_recon == 12)
+        launch_mee_cfg<GF, SF, real, 12, 4>(m, s);
+    else
+        launch_mee_cfg<GF, SF, real, 18, 4>(m, s);
     return true;
 }
 

@@ -21,6 +21,35 @@ bool launch_dslash_int20(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int30d(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int30f(int, bool, int, const DslashArgs &, cudaStream_t);
 
+bool launch_mee_f32(int, int, const MeeArgs &, cudaStream_t);
+bool launch_mee_half(int, int, const MeeArgs &, cudaStream_t);
+bool launch_mee_int20(int, int, const MeeArgs &, cudaStream_t);
+bool launch_mee_int30f(int, int, const MeeArgs &, cudaStream_t);
+
+std::atomic<int> fused_mode{0};
+
+bool mee_fused_available(int gf, int sf, int cf, const Geom &g)
+{
+    if (cf != HISQ_COMPUTE_F32 || g.L[3] > kMaxFusedLt || fused_mode.load() == 0) return false;
+    return (gf == G_F32 && sf == S_F32) || (gf == G_FIX16 && (sf == S_HALF || sf == S_INT20)) ||
+           (gf == G_FIX32 && sf == S_INT30);
+}
+
+extern std::atomic<int> fused_lag, fused_bps;
+
+bool launch_mee_fused(int gf, int sf, int cf, int long_recon, const MeeArgs &m_in, cudaStream_t s)
+{
+    if (!mee_fused_available(gf, sf, cf, m_in.d1.g) || m_in.d2.red.sync == nullptr) return false;
+    MeeArgs m = m_in;
+    m.lag = fused_lag.load();
+    m.blocks_per_sm = fused_bps.load();
+    const int cfg = 4;
+    if (gf == G_F32) return launch_mee_f32(long_recon, cfg, m, s);
+    if (sf == S_HALF) return launch_mee_half(long_recon, cfg, m, s);
+    if (sf == S_INT20) return launch_mee_int20(long_recon, cfg, m, s);
+    return launch_mee_int30f(long_recon, cfg, m, s);
+}
+
 namespace {
 
 bool launch_with(int gf, int sf, int cf, int lrec, bool red, int cfg, const DslashArgs &a, cudaStream_t s)
@@ -173,6 +202,22 @@ extern "C" int hisq_stencil_config_in_use(const hisq_gauge *g, hisq_prec p, int 
 {
     if (!g) return -1;
     return hisq::stencil_config_in_use(p.gauge, p.spinor, p.compute, p.long_recon, reduce != 0, g->geom);
+}
+
+extern "C" int hisq_mee_fused(int mode)
+{
+    if (mode < 0 || mode > 1) return -2;
+    return hisq::fused_mode.exchange(mode);
+}
+
+namespace hisq {
+std::atomic<int> fused_lag{4}, fused_bps{0};
+}
+
+extern "C" void hisq_mee_fused_shape(int lag, int blocks_per_sm)
+{
+    if (lag >= 0) hisq::fused_lag.store(lag);
+    if (blocks_per_sm >= 0) hisq::fused_bps.store(blocks_per_sm);
 }
 
 extern "C" int hisq_stencil_config(int cfg)

@@ -6,4 +6,8 @@ bool launch_dslash_half(int long_recon, bool reduce, int cfg, const DslashArgs &
 {
     return launch_dslash_t<G_FIX16, S_HALF, float>(long_recon, reduce, cfg, a, s);
 }
+bool launch_mee_half(int long_recon, int cfg, const MeeArgs &m, cudaStream_t s)
+{
+    return launch_mee_fused_t<G_FIX16, S_HALF, float>(long_recon, cfg, m, s);
+}
 }  // namespace hisq

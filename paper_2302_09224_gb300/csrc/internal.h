@@ -70,7 +70,11 @@ struct RedBuf {
     double *partials;        // kMaxRedBlocks * kMaxRed values: nr per block of a launch
     unsigned int *counter;   // zero between launches
     double *result;          // [kMaxRed] written by the last block
+    unsigned int *sync;      // fused M_ee pass: [0] items handed out, [32 + t] finished chunks of
+                             // slice t (kMaxFusedLt slices); zero between launches
 };
+constexpr int kMaxFusedLt = 4096;
+constexpr size_t kSyncWords = 32 + kMaxFusedLt;
 
 // Whether a reducing launch over n sites (blocks of `block` threads, gy grid
 // rows, nr values per block) fits the partials buffer.
@@ -177,6 +181,15 @@ struct DslashArgs {
     int slot;               // ring slot handed to the finisher
 };
 
+// The fused M_ee pass (d1: D_oe into tmp; d2: D_eo from tmp with xpay and the
+// reduction), scheduled in t-slices through red.sync.
+struct MeeArgs {
+    DslashArgs d1;
+    DslashArgs d2;
+    int lag;            // slices between the last D_oe a D_eo slice reads and that D_eo
+    int blocks_per_sm;  // resident blocks per SM asked (0: as many as fit)
+};
+
 // A tile of right-hand sides for the batched stencil: right-hand side t lives
 // in the fields at in/out/y + t * field_bytes.
 constexpr int kMaxRHS = 16;
@@ -221,6 +234,10 @@ bool launch_dslash_mrhs(int gf, int sf, int cf, int long_recon, bool reduce, int
 // outside stream capture.
 void tune_dslash(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
 int stencil_config(int gf, int sf, int cf, int long_recon, bool reduce, const Geom &g);
+// The fused M_ee pass (red.sync must be set); false when the triplet or the
+// lattice has none, or it is switched off (hisq_mee_fused).
+bool mee_fused_available(int gf, int sf, int cf, const Geom &g);
+bool launch_mee_fused(int gf, int sf, int cf, int long_recon, const MeeArgs &m, cudaStream_t s);
 int stencil_config_in_use(int gf, int sf, int cf, int long_recon, bool reduce, const Geom &g);
 
 void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);

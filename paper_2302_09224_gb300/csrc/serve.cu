@@ -275,7 +275,8 @@ void Server::worker(int id)
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     // this thread's reduction buffer and error flag
     void *buf = nullptr;
-    const size_t red_bytes = sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256;
+    const size_t red_bytes = sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256 +
+                             sizeof(unsigned) * kSyncWords;
     Lane lane{};
     if (ctx_alloc(c, red_bytes, &buf) == HISQ_OK) {
         cudaMemset(buf, 0, red_bytes);
@@ -283,6 +284,7 @@ void Server::worker(int id)
         lane.red.result = lane.red.partials + (size_t)kMaxRedBlocks * kMaxRed;
         lane.red.counter = (unsigned *)(lane.red.result + kMaxRed);
         lane.err = (int *)(lane.red.counter + 16);
+        lane.red.sync = lane.red.counter + 64;
         set_thread_lane(&lane);
     }
     std::unique_lock<std::mutex> lk(mu);

@@ -129,6 +129,8 @@ _SIGS = {
     "hisq_launch_count": (_I64, [_P]),
     "hisq_stencil_config": (_I, [_I]),
     "hisq_stencil_config_reduce": (_I, [_I]),
+    "hisq_mee_fused": (_I, [_I]),
+    "hisq_mee_fused_shape": (None, [_I, _I]),
     "hisq_stencil_config_in_use": (_I, [_P, hisq_prec, _I]),
     "hisq_default_params": (None, [ctypes.POINTER(hisq_solver_params)]),
     "hisq_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P, ctypes.POINTER(hisq_solve_info)]),
@@ -295,6 +297,14 @@ def hisq_profile_read(ctx, kind: int) -> hisq_kernel_stats:
 
 def hisq_stencil_config(cfg: int) -> int:
     return int(lib().hisq_stencil_config(int(cfg)))
+
+
+def hisq_mee_fused(mode: int) -> int:
+    return int(lib().hisq_mee_fused(int(mode)))
+
+
+def hisq_mee_fused_shape(lag: int, blocks_per_sm: int):
+    lib().hisq_mee_fused_shape(int(lag), int(blocks_per_sm))
 
 
 def hisq_stencil_config_reduce(cfg: int) -> int:
