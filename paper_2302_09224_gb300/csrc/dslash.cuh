@@ -269,10 +269,8 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
     if (!Spinor<SF>::store(a.out, vh, cb, o)) atomicExch(a.err, 1);
 }
 
-// A plain pass runs one thread per site.  A reducing pass runs one wave of
-// blocks (every block resident at once) over the sites with a grid-stride
-// loop: the end of a reducing block (block sum, partial store, fence, counter)
-// is then paid once per resident block instead of once per 128 sites.
+// One thread per site.  A reducing pass ends each block with its block sum
+// and a partial store; stencil_finish_kernel, launched after it, sums them.
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)
@@ -286,14 +284,25 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
     const real ratio = lsc / fsc;
     real rv[2] = {0, 0};
-    if constexpr (RED) {
-        for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < vh; cb += gridDim.x * blockDim.x)
-            stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
-        __shared__ double tot[2];
-        if (reduce_grid<2>(rv, a.red, tot) && threadIdx.x == 0) run_finisher(a.fin, tot, a.st, a.slot);
-    } else {
-        const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-        if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
+    if constexpr (RED) store_block_partial<2, real>(rv, a.red);  // summed by stencil_finish_kernel
+}
+
+// After a reducing pass: one block sums the pass's block partials and runs the
+// solver's finisher (a separate launch instead of a completion counter in
+// every block of the pass: no fence or atomic ends a stencil block).
+template <typename real>
+__global__ void __launch_bounds__(1024) stencil_finish_kernel(RedBuf red, unsigned nblocks, int fin, void *st,
+                                                               int slot, const int *active)
+{
+    if (active != nullptr && *(volatile const int *)active == 0) return;
+    __shared__ double tot[2];
+    sum_partials<2, real>(red, nblocks, tot);
+    if (threadIdx.x == 0) {
+        red.result[0] = tot[0];
+        red.result[1] = tot[1];
+        run_finisher(fin, tot, st, slot);
     }
 }
 
@@ -301,13 +310,9 @@ template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 void launch_cfg(const DslashArgs &a, cudaStream_t s)
 {
     constexpr int B = stencil_block(CFG);
-    auto kern = dslash_kernel<GF, SF, real, LREC, RED, CFG>;
-    int nb = (a.g.vh + B - 1) / B;
-    if constexpr (RED) {
-        static const int wave = wave_blocks(kern, B);  // one device model per process
-        nb = nb < wave ? nb : wave;
-    }
-    kern<<<nb, B, 0, s>>>(a);
+    const int nb = (a.g.vh + B - 1) / B;
+    dslash_kernel<GF, SF, real, LREC, RED, CFG><<<nb, B, 0, s>>>(a);
+    if constexpr (RED) stencil_finish_kernel<real><<<1, 1024, 0, s>>>(a.red, (unsigned)nb, a.fin, a.st, a.slot, a.active);
 }
 
 template <int GF, int SF, typename real, int LREC, bool RED>

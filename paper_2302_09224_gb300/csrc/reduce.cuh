@@ -71,40 +71,14 @@ __device__ __forceinline__ void warp_sum_ff(FF v[NR])
         }
 }
 
-// Returns true in every thread of the last block, with the grid totals in
-// `tot` (shared memory).  All threads of every block must call it.  Grids may
-// be two-dimensional (blocks are numbered x fastest).
-//
-// FP64 values (FP64 compute) are summed in FP64 throughout.  FP32 values (one
-// thread's sites formed in the FP32 compute precision) are summed in FP32 up
-// to the block, each block storing one FP32 partial; the last block sums the
-// partials in the FP32 pair arithmetic above and returns hi + lo in FP64.  On
-// GB300 the FP64 pipe issues a small fraction of the FP32 rate, so FP64
-// arithmetic in every block (or a long FP64 chain in the last one) dominated
-// the short reducing kernels.
+// One block sums the partials of nblocks blocks (in a fixed order) into tot
+// (shared memory), valid in thread 0: FP64 partials in FP64, FP32 partials in
+// the FP32 pair arithmetic.
 template <int NR, typename T>
-__device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
+__device__ void sum_partials(const RedBuf &rb, unsigned nblocks, double *tot)
 {
-    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "float or double");
     __shared__ T sh[32][NR];
-    __shared__ int is_last;
-    const unsigned nblocks = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-    T *part = reinterpret_cast<T *>(rb.partials);
-    T v[NR];
-#pragma unroll
-    for (int k = 0; k < NR; k++) v[k] = vin[k];
-    block_sum<NR, T>(v, sh);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = v[k];
-        __threadfence();
-        const unsigned prev = atomicAdd(rb.counter, 1u);
-        is_last = (prev == nblocks - 1);
-    }
-    __syncthreads();
-    if (!is_last) return false;
-    __threadfence();
+    const T *part = reinterpret_cast<const T *>(rb.partials);
     // every block's partials: coherent L2 loads (ld.cg), U rows per thread in
     // flight at once (one L2 round trip per U rows); the order is fixed
     constexpr int U = NR <= 4 ? 8 : NR <= 8 ? 4 : 1;
@@ -164,6 +138,43 @@ __device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
                 for (int k = 0; k < NR; k++) tot[k] = (double)w[k].hi + (double)w[k].lo;
         }
     }
+}
+
+// Returns true in every thread of the last block, with the grid totals in
+// `tot` (shared memory).  All threads of every block must call it.  Grids may
+// be two-dimensional (blocks are numbered x fastest).
+//
+// FP64 values (FP64 compute) are summed in FP64 throughout.  FP32 values (one
+// thread's sites formed in the FP32 compute precision) are summed in FP32 up
+// to the block, each block storing one FP32 partial; the last block sums the
+// partials in the FP32 pair arithmetic above and returns hi + lo in FP64.  On
+// GB300 the FP64 pipe issues a small fraction of the FP32 rate, so FP64
+// arithmetic in every block (or a long FP64 chain in the last one) dominated
+// the short reducing kernels.
+template <int NR, typename T>
+__device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "float or double");
+    __shared__ T sh[32][NR];
+    __shared__ int is_last;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    T *part = reinterpret_cast<T *>(rb.partials);
+    T v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) v[k] = vin[k];
+    block_sum<NR, T>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = v[k];
+        __threadfence();
+        const unsigned prev = atomicAdd(rb.counter, 1u);
+        is_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    sum_partials<NR, T>(rb, nblocks, tot);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NR; k++) rb.result[k] = tot[k];
@@ -185,6 +196,24 @@ int wave_blocks(K kernel, int block)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0);
     return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+}
+
+// Only this block's share: its sums stored at its index of rb.partials, no
+// completion counter (a separate one-block kernel sums them after the launch).
+template <int NR, typename T>
+__device__ void store_block_partial(const T vin[NR], const RedBuf &rb)
+{
+    __shared__ T sh[32][NR];
+    T v[NR];
+#pragma unroll
+    for (int k = 0; k < NR; k++) v[k] = vin[k];
+    block_sum<NR, T>(v, sh);
+    if (threadIdx.x == 0) {
+        T *part = reinterpret_cast<T *>(rb.partials);
+        const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = v[k];
+    }
 }
 
 }  // namespace hisq
