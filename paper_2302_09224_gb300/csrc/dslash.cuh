@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
         if (threadIdx.x == 0) item_sh = (int)atomicAdd(work, 1u);
         __syncthreads();
         const int item = item_sh;
-        __syncthreads();  // item_sh is rewritten next round
+        __syncthreads();  // item_sh is rewritten by the next fetch
         if (item >= nitems) break;
         const int task = item / nch, chunk = item - task * nch;
         int kind, slice;
