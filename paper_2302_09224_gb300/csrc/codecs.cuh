@@ -18,6 +18,7 @@
 
 #include <cstdint>
 
+#include "ff.cuh"
 #include "internal.h"
 
 namespace hisq {
@@ -300,7 +301,11 @@ struct Spinor<S_INT30> {
         const uint32_t E = (a.x >> 30) | ((a.y >> 30) << 2) | ((a.z >> 30) << 4) | ((a.w >> 30) << 6);
         const int32_t q[6] = {sext_bits(a.x, 30), sext_bits(a.y, 30), sext_bits(a.z, 30),
                               sext_bits(a.w, 30), sext_bits(c[1].x, 30), sext_bits(c[1].y, 30)};
-        if constexpr (sizeof(real) == 8) {
+        if constexpr (is_ff<real>::value) {  // exact: q as an FP32 pair, times a power of two
+            const float up = __uint_as_float(E << 23);
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = ff_scale(ff_from_int(q[k]), up);
+        } else if constexpr (sizeof(real) == 8) {
             const double up = __longlong_as_double((long long)(E + 896u) << 52);  // 2^(E-127)
 #pragma unroll
             for (int k = 0; k < 6; k++) v[k] = __dmul_rn((double)q[k], up);
@@ -477,7 +482,9 @@ struct Link {
             }
 #pragma unroll
             for (int k = 0; k < RECON; k++) {
-                if constexpr (sizeof(real) == 8)
+                if constexpr (is_ff<real>::value)
+                    U[k] = ff_from_int(q[k]);
+                else if constexpr (sizeof(real) == 8)
                     U[k] = (double)q[k];
                 else
                     U[k] = __int2float_rn(q[k]);

@@ -271,6 +271,11 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
 
 // One thread per site.  A reducing pass ends each block with its block sum
 // and a partial store; stencil_finish_kernel, launched after it, sums them.
+// Type of the per-block sums: FP32 pairs are summed as FP64 (one conversion
+// per thread; shuffles and partials take plain scalars).
+template <typename real>
+using red_t = std::conditional_t<is_ff<real>::value, double, real>;
+
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)
@@ -283,10 +288,13 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     const real fsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.fat_scale_d : (real)a.gv.fat_scale_f) : real(1);
     const real lsc = kScaled ? (sizeof(real) == 8 ? (real)a.gv.lng_scale_d : (real)a.gv.lng_scale_f) : real(1);
     const real ratio = lsc / fsc;
-    real rv[2] = {0, 0};
+    real rv[2] = {real(0), real(0)};
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
-    if constexpr (RED) store_block_partial<2, real>(rv, a.red);  // summed by stencil_finish_kernel
+    if constexpr (RED) {  // summed by stencil_finish_kernel
+        const red_t<real> r2[2] = {(red_t<real>)rv[0], (red_t<real>)rv[1]};
+        store_block_partial<2, red_t<real>>(r2, a.red);
+    }
 }
 
 // After a reducing pass: one block sums the pass's block partials and runs the
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(1024) stencil_finish_kernel(RedBuf red, unsign
 {
     if (active != nullptr && *(volatile const int *)active == 0) return;
     __shared__ double tot[2];
-    sum_partials<2, real>(red, nblocks, tot);
+    sum_partials<2, red_t<real>>(red, nblocks, tot);
     if (threadIdx.x == 0) {
         red.result[0] = tot[0];
         red.result[1] = tot[1];
