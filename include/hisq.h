@@ -196,6 +196,13 @@ HISQ_API size_t hisq_spinor_bytes(int sfmt, int64_t n);
 HISQ_API hisq_status hisq_spinor_pack(hisq_ctx *ctx, int sfmt, int64_t n, const double *in, void *packed,
                              int64_t *n_bad, void *stream);
 
+/* Encode n sites of FP32 [n][6] input (device) into format sfmt (F32, HALF16,
+ * INT20 or INT30) exactly as the FP32-compute kernels store a field; for
+ * INT30 the bits equal those of hisq_spinor_pack on the same (FP32-exact)
+ * values.  *n_bad counts non-finite sites (stored as zero). */
+HISQ_API hisq_status hisq_spinor_pack32(hisq_ctx *ctx, int sfmt, int64_t n, const float *in, void *packed,
+                               int64_t *n_bad, void *stream);
+
 /* Decode n sites of format sfmt into FP64 [n][6] (device pointers).  compute
  * selects the precision of the decode (F32 decodes as the F32 kernels do). */
 HISQ_API hisq_status hisq_spinor_unpack(hisq_ctx *ctx, int sfmt, int compute, int64_t n, const void *packed,

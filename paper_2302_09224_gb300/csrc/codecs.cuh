@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "ff.cuh"
 #include "internal.h"
@@ -322,9 +323,50 @@ struct Spinor<S_INT30> {
         gather(b, n, i, c);
         decode(c, v);
     }
+    // FP32 values, the same bits as the FP64 rule without FP64 arithmetic: for
+    // a site maximum mx = m 2^(f-127) (f its exponent field, m < 2 - 2^-23)
+    // the FP64 quotient mx/(2^29-1) = m (1 + 1/(2^29-1)) 2^(f-156) stays below
+    // 2^(f-155) (m (1 + 2^-29) < 2 - 2^-53), so its exponent gives E = f - 28
+    // (subnormal or small mx: E = 1); v 2^(127-E) is then exact in FP32 (a
+    // power of two, magnitude below 2^29) and rounds to the same integer.
+    __device__ static bool store_f32(char *b, int n, int i, const float v[6])
+    {
+        float mx = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            ok = ok && isfinite(v[k]);
+            mx = fmaxf(mx, fabsf(v[k]));
+        }
+        uint32_t E = 1;
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        if (ok) {
+            const int f = (int)((__float_as_uint(mx) >> 23) & 0xffu);
+            E = (uint32_t)(f > 29 ? f - 28 : 1);
+            // 2^(127-E), E in [1, 226]: a normal FP32 power of two
+            const float down = __uint_as_float((254u - E) << 23);
+#pragma unroll
+            for (int k = 0; k < 6; k++) u[k] = (uint32_t)__float2int_rn(fmul(v[k], down));
+        }
+        pack(b, n, i, E, u);
+        return ok;
+    }
+
+    __device__ static void pack(char *b, int n, int i, uint32_t E, const uint32_t u[6])
+    {
+        uint4 a;
+        a.x = (u[0] & 0x3fffffffu) | ((E & 3u) << 30);
+        a.y = (u[1] & 0x3fffffffu) | (((E >> 2) & 3u) << 30);
+        a.z = (u[2] & 0x3fffffffu) | (((E >> 4) & 3u) << 30);
+        a.w = (u[3] & 0x3fffffffu) | (((E >> 6) & 3u) << 30);
+        reinterpret_cast<uint4 *>(b)[i] = a;
+        reinterpret_cast<uint2 *>(b + (size_t)16 * n)[i] = make_uint2(u[4] & 0x3fffffffu, u[5] & 0x3fffffffu);
+    }
+
     template <typename real>
     __device__ static bool store(char *b, int n, int i, const real v[6])
     {
+        if constexpr (std::is_same<real, float>::value) return store_f32(b, n, i, v);
         double d[6];
         double mx = 0.0;
         bool ok = true;
@@ -349,13 +391,7 @@ struct Spinor<S_INT30> {
                 for (int k = 0; k < 6; k++) u[k] = (uint32_t)(int32_t)__double2ll_rn(__dmul_rn(d[k], down));
             }
         }
-        uint4 a;
-        a.x = (u[0] & 0x3fffffffu) | ((E & 3u) << 30);
-        a.y = (u[1] & 0x3fffffffu) | (((E >> 2) & 3u) << 30);
-        a.z = (u[2] & 0x3fffffffu) | (((E >> 4) & 3u) << 30);
-        a.w = (u[3] & 0x3fffffffu) | (((E >> 6) & 3u) << 30);
-        reinterpret_cast<uint4 *>(b)[i] = a;
-        reinterpret_cast<uint2 *>(b + (size_t)16 * n)[i] = make_uint2(u[4] & 0x3fffffffu, u[5] & 0x3fffffffu);
+        pack(b, n, i, E, u);
         return ok;
     }
 };

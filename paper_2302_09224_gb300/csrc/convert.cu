@@ -25,6 +25,18 @@ __global__ void pack_kernel(int64_t n, const double *in, char *out, int *bad)
     if (!Spinor<SF>::store(out, (int)n, (int)i, v)) atomicAdd(bad, 1);
 }
 
+// FP32 input through the FP32 store (the one FP32-compute kernels use)
+template <int SF>
+__global__ void pack32_kernel(int64_t n, const float *in, char *out, int *bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = in[6 * i + k];
+    if (!Spinor<SF>::store(out, (int)n, (int)i, v)) atomicAdd(bad, 1);
+}
+
 template <int SF, typename real>
 __global__ void unpack_kernel(int64_t n, const char *in, double *out)
 {
@@ -185,6 +197,19 @@ void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *bad
     case S_HALF: pack_kernel<S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT20: pack_kernel<S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT30: pack_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    default: break;
+    }
+}
+
+void launch_pack32_spinor(int sf, int64_t n, const float *in, char *out, int *bad, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nb = nblocks(n, kBlock);
+    switch (sf) {
+    case S_F32: pack32_kernel<S_F32><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_HALF: pack32_kernel<S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT20: pack32_kernel<S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT30: pack32_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     default: break;
     }
 }

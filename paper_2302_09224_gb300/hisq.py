@@ -121,6 +121,7 @@ _SIGS = {
     "hisq_dslash_noalloc": (_I, [_P, _P, hisq_prec, _I, _D, _P, _P, _P, _P]),
     "hisq_spinor_bytes": (_SZ, [_I, _I64]),
     "hisq_spinor_pack": (_I, [_P, _I, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
+    "hisq_spinor_pack32": (_I, [_P, _I, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
     "hisq_spinor_unpack": (_I, [_P, _I, _I, _I64, _P, _P, _P]),
     "hisq_profile_enable": (None, [_P, _I]),
     "hisq_profile_reset": (None, [_P]),
@@ -269,6 +270,13 @@ def hisq_spinor_pack(ctx, sfmt: int, n: int, x, packed, stream=None) -> int:
     bad = _I64(0)
     _check(ctx, lib().hisq_spinor_pack(ctx, int(sfmt), int(n), _ptr(x), _ptr(packed), ctypes.byref(bad),
                                        _stream(stream)))
+    return int(bad.value)
+
+
+def hisq_spinor_pack32(ctx, sfmt: int, n: int, x, packed, stream=None) -> int:
+    bad = _I64(0)
+    _check(ctx, lib().hisq_spinor_pack32(ctx, int(sfmt), int(n), _ptr(x), _ptr(packed), ctypes.byref(bad),
+                                         _stream(stream)))
     return int(bad.value)
 
 

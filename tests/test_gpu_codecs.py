@@ -74,6 +74,35 @@ def test_int30_bit_exact(ctx, orc, n):
     np.testing.assert_array_equal(np.concatenate([a, b], axis=1), w)
 
 
+@pytest.mark.parametrize("n", [16, 4096 + 13])
+def test_fp32_store_path_bit_exact(ctx, orc, n):
+    """The FP32-input store (what FP32-compute kernels write) against the
+    oracle's FP64 codecs on the same FP32-exact values: 30-bit records are
+    derived there without FP64 arithmetic and must still match bit for bit."""
+    v = sites(n, 300 + n)
+    v[9] = [1e-30, 2e-44, 0, 0, 0, 0]                 # tiny site maximum: exponent clamped to 1
+    v[13] = [np.nextafter(np.float32(2), np.float32(0)), 1, 0, 0, 0, 0]   # largest FP32 significand
+    with np.errstate(over="ignore"):
+        f = v.astype(np.float32)
+    x = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    for fmt in (hisq.HISQ_SPINOR_INT30, hisq.HISQ_SPINOR_INT20, hisq.HISQ_SPINOR_HALF16):
+        buf = torch.zeros(hisq.hisq_spinor_bytes(fmt, n), dtype=torch.uint8, device="cuda")
+        bad = hisq.hisq_spinor_pack32(ctx, fmt, n, x, buf)
+        got = buf.cpu().numpy()
+        if fmt == hisq.HISQ_SPINOR_INT30:
+            w, obad = orc.int30_pack(f.astype(np.float64))
+            a = got[:16 * n].view(np.uint32).reshape(n, 4)
+            b = got[16 * n:].view(np.uint32).reshape(n, 2)
+            np.testing.assert_array_equal(np.concatenate([a, b], axis=1), w)
+        elif fmt == hisq.HISQ_SPINOR_INT20:
+            w, obad = orc.int20_pack(f)
+            np.testing.assert_array_equal(got.view(np.uint32).reshape(-1, 4), w)
+        else:
+            w, obad = orc.half_pack(f)
+            np.testing.assert_array_equal(got.reshape(-1, 16), w)
+        assert bad == obad
+
+
 def test_f32_f64_layouts(ctx):
     n = 1000
     v = sites(n, 7)[20:]
