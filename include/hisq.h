@@ -203,6 +203,14 @@ HISQ_API hisq_status hisq_spinor_pack(hisq_ctx *ctx, int sfmt, int64_t n, const 
 HISQ_API hisq_status hisq_spinor_pack32(hisq_ctx *ctx, int sfmt, int64_t n, const float *in, void *packed,
                                int64_t *n_bad, void *stream);
 
+/* Encode n sites given as FP32 pairs [n][6][hi, lo] (value hi + lo, |lo| at
+ * most half an ulp of hi; device) into INT30 exactly as the FP64-class
+ * kernels store a field: the 30-bit rule applied to the exact value hi + lo,
+ * so the bits equal those of hisq_spinor_pack wherever hi + lo is exact in
+ * FP64. */
+HISQ_API hisq_status hisq_spinor_pack_pair_int30(hisq_ctx *ctx, int64_t n, const float *in, void *packed,
+                                        int64_t *n_bad, void *stream);
+
 /* Decode n sites of format sfmt into FP64 [n][6] (device pointers).  compute
  * selects the precision of the decode (F32 decodes as the F32 kernels do). */
 HISQ_API hisq_status hisq_spinor_unpack(hisq_ctx *ctx, int sfmt, int compute, int64_t n, const void *packed,

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 {
     if (skip(a.active)) return;
     constexpr int U = kRSites, C = Spinor<SF>::chunks;
-    real v[2] = {0, 0};
+    red_t<real> v[2] = {0, 0};
     const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
     // one wave of blocks loops over groups of U sites per thread (see wave_blocks)
     for (int i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < a.n; i0 += gridDim.x * blockDim.x * U) {
@@ -58,15 +58,15 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
             real r[6], ap[6], rn[6];
             Spinor<SF>::decode(cr[u], r);
             Spinor<SF>::decode(ca[u], ap);
-            real n2 = 0, d = 0;  // in the compute precision; reduce_grid sums the threads
+            real n2 = real(0), d = real(0);  // in the compute precision; reduce_grid sums the threads
 #pragma unroll
             for (int k = 0; k < 6; k++) {
                 rn[k] = r[k] - alpha * ap[k];
                 n2 += rn[k] * rn[k];
                 d += rn[k] * r[k];
             }
-            v[0] += n2;
-            v[1] += d;
+            v[0] += (red_t<real>)n2;
+            v[1] += (red_t<real>)d;
             if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
         }
     }
@@ -246,9 +246,9 @@ void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
     case S_F32: r_update_t<S_F32, float>(a, s); break;
     case S_HALF: r_update_t<S_HALF, float>(a, s); break;
     case S_INT20: r_update_t<S_INT20, float>(a, s); break;
-    case S_INT30:
+    case S_INT30:  // FP64-class compute in FP32 pairs (see ff.cuh)
         if (cf == HISQ_COMPUTE_F64)
-            r_update_t<S_INT30, double>(a, s);
+            r_update_t<S_INT30, ff>(a, s);
         else
             r_update_t<S_INT30, float>(a, s);
         break;
@@ -257,7 +257,12 @@ void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 
 void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, (a.n + kBlock * kPSites - 1) / (kBlock * kPSites), kBlock, 0, s);
+    const int nb = (a.n + kBlock * kPSites - 1) / (kBlock * kPSites);
+    if (sf == S_INT30 && cf == HISQ_COMPUTE_F64) {  // FP64-class compute in FP32 pairs
+        p_update_kernel<S_INT30, ff><<<nb, kBlock, 0, s>>>(a);
+        return;
+    }
+    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, nb, kBlock, 0, s);
 }
 
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)

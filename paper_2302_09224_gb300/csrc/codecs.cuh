@@ -352,6 +352,59 @@ struct Spinor<S_INT30> {
         return ok;
     }
 
+    // FP32-pair values (FP64-class compute), the 30-bit rule on the exact value
+    // hi + lo without FP64 arithmetic.  Exponent: as store_f32 from hi's
+    // exponent field f (E = f - 28), except that a power-of-two hi with an
+    // opposite-sign lo larger than 2^(p-29) (p the exponent of hi) lies in
+    // the binade below (E = f - 29).  Integer: round-to-nearest-even of the
+    // scaled pair, exactly: r = rint(hi'), then the exact remainder
+    // (hi' - r) + lo' (TwoSum) rounded the same way in a second stage.
+    __device__ static bool store_ff(char *b, int n, int i, const ff v[6])
+    {
+        bool ok = true;
+        int km = 0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            ok = ok && isfinite(v[k].hi) && isfinite(v[k].lo);
+            // the larger magnitude: |hi|, then the lo with hi's sign
+            const float a = fabsf(v[k].hi), am = fabsf(v[km].hi);
+            const float l = copysignf(1.0f, v[k].hi) * v[k].lo, lm = copysignf(1.0f, v[km].hi) * v[km].lo;
+            if (a > am || (a == am && l > lm)) km = k;
+        }
+        uint32_t E = 1;
+        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        if (ok) {
+            const ff m = v[km];
+            const uint32_t bits = __float_as_uint(fabsf(m.hi));
+            const int f = (int)(bits >> 23);
+            int e = f - 28;
+            if ((bits & 0x7fffffu) == 0u && f > 0 && m.lo != 0.0f && ((m.lo < 0.0f) != (m.hi < 0.0f))) {
+                const float thr = f >= 30 ? __uint_as_float((uint32_t)(f - 29) << 23) : 0.0f;  // 2^(p-29)
+                if (fabsf(m.lo) > thr) e -= 1;
+            }
+            E = (uint32_t)(e > 1 ? e : 1);
+            const float down = __uint_as_float((254u - E) << 23);  // 2^(127-E)
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const float xh = fmul(v[k].hi, down), xl = fmul(v[k].lo, down);
+                const float r = rintf(xh);
+                const ff se = ff_two_sum(__fsub_rn(xh, r), xl);  // exact remainder
+                const float kk = rintf(se.hi);
+                const ff uw = ff_two_sum(__fsub_rn(se.hi, kk), se.lo);
+                int q = __float2int_rn(r) + __float2int_rn(kk);
+                if (uw.hi > 0.5f || (uw.hi == 0.5f && uw.lo > 0.0f))
+                    q += 1;
+                else if (uw.hi < -0.5f || (uw.hi == -0.5f && uw.lo < 0.0f))
+                    q -= 1;
+                else if (uw.lo == 0.0f && (uw.hi == 0.5f || uw.hi == -0.5f) && (q & 1))
+                    q += uw.hi > 0.0f ? 1 : -1;  // a tie: to the even neighbour
+                u[k] = (uint32_t)q;
+            }
+        }
+        pack(b, n, i, E, u);
+        return ok;
+    }
+
     __device__ static void pack(char *b, int n, int i, uint32_t E, const uint32_t u[6])
     {
         uint4 a;
@@ -367,6 +420,7 @@ struct Spinor<S_INT30> {
     __device__ static bool store(char *b, int n, int i, const real v[6])
     {
         if constexpr (std::is_same<real, float>::value) return store_f32(b, n, i, v);
+        if constexpr (is_ff<real>::value) return store_ff(b, n, i, v);
         double d[6];
         double mx = 0.0;
         bool ok = true;

@@ -530,6 +530,27 @@ hisq_status hisq_spinor_pack32(hisq_ctx *c, int sfmt, int64_t n, const float *in
     return HISQ_OK;
 }
 
+hisq_status hisq_spinor_pack_pair_int30(hisq_ctx *c, int64_t n, const float *in, void *packed, int64_t *n_bad,
+                                        void *stream)
+{
+    if (!c || !in || !packed || n < 0 || n > INT32_MAX)
+        return fail(c, HISQ_EINVAL, "hisq_spinor_pack_pair_int30: bad argument");
+    cudaSetDevice(c->device);
+    cudaStream_t s = pick_stream(c, stream);
+    int *bad = cur_err(c);
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
+    {
+        LaunchScope ls(c, s, PROF_CONVERT, (48.0 + spinor_site_bytes(S_INT30)) * n);
+        launch_pack_pair_int30(n, in, (char *)packed, bad, s);
+    }
+    int h = 0;
+    cudaMemcpyAsync(&h, bad, sizeof h, cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hisq_spinor_pack_pair_int30");
+    if (n_bad) *n_bad = h;
+    return HISQ_OK;
+}
+
 hisq_status hisq_spinor_unpack(hisq_ctx *c, int sfmt, int compute, int64_t n, const void *packed, double *out,
                                void *stream)
 {

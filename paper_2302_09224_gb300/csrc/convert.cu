@@ -37,6 +37,17 @@ __global__ void pack32_kernel(int64_t n, const float *in, char *out, int *bad)
     if (!Spinor<SF>::store(out, (int)n, (int)i, v)) atomicAdd(bad, 1);
 }
 
+// FP32-pair input [n][6][hi, lo] through the pair store (FP64-class kernels)
+__global__ void pack_pair_kernel(int64_t n, const float *in, char *out, int *bad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ff v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ff(in[12 * i + 2 * k], in[12 * i + 2 * k + 1]);
+    if (!Spinor<S_INT30>::store(out, (int)n, (int)i, v)) atomicAdd(bad, 1);
+}
+
 template <int SF, typename real>
 __global__ void unpack_kernel(int64_t n, const char *in, double *out)
 {
@@ -212,6 +223,12 @@ void launch_pack32_spinor(int sf, int64_t n, const float *in, char *out, int *ba
     case S_INT30: pack32_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     default: break;
     }
+}
+
+void launch_pack_pair_int30(int64_t n, const float *in, char *out, int *bad, cudaStream_t s)
+{
+    if (n <= 0) return;
+    pack_pair_kernel<<<nblocks(n, kBlock), kBlock, 0, s>>>(n, in, out, bad);
 }
 
 void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s)

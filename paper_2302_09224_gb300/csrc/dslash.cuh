@@ -122,8 +122,60 @@ struct SiteAccPacked {
     }
 };
 
+// FP32-pair accumulator (FP64-class compute): each product enters through
+// TwoProd and TwoSum, the error terms of the running sum gathered in lo and
+// folded in once, when the colour vector is read (12 FP32 operations per real
+// multiply-add instead of a normalised pair product and sum).
+struct SiteAccFF {
+    float hi[6], lo[6];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) hi[k] = lo[k] = 0.0f;
+    }
+    // acc_k += a b
+    __device__ __forceinline__ void fma(int k, ff a, ff b)
+    {
+        const float p = __fmul_rn(a.hi, b.hi);
+        const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p)));
+        const float s = __fadd_rn(hi[k], p);
+        const float bb = __fsub_rn(s, hi[k]);
+        const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi[k] = s;
+        lo[k] = __fadd_rn(lo[k], __fadd_rn(e, t));
+    }
+    __device__ __forceinline__ void add(const ff U[18], const ff s[6])
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const ff ur = U[2 * (3 * i + j)], ui = U[2 * (3 * i + j) + 1];
+                fma(2 * i, ur, s[2 * j]);
+                fma(2 * i, -ui, s[2 * j + 1]);
+                fma(2 * i + 1, ur, s[2 * j + 1]);
+                fma(2 * i + 1, ui, s[2 * j]);
+            }
+    }
+    __device__ __forceinline__ void adj_sub(const ff U[18], const ff s[6])
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const ff ur = U[2 * (3 * j + i)], ui = U[2 * (3 * j + i) + 1];  // conj(U_ji)
+                fma(2 * i, -ur, s[2 * j]);
+                fma(2 * i, -ui, s[2 * j + 1]);
+                fma(2 * i + 1, -ur, s[2 * j + 1]);
+                fma(2 * i + 1, ui, s[2 * j]);
+            }
+    }
+    __device__ __forceinline__ ff get(int k) const { return ff_fast_two_sum(hi[k], lo[k]); }
+};
+
 template <typename real>
-using SiteAcc = std::conditional_t<std::is_same<real, float>::value, SiteAccPacked, SiteAccScalar<real>>;
+using SiteAcc = std::conditional_t<std::is_same<real, float>::value, SiteAccPacked,
+                                   std::conditional_t<is_ff<real>::value, SiteAccFF, SiteAccScalar<real>>>;
 
 // Launch shapes tried by the tuner: threads per block, the minimum number of
 // resident blocks per SM asked of the register allocator (loads in flight per
@@ -271,11 +323,6 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
 
 // One thread per site.  A reducing pass ends each block with its block sum
 // and a partial store; stencil_finish_kernel, launched after it, sums them.
-// Type of the per-block sums: FP32 pairs are summed as FP64 (one conversion
-// per thread; shuffles and partials take plain scalars).
-template <typename real>
-using red_t = std::conditional_t<is_ff<real>::value, double, real>;
-
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)

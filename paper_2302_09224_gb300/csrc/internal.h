@@ -242,6 +242,7 @@ int stencil_config_in_use(int gf, int sf, int cf, int long_recon, bool reduce, c
 
 void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *err, cudaStream_t s);
 void launch_pack32_spinor(int sf, int64_t n, const float *in, char *out, int *err, cudaStream_t s);
+void launch_pack_pair_int30(int64_t n, const float *in, char *out, int *err, cudaStream_t s);
 void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out, cudaStream_t s);
 
 // gauge preparation

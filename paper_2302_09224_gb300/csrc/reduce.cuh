@@ -10,9 +10,17 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "ff.cuh"
 #include "internal.h"
 
 namespace hisq {
+
+// Type of the per-block sums: FP32 pairs are summed as FP64 (one conversion
+// per thread; shuffles and partials take plain scalars).
+template <typename real>
+using red_t = std::conditional_t<is_ff<real>::value, double, real>;
 
 template <int NR, typename T>
 __device__ __forceinline__ void warp_sum(T v[NR])

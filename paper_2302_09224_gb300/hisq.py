@@ -122,6 +122,7 @@ _SIGS = {
     "hisq_spinor_bytes": (_SZ, [_I, _I64]),
     "hisq_spinor_pack": (_I, [_P, _I, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
     "hisq_spinor_pack32": (_I, [_P, _I, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
+    "hisq_spinor_pack_pair_int30": (_I, [_P, _I64, _P, _P, ctypes.POINTER(_I64), _P]),
     "hisq_spinor_unpack": (_I, [_P, _I, _I, _I64, _P, _P, _P]),
     "hisq_profile_enable": (None, [_P, _I]),
     "hisq_profile_reset": (None, [_P]),
@@ -277,6 +278,13 @@ def hisq_spinor_pack32(ctx, sfmt: int, n: int, x, packed, stream=None) -> int:
     bad = _I64(0)
     _check(ctx, lib().hisq_spinor_pack32(ctx, int(sfmt), int(n), _ptr(x), _ptr(packed), ctypes.byref(bad),
                                          _stream(stream)))
+    return int(bad.value)
+
+
+def hisq_spinor_pack_pair_int30(ctx, n: int, x, packed, stream=None) -> int:
+    bad = _I64(0)
+    _check(ctx, lib().hisq_spinor_pack_pair_int30(ctx, int(n), _ptr(x), _ptr(packed), ctypes.byref(bad),
+                                                  _stream(stream)))
     return int(bad.value)
 
 

@@ -103,6 +103,42 @@ def test_fp32_store_path_bit_exact(ctx, orc, n):
         assert bad == obad
 
 
+@pytest.mark.parametrize("n", [16, 4096 + 13])
+def test_pair_store_path_bit_exact(ctx, orc, n):
+    """The 30-bit store from FP32 pairs (what the FP64-class kernels write,
+    without FP64 arithmetic) against the oracle's FP64 codec on the values
+    hi + lo: exponents from power-of-two hi with tails of either sign, and
+    exact ties after scaling, bit for bit."""
+    g = np.random.Generator(np.random.Philox(key=400 + n))
+    hi = (g.standard_normal((n, 6)) * np.exp(g.uniform(-30, 30, size=(n, 1)))).astype(np.float32)
+    hi[::3, 0] = np.float32(2.0) ** g.integers(-60, 60, size=hi[::3, 0].shape).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float64)
+    lo = (g.uniform(-0.5, 0.5, size=(n, 6)) * ulp * 10.0 ** -g.integers(0, 8, size=(n, 6))).astype(np.float32)
+    lo[::5] = (np.sign(g.standard_normal((len(lo[::5]), 6))) * ulp[::5] / 2).astype(np.float32)  # ties
+    hi[2] = 0.0
+    lo[2] = 0.0
+    # power-of-two site maxima with opposite-sign tails above and below 2^(p-29)
+    hi[1] = [1.0, 0.25, 0, 0, 0, 0]
+    lo[1] = [-2.0 ** -25, 0, 0, 0, 0, 0]
+    hi[3] = [0, -2.0, 0, 0, 0.5, 0]
+    lo[3] = [0, 2.0 ** -40, 0, 0, 0, 0]
+    lo = np.where(np.abs(lo.astype(np.float64)) <= ulp / 2, lo, np.float32(0))
+    # keep only tails whose sum with hi is exact in FP64 (the reference below)
+    exact = (hi.astype(np.float64) + lo.astype(np.float64)) - hi.astype(np.float64) == lo.astype(np.float64)
+    lo = np.where(exact, lo, np.float32(0))
+    pairs = np.stack([hi, lo], axis=-1)
+    x = torch.from_numpy(np.ascontiguousarray(pairs)).cuda()
+    buf = torch.zeros(hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_INT30, n), dtype=torch.uint8, device="cuda")
+    bad = hisq.hisq_spinor_pack_pair_int30(ctx, n, x, buf)
+    d = hi.astype(np.float64) + lo.astype(np.float64)  # exact (filtered above)
+    w, obad = orc.int30_pack(d)
+    got = buf.cpu().numpy()
+    a = got[:16 * n].view(np.uint32).reshape(n, 4)
+    b = got[16 * n:].view(np.uint32).reshape(n, 2)
+    np.testing.assert_array_equal(np.concatenate([a, b], axis=1), w)
+    assert bad == obad == 0
+
+
 def test_f32_f64_layouts(ctx):
     n = 1000
     v = sites(n, 7)[20:]
