@@ -637,10 +637,27 @@ def run_serve(args):
         statuses[hisq.STATUS_NAMES[st]] = statuses.get(hisq.STATUS_NAMES[st], 0) + 1
     wall = time.perf_counter() - t0
     s = hisq.hisq_serve_stats(ctx)
-    print(json.dumps({"workload": f"serving: {args.requests} Poisson requests at 200/s (seed 1), volumes "
-                      "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts)",
-                      "completed": s.completed, "statuses": statuses, "latency_p50_s": s.latency_p50_s,
-                      "latency_p99_s": s.latency_p99_s, "solves_per_s": s.solves_per_s, "wall_s": wall}))
+    line = {"workload": f"serving: {args.requests} Poisson requests at 200/s (seed 1), volumes "
+                        "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts)",
+            "completed": s.completed, "statuses": statuses, "latency_p50_s": s.latency_p50_s,
+            "latency_p99_s": s.latency_p99_s, "solves_per_s": s.solves_per_s, "wall_s": wall}
+    if args.serve_sequential:
+        # the same requests solved one after another on one stream, no batching or overlap
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for r in reqs:
+            b = synth.spinor(r["dims"], r["rhs_seed"], device="cuda")
+            p = hisq.hisq_default_params()
+            p.mass, p.tol, p.on_device = r["mass"], r["tol"], 1
+            if r["multishift"]:
+                xs = [torch.zeros_like(b) for _ in r["shifts"]]
+                hisq.hisq_multishift_cg(ctx, gauges[r["dims"]], p, r["shifts"], [r["tol"]] * len(r["shifts"]), b, xs)
+            else:
+                hisq.hisq_cg(ctx, gauges[r["dims"]], p, b, torch.zeros_like(b))
+        torch.cuda.synchronize()
+        seq = time.perf_counter() - t1
+        line.update({"sequential_s": seq, "throughput_vs_sequential": seq / wall})
+    print(json.dumps(line))
     for g in gauges.values():
         hisq.hisq_free_gauge(ctx, g)
     hisq.hisq_destroy(ctx)
@@ -674,6 +691,8 @@ def main():
     ap.add_argument("--ms-pairs", default="f32/half,int30/int20,int20/int20",
                     help="multi-shift stage / refinement formats for --workload multishift")
     ap.add_argument("--requests", type=int, default=100, help="requests of --workload serve")
+    ap.add_argument("--serve-sequential", action="store_true",
+                    help="--workload serve: also solve the requests one after another for comparison")
     ap.add_argument("--maxiter", type=int, default=20)
     args = ap.parse_args()
     if args.stencil:

@@ -212,8 +212,9 @@ TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Ga
 // loaded with a system (its right-hand side is copied in), iterated block by
 // block together with the other occupied slots, and harvested when it stops;
 // a freed slot can be loaded again at any block boundary (continuous
-// batching).  Empty slots are inactive: the stencil still processes their
-// (zero) fields, every other kernel skips them.
+// batching).  Empty and stopped slots are inactive: the BLAS kernels skip
+// them, the stencil skips tiles in which every slot is inactive (slots are
+// filled lowest first).
 // ---------------------------------------------------------------------------
 BatchSession::BatchSession(hisq_ctx *c_, hisq_gauge *g_, const BCGConfig &cfg_, cudaStream_t s_)
     : c(c_), g(g_), cfg(cfg_), s(s_), ws(c_, s_), vh(g_->geom.vh), nr(cfg_.nrhs), N(cfg_.nbuf)

@@ -33,6 +33,18 @@ __device__ __forceinline__ void load_link_scaled(const char *base, size_t pstrid
     if constexpr (RECON == 12) rebuild_row2(U, sign12);
 }
 
+// Whether any right-hand side of the tile [t0, t0 + T) is still iterating
+// (solver states present); a tile of stopped or empty slots is skipped.
+template <int T>
+__device__ __forceinline__ bool tile_active(const DslashMArgs &a)
+{
+    if (a.st == nullptr) return true;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < T; j++) any = any || *(volatile const int *)&a.st[a.t0 + j].active != 0;
+    return any;
+}
+
 // U <- -U^+ (a backward term's matrix, so that every term is accumulated as
 // acc += U s).
 template <typename real>
@@ -58,6 +70,7 @@ template <int GF, int SF, typename real, int LREC, int T, bool RED>
 __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const DslashMArgs a)
 {
     if (a.active_any != nullptr && *(volatile const int *)a.active_any == 0) return;
+    if (!tile_active<T>(a)) return;  // every system of this tile stopped or empty: uniform over the grid
     const Geom &g = a.g;
     const int vh = g.vh;
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,6 +264,7 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_staged_kernel(const Ds
     static_assert(Spinor<SF>::chunks == 1, "staged tiles take 16-byte spinor records");
     extern __shared__ __align__(16) uint4 stage_smem[];
     if (a.active_any != nullptr && *(volatile const int *)a.active_any == 0) return;
+    if (!tile_active<T>(a)) return;  // every system of this tile stopped or empty: uniform over the grid
     const Geom &g = a.g;
     const int vh = g.vh;
     const int tid = threadIdx.x;
