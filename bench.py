@@ -74,7 +74,7 @@ def profiled_traffic():
     except OSError:
         return None
     m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram bytes per launch \(scaled to 32\^3x64, mean of both passes\):\s*([0-9.eE+]+)", text)
+    m_b = re.search(r"dram bytes per launch \(32\^3x64, mean of both passes\):\s*([0-9.eE+]+)", text)
     if not (m_hash and m_b) or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
