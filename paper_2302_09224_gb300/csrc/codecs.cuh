@@ -481,6 +481,61 @@ struct LinkScaled {
     static constexpr bool value = GF == G_FIX16 || GF == G_FIX32;
 };
 
+// FP32 pairs, three 16-byte planes of (hi, lo, hi, lo): the accumulators of
+// FP64-class (pair) kernels, read and written without conversion.
+template <>
+struct Spinor<S_FF> {
+    static constexpr int chunks = 3;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) c[k] = ld_cached(reinterpret_cast<const uint4 *>(b) + (size_t)k * n + i);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const ff a(__uint_as_float(c[k].x), __uint_as_float(c[k].y));
+            const ff b(__uint_as_float(c[k].z), __uint_as_float(c[k].w));
+            if constexpr (is_ff<real>::value) {
+                v[2 * k] = a;
+                v[2 * k + 1] = b;
+            } else {
+                v[2 * k] = (real)(double)a;
+                v[2 * k + 1] = (real)(double)b;
+            }
+        }
+    }
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            ff a, bb;
+            if constexpr (is_ff<real>::value) {
+                a = v[2 * k];
+                bb = v[2 * k + 1];
+            } else {
+                a = ff((double)v[2 * k]);
+                bb = ff((double)v[2 * k + 1]);
+            }
+            ok = ok && isfinite(a.hi) && isfinite(bb.hi);
+            reinterpret_cast<uint4 *>(b)[(size_t)k * n + i] =
+                make_uint4(__float_as_uint(a.hi), __float_as_uint(a.lo), __float_as_uint(bb.hi), __float_as_uint(bb.lo));
+        }
+        return ok;
+    }
+};
+
 // A spinor record read through L2 only (ld.global.cg): for fields that other
 // blocks of the same kernel write (the read-only path may not be used there).
 // Same planar layout as Spinor<SF>::gather.

@@ -53,7 +53,7 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) shift_update_kernel(MSArgs a)
 {
     if (a.active && *(volatile const int *)a.active == 0) return;
-    constexpr int AF = sizeof(real) == 8 ? S_F64 : S_F32;
+    constexpr int AF = is_ff<real>::value ? S_FF : sizeof(real) == 8 ? S_F64 : S_F32;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const MSState *m = a.m;
     if (i < a.n) {
@@ -213,6 +213,8 @@ struct MSRun {
         LaunchScope ls(c, s, PROF_BLAS, (double)ns * (96.0 + 2.0 * spinor_site_bytes(acc_fmt)) * vh);
         if (acc_fmt == S_F64)
             acc_flush_kernel<S_F64><<<nblk(vh), kBlock, 0, s>>>(a);
+        else if (acc_fmt == S_FF)
+            acc_flush_kernel<S_FF><<<nblk(vh), kBlock, 0, s>>>(a);
         else
             acc_flush_kernel<S_F32><<<nblk(vh), kBlock, 0, s>>>(a);
     }
@@ -275,7 +277,8 @@ struct MSRun {
             case S_HALF: shift_update_kernel<S_HALF, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
             case S_INT20: shift_update_kernel<S_INT20, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
             case S_INT30:
-                if (f64) shift_update_kernel<S_INT30, double><<<nblk(vh), kBlock, 0, s>>>(a);
+                if (f64)  // FP64-class compute in FP32 pairs, pair accumulators
+                    shift_update_kernel<S_INT30, ff><<<nblk(vh), kBlock, 0, s>>>(a);
                 else shift_update_kernel<S_INT30, float><<<nblk(vh), kBlock, 0, s>>>(a);
                 break;
             }
@@ -292,7 +295,7 @@ struct MSRun {
         if (!e) e = gauge_view_for(c, g, prec_f64(), &gv_d);
         if (e) return e;
         sb = spinor_field_bytes(p.sloppy.spinor, vh);
-        acc_fmt = p.sloppy.compute == HISQ_COMPUTE_F64 ? S_F64 : S_F32;
+        acc_fmt = p.sloppy.compute != HISQ_COMPUTE_F64 ? S_F32 : p.sloppy.spinor == S_INT30 ? S_FF : S_F64;
         accb = spinor_field_bytes(acc_fmt, vh);
         const size_t b48 = (size_t)48 * vh;
         e = ws.alloc(sb, (void **)&r_s);

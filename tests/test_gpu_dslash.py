@@ -213,3 +213,23 @@ def test_every_launch_shape(ctx, orc, cfg, name):
             assert rel(out, exact) <= BOUND_EXACT[name], (cfg, name, dims)
     finally:
         hisq.hisq_stencil_config(prev)
+
+
+def test_launch_shape_controls(ctx):
+    """Forced shapes per pass are reported by the in-use query; invalid values are refused."""
+    dims = (4, 4, 4, 8)
+    fat, lng = lattice(dims, False)
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    p = hisq.prec("int20", 12)
+    prev = hisq.hisq_stencil_config(2)
+    prev_r = hisq.hisq_stencil_config_reduce(3)
+    try:
+        assert hisq.hisq_stencil_config_in_use(g, p, False) == 2
+        assert hisq.hisq_stencil_config_in_use(g, p, True) == 3
+        hisq.hisq_stencil_config_reduce(-1)  # the reducing pass follows the plain one again
+        assert hisq.hisq_stencil_config_in_use(g, p, True) == 2
+        assert hisq.hisq_stencil_config(7) == -2 and hisq.hisq_stencil_config_reduce(-5) == -2
+    finally:
+        hisq.hisq_stencil_config(prev)
+        hisq.hisq_stencil_config_reduce(prev_r)
+        hisq.hisq_free_gauge(ctx, g)
