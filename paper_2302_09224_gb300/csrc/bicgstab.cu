@@ -149,9 +149,8 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, const char *y)
 {
     if (skip(a.active)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     real v[3] = {0, 0, 0};
-    if (s < a.vh) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
         real xv[6], yv[6];
         Spinor<SF>::load(half(x, a.hb), a.vh, s, xv);
         Spinor<SF>::load(half(y, a.hb), a.vh, s, yv);
@@ -163,9 +162,9 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, con
             d1 += xr * yi - xi * yr;
             d2 += yr * yr + yi * yi;
         }
-        v[0] = d0;
-        v[1] = d1;
-        v[2] = d2;
+        v[0] += d0;
+        v[1] += d1;
+        v[2] += d2;
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -176,9 +175,8 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) u_multi_kernel(BArgs a)
 {
     if (skip(a.active)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.vh) return;
     const real br = (real)a.b->beta_re, bi = (real)a.b->beta_im;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x)
     for (int i = 0; i <= a.j; i++) {
         real r[6], u[6];
         Spinor<SF>::load(half(a.R + i * a.fb, a.hb), a.vh, s, r);
@@ -199,9 +197,8 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
 {
     if (skip(a.active)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.vh) return;
     const real ar = (real)a.b->alpha_re, ai = (real)a.b->alpha_im;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
     for (int i = 0; i <= a.j; i++) {
         real u[6], r[6];
         Spinor<SF>::load(half(a.U + (i + 1) * a.fb, a.hb), a.vh, s, u);
@@ -227,6 +224,7 @@ __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
         x[2 * c + 1] += (double)(ar * u0[2 * c + 1] + ai * u0[2 * c]);
     }
     Spinor<S_F64>::store(xf, a.vh, s, x);
+    }
 }
 
 // Modified Gram-Schmidt step (j, i): r_j -= tau_{i-1,j} r_{i-1} (i >= 2), then
@@ -235,9 +233,8 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
 {
     if (skip(a.active)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     real v[3] = {0, 0, 0};
-    if (s < a.vh) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
         real rj[6], ri[6];
         char *rjf = half(a.R + a.j * a.fb, a.hb);
         Spinor<SF>::load(rjf, a.vh, s, rj);
@@ -268,9 +265,9 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
             }
             d2 += jr * jr + ji * ji;
         }
-        v[0] = d0;
-        v[1] = d1;
-        v[2] = d2;
+        v[0] += d0;
+        v[1] += d1;
+        v[2] += d2;
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -312,11 +309,10 @@ template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
 {
     if (skip(a.active)) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const BState *b = a.b;
     const int l = b->l;
     real v[1] = {0};
-    if (s < a.vh) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
         // updates in the compute precision; x's increment is added in FP64
         real dx[6] = {0, 0, 0, 0, 0, 0}, r0[6], u0[6], t[6];
         char *xf = reinterpret_cast<char *>(a.x64) + blockIdx.y * (size_t)48 * a.vh;
@@ -350,7 +346,7 @@ __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
         if (!Spinor<SF>::store(u0f, a.vh, s, u0)) atomicExch(a.err, 1);
         real n2 = 0;
         for (int k = 0; k < 6; k++) n2 += r0[k] * r0[k];
-        v[0] = n2;
+        v[0] += n2;
     }
     __shared__ double tot[1];
     if (reduce_grid<1>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -366,7 +362,20 @@ __global__ void restart_kernel(BState *b, const double *sum)
     if (!b->active) b->reason = REASON_BREAKDOWN;
 }
 
-dim3 grid2(int vh) { return dim3((vh + kBlock - 1) / kBlock, 2); }
+// Two rows (parities) of blocks that loop over their parity's sites: at most
+// 4 blocks per SM per row (one wave at the kernels' occupancy), so that the
+// end of a reducing block is paid once per resident block.
+dim3 grid2(int vh)
+{
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
+    const int need = (vh + kBlock - 1) / kBlock;
+    return dim3(need < 4 * sms ? need : 4 * sms, 2);
+}
 
 #define B_DISPATCH(SF_, CF_, KERNEL, GRID, ...)                                              \
     do {                                                                                    \
