@@ -173,7 +173,7 @@ void Server::run_batch(const std::shared_ptr<Req> &first, cudaStream_t s)
     hisq_status e = bs.setup();
     // staging for one system: caller layout and the planar FP64 field
     Workspace stage(c, s);
-    double *aos = nullptr, *planar = nullptr, *host = nullptr;
+    double *aos = nullptr, *planar = nullptr;
     if (!e) e = stage.alloc((size_t)48 * vh, (void **)&aos);
     if (!e) e = stage.alloc((size_t)48 * vh, (void **)&planar);
     if (e) {
@@ -193,7 +193,6 @@ void Server::run_batch(const std::shared_ptr<Req> &first, cudaStream_t s)
         give_back(e);  // cannot fit even with nothing else running
         return;
     }
-    (void)host;
     auto load_one = [&](int t, const std::shared_ptr<Req> &q) -> hisq_status {
         const double *src = q->r.b;
         if (!q->r.on_device) {
