@@ -56,7 +56,7 @@ def measured_peak():
 def kernel_source_hash():
     """Hash of the stencil's code (comments and blank lines ignored)."""
     h = hashlib.sha256()
-    for name in ("dslash.cuh", "codecs.cuh", "reduce.cuh", "finish.cuh"):
+    for name in ("dslash.cuh", "codecs.cuh", "reduce.cuh", "finish.cuh", "ff.cuh"):
         with open(os.path.join(ROOT, "paper_2302_09224_gb300", "csrc", name)) as f:
             for line in f:
                 code = line.split("//", 1)[0].strip()
