@@ -501,6 +501,53 @@ def run_solve_only(args):
     return 0
 
 
+def run_batched_solve(args):
+    """Short batched CG solves on one lattice for every (tile, kernel) pair: the batched stencil's time per
+    launch and its algorithmic bandwidth (profiler events on the solver's stream), the small case for ncu
+    captures of the batched kernels, and the sweep behind the tile tuner."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims = tuple(int(v) for v in args.batched_solve.split(","))
+    nr = args.nrhs
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    del fat, lng
+    b = torch.stack([synth.spinor(dims, synth.rhs_seed(k), device="cuda") for k in range(nr)]).contiguous()
+    tiles = [int(v) for v in args.rhs_tiles.split(",")]
+    kernels = [int(v) for v in args.rhs_kernels.split(",")]
+    out = []
+    for T in tiles:
+        for kern in kernels:
+            p = hisq.hisq_default_params()
+            p.mass, p.tol, p.delta, p.on_device = MASS, TOL, DELTA, 1
+            p.sloppy = hisq.prec(args.prec, 12)
+            p.maxiter = args.maxiter
+            p.nrhs, p.rhs_tile, p.rhs_kernel = nr, T, kern
+            x = torch.zeros_like(b)
+            hisq.hisq_cg(ctx, g, p, b, x)  # tuning and warm-up
+            x.zero_()
+            hisq.hisq_profile_reset(ctx)
+            hisq.hisq_profile_enable(ctx, True)
+            st, info = hisq.hisq_cg(ctx, g, p, b, x)
+            torch.cuda.synchronize()
+            sten = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+            blas = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_BLAS)
+            hisq.hisq_profile_enable(ctx, False)
+            passes = max(sten.launches, 1)
+            out.append({"tile": T, "kernel": ["tuned", "registers", "staged"][kern], "status": hisq.STATUS_NAMES.get(st, st),
+                        "iters": info.iters, "stencil_ms_per_pass": sten.ms / passes,
+                        "stencil_us_per_rhs_pass": 1e3 * sten.ms / passes / nr,
+                        "stencil_gbs": sten.bytes / max(sten.ms, 1e-9) / 1e6,
+                        "blas_us_per_rhs_iter": 1e3 * blas.ms / max(info.iters, 1) / nr})
+            print(json.dumps(out[-1]), flush=True)
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
 def run_multishift(args):
     """12 shifts log-spaced in [1e-4, 1] on 32^3x64, base m = 0.005, per-shift targets 1e-10..1e-7: the
     multi-shift stage (all shifts in one fused update kernel per iteration) plus refinement, per format."""
@@ -694,11 +741,18 @@ def main():
     ap.add_argument("--serve-sequential", action="store_true",
                     help="--workload serve: also solve the requests one after another for comparison")
     ap.add_argument("--maxiter", type=int, default=20)
+    ap.add_argument("--batched-solve", default=None,
+                    help="LX,LY,LZ,LT: short batched CG solves per (tile, kernel), batched stencil timing (profiling)")
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--rhs-tiles", default="1,2,4,8,16")
+    ap.add_argument("--rhs-kernels", default="1,2", help="1 registers, 2 staged neighbour loads, 0 tuned")
     args = ap.parse_args()
     if args.stencil:
         return run_stencil_only(args)
     if args.solve:
         return run_solve_only(args)
+    if args.batched_solve:
+        return run_batched_solve(args)
     if args.workload == "multishift":
         return run_multishift(args)
     if args.workload == "batched":
