@@ -243,19 +243,19 @@ __device__ __forceinline__ void stage_link(uint4 *slot0, int stride, const char 
         cp_async_8(slot0 + LK::n16 * stride, base + LK::n16 * pstride + (size_t)li * 8);
 }
 
-// Term q = 4 mu + 2 hop + dir of a site: neighbour (checkerboard) index and
-// link index.
+// Term k = 2 hop + dir of direction mu at a site: neighbour (checkerboard)
+// index, link index and the neighbour's mu coordinate.
 struct TermIdx {
     int nb, li, cn;
 };
 
-__device__ __forceinline__ TermIdx term_index(const Geom &g, int mu, int hop, int dir, int cmu, int lex, int cb, int po)
+__device__ __forceinline__ TermIdx term_index(const Geom &g, int mu, int hop, int dir, int cmu, int base, int cb, int po)
 {
     TermIdx r;
     const int k = hop ? 3 : 1;
-    const int L = g.L[mu], st = g.stride[mu];
-    r.cn = wrap_coord(dir ? cmu - k : cmu + k, L);
-    r.nb = ((lex - cmu * st) + r.cn * st) >> 1;
+    const int st = g.stride[mu];
+    r.cn = wrap_coord(dir ? cmu - k : cmu + k, g.L[mu]);
+    r.nb = (base + r.cn * st) >> 1;
     r.li = ((dir ? 1 - po : po) * 4 + mu) * g.vh + (dir ? r.nb : cb);
     return r;
 }
@@ -267,8 +267,13 @@ __device__ __forceinline__ TermIdx term_index(const Geom &g, int mu, int hop, in
 // backward, one hop and three) are unrolled, so every term's link format and
 // product are fixed at compile time.
 // ---------------------------------------------------------------------------
+// Resident blocks per SM asked of the register allocator: five for tiles of up
+// to four (at most 96 registers: twenty warps keep the loads of neighbour
+// records in flight), no cap for larger tiles (their accumulators need more).
+__host__ __device__ constexpr int mrhs_min_blocks(int T) { return T <= 4 ? 5 : 1; }
+
 template <int GF, int SF, int LREC, int T, bool RED, bool STAGED>
-__global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const __grid_constant__ DslashMArgs a)
+__global__ void __launch_bounds__(kMrhsBlock, mrhs_min_blocks(T)) dslash_mrhs_kernel(const __grid_constant__ DslashMArgs a)
 {
     constexpr int NL = T >= 2 ? 2 : 1, NG = T / NL;  // lanes per group, groups
     using V = lanes_t<NL>;
@@ -323,29 +328,36 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const __grid_co
                                 a.in + (size_t)(a.t0 + j) * a.field_bytes + (size_t)ti.nb * 16);
             }
         };
+        // staged: each term's indices are computed once, when its copies are
+        // issued (one term ahead), and carried to the term itself
+        TermIdx cur = term_index(g, 0, 0, 0, x, lex - x, cb, po);
         if constexpr (STAGED) {
-            issue(term_index(g, 0, 0, 0, x, lex, cb, po), 0, 0);
+            issue(cur, 0, 0);
             cp_async_commit();
         }
 
 #pragma unroll 1
         for (int mu = 0; mu < 4; mu++) {
             const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+            const int base = lex - cmu * g.stride[mu];  // the site with coordinate mu set to 0
             const float eta = ((eta_bits >> mu) & 1) ? -1.0f : 1.0f;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const int hop = k >> 1, dir = k & 1;
-                const TermIdx cur = term_index(g, mu, hop, dir, cmu, lex, cb, po);
                 constexpr int LC = Link<GF, 18>::chunks > Link<GF, LREC>::chunks ? Link<GF, 18>::chunks
                                                                                   : Link<GF, LREC>::chunks;
                 uint4 lc[LC];
                 uint4 sc[T * SC];
+                TermIdx nxt = cur;
                 if constexpr (STAGED) {
                     const int q = 4 * mu + k;
-                    if (q + 1 < 16) {
-                        const int mn = k == 3 ? mu + 1 : mu, kn = k == 3 ? 0 : k + 1;
-                        const int cn = mn == mu ? cmu : mn == 1 ? y : mn == 2 ? z : t;
-                        issue(term_index(g, mn, kn >> 1, kn & 1, cn, lex, cb, po), kn >> 1, (q + 1) & 1);
+                    if (k < 3) {
+                        nxt = term_index(g, mu, (k + 1) >> 1, (k + 1) & 1, cmu, base, cb, po);
+                        issue(nxt, (k + 1) >> 1, (q + 1) & 1);
+                    } else if (mu < 3) {
+                        const int m1 = mu + 1, c1 = m1 == 1 ? y : m1 == 2 ? z : t;
+                        nxt = term_index(g, m1, 0, 0, c1, lex - c1 * g.stride[m1], cb, po);
+                        issue(nxt, 0, (q + 1) & 1);
                     } else if (a.xpay) {
                         // the xpay records of every right-hand side, in flight during the last term
 #pragma unroll
@@ -360,6 +372,7 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const __grid_co
 #pragma unroll
                     for (int j = 0; j < T; j++) sc[j] = *slot(stage, kLinkSlots + j);
                 } else {
+                    cur = term_index(g, mu, hop, dir, cmu, base, cb, po);
                     if (hop == 0)
                         Link<GF, 18>::gather(a.gv.fat, pstride, cur.li, lc);
                     else
@@ -403,6 +416,7 @@ __global__ void __launch_bounds__(kMrhsBlock) dslash_mrhs_kernel(const __grid_co
                         term_mv<false, V>(re[gi], im[gi], ur, ui, oa, ob, oc);
                     }
                 }
+                if constexpr (STAGED) cur = nxt;
             }
         }
 
