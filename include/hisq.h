@@ -247,6 +247,13 @@ HISQ_API hisq_status hisq_profile_read(hisq_ctx *ctx, int kind, hisq_kernel_stat
  * event pair costs some device time, so a caller timing a solve may select
  * only the class it needs.  Unselected classes are not counted. */
 HISQ_API void hisq_profile_select(hisq_ctx *ctx, unsigned mask);
+/* Sample period of the CG solver's graphs: with every > 1 the solver keeps a
+ * second graph without event pairs and times only one block of iterations in
+ * `every` (the first of each solve included), so that the event nodes (each
+ * costs device time) perturb a timed solve less; the per-class averages then
+ * come from the sampled blocks.  Other solvers time every launch.  every = 1
+ * (default) times every block.  EINVAL when every < 1. */
+HISQ_API hisq_status hisq_profile_sample(hisq_ctx *ctx, int every);
 
 /* Launch shape of the stencil kernels: -1 (default) lets the library time the
  * shapes the first time a (precision, lattice) pair is used and keep the

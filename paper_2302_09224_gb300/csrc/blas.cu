@@ -29,7 +29,9 @@ __device__ __forceinline__ bool skip(const int *active)
 
 // Sites per thread of the two per-iteration BLAS kernels: every load of a
 // thread's sites is issued before any of them is used (memory-level
-// parallelism for these short, latency-bound kernels).
+// parallelism for these short, latency-bound kernels).  Four sites a thread
+// (one pass over 2^20 sites) and a grid over all sites instead of one wave
+// measured the same within 2 % in the 32^3x64 solve.
 constexpr int kRSites = 2;
 constexpr int kPSites = 2;
 
@@ -118,19 +120,32 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
     if (skip(a.active)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    constexpr int G = 4, C = Spinor<SF>::chunks;  // slots whose loads are in flight together
+    uint4 cx[Spinor<S_F64>::chunks];
+    Spinor<S_F64>::gather(reinterpret_cast<const char *>(a.x64), a.n, i, cx);
     // the increment sum_j alpha_j p_j carries the sloppy vectors' precision,
     // so it is formed in the compute precision and added to x in FP64
     real dx[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = 0; j < a.nslots; j++) {
-        const real al = (real)a.st->alpha_ring[j];
-        if (al == real(0)) continue;
-        real p[6];
-        Spinor<SF>::load(a.v0 + (size_t)j * a.slot_bytes, a.n, i, p);
+    for (int j0 = 0; j0 < a.nslots; j0 += G) {
+        uint4 cp[G][C];
+        real al[G];
 #pragma unroll
-        for (int k = 0; k < 6; k++) dx[k] += al * p[k];
+        for (int g = 0; g < G; g++) {
+            const int j = j0 + g;
+            al[g] = j < a.nslots ? (real)a.st->alpha_ring[j] : real(0);
+            if (al[g] != real(0)) Spinor<SF>::gather(a.v0 + (size_t)j * a.slot_bytes, a.n, i, cp[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            if (al[g] == real(0)) continue;
+            real p[6];
+            Spinor<SF>::decode(cp[g], p);
+#pragma unroll
+            for (int k = 0; k < 6; k++) dx[k] += al[g] * p[k];
+        }
     }
     double x[6];
-    Spinor<S_F64>::load(reinterpret_cast<const char *>(a.x64), a.n, i, x);
+    Spinor<S_F64>::decode(cx, x);
 #pragma unroll
     for (int k = 0; k < 6; k++) x[k] += (double)dx[k];
     Spinor<S_F64>::store(reinterpret_cast<char *>(a.x64), a.n, i, x);

@@ -304,50 +304,63 @@ struct CGRun {
         if (e) return e;
         hisq_status status = HISQ_OK;
         bool done = st_h->hi_rr <= init.stop2;
-        // with the profiler on, the graph carries an event pair around each launch
+        // with the profiler on, the graph carries an event pair around each
+        // launch; with a sample period above one, a second instance without
+        // them runs the other blocks (event nodes cost device time)
         const bool graph = cfg.use_graph;
-        cudaGraphExec_t exec = nullptr;
+        const int every = c->prof.on ? c->prof.every : 1;
+        cudaGraphExec_t exec = nullptr, exec_plain = nullptr;
         int64_t nodes = 0;
+        int64_t block = 0;
         std::vector<Profiler::Rec> grecs;
+        auto capture = [&](bool record, cudaGraphExec_t *out) -> cudaError_t {
+            cudaGraph_t gr = nullptr;
+            set_thread_capturing(true);
+            if (record) set_graph_recorder(&grecs);
+            cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                iterate_block(x64);
+                ce = cudaStreamEndCapture(s, &gr);
+            }
+            set_graph_recorder(nullptr);
+            set_thread_capturing(false);
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(out, gr, 0);
+            size_t nn = 0;
+            if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
+            if (gr) cudaGraphDestroy(gr);
+            nodes = (int64_t)nn;
+            return ce;
+        };
         while (!done) {
             if (st_h->k >= cfg.maxiter) {
                 status = HISQ_ENOTCONV;
                 break;
             }
             const int k0 = st_h->k;
+            const bool timed = !graph || block % every == 0;
             if (graph) {
-                if (!exec) {
-                    cudaGraph_t gr = nullptr;
-                    set_thread_capturing(true);
-                    if (c->prof.on) set_graph_recorder(&grecs);
-                    cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-                    if (ce == cudaSuccess) {
-                        iterate_block(x64);
-                        ce = cudaStreamEndCapture(s, &gr);
-                    }
-                    set_graph_recorder(nullptr);
-                    set_thread_capturing(false);
-                    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
-                    size_t nn = 0;
-                    if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
-                    if (gr) cudaGraphDestroy(gr);
+                cudaGraphExec_t *ex = (timed || !c->prof.on) ? &exec : &exec_plain;
+                if (!*ex) {
+                    const cudaError_t ce = capture(c->prof.on && ex == &exec, ex);
                     if (ce != cudaSuccess) {
+                        if (exec) cudaGraphExecDestroy(exec);
+                        if (exec_plain) cudaGraphExecDestroy(exec_plain);
                         prof_graph_release(c, grecs);
                         return cuda_fail(c, ce, "CG graph capture");
                     }
-                    nodes = (int64_t)nn;
                 }
-                cudaGraphLaunch(exec, s);
+                cudaGraphLaunch(*ex, s);
                 c->launches += nodes;
             } else {
                 iterate_block(x64);
             }
+            block++;
             e = pull_state();
             if (e) break;
-            if (graph)
-                prof_graph_account(c, grecs, st_h->k - k0);
-            else
+            if (!graph)
                 prof_settle(c, st_h->k - k0);
+            else if (timed)
+                prof_graph_account(c, grecs, st_h->k - k0);
             const int reason = st_h->reason;
             if (reason == REASON_BREAKDOWN) {
                 status = HISQ_EBREAKDOWN;
@@ -365,6 +378,7 @@ struct CGRun {
             }
         }
         if (exec) cudaGraphExecDestroy(exec);
+        if (exec_plain) cudaGraphExecDestroy(exec_plain);
         prof_graph_release(c, grecs);
         if (e) return e;
         if (status != HISQ_OK) {

@@ -676,6 +676,15 @@ void hisq_profile_select(hisq_ctx *c, unsigned mask)
     c->prof.mask = mask;
 }
 
+hisq_status hisq_profile_sample(hisq_ctx *c, int every)
+{
+    if (!c) return HISQ_EINVAL;
+    if (every < 1) return fail(c, HISQ_EINVAL, "profile sample period must be >= 1 (got %d)", every);
+    std::lock_guard<std::mutex> lk(c->prof_mu);
+    c->prof.every = every;
+    return HISQ_OK;
+}
+
 void hisq_profile_reset(hisq_ctx *c)
 {
     if (!c) return;

@@ -288,6 +288,7 @@ enum ProfKind { PROF_STENCIL = 0, PROF_STENCIL_HI = 1, PROF_BLAS = 2, PROF_CONVE
 struct Profiler {
     bool on = false;
     unsigned mask = ~0u;  // classes that get event pairs
+    int every = 1;        // a graph-launched solver times one block of iterations in `every`
     struct Rec {
         cudaEvent_t a, b;
         int kind;

@@ -127,6 +127,7 @@ _SIGS = {
     "hisq_profile_enable": (None, [_P, _I]),
     "hisq_profile_reset": (None, [_P]),
     "hisq_profile_select": (None, [_P, ctypes.c_uint]),
+    "hisq_profile_sample": (_I, [_P, _I]),
     "hisq_profile_read": (_I, [_P, _I, ctypes.POINTER(hisq_kernel_stats)]),
     "hisq_launch_count": (_I64, [_P]),
     "hisq_stencil_config": (_I, [_I]),
@@ -303,6 +304,10 @@ def hisq_profile_reset(ctx):
 
 def hisq_profile_select(ctx, mask: int):
     lib().hisq_profile_select(ctx, int(mask) & 0xFFFFFFFF)
+
+
+def hisq_profile_sample(ctx, every: int):
+    _check(ctx, lib().hisq_profile_sample(ctx, int(every)))
 
 
 def hisq_profile_read(ctx, kind: int) -> hisq_kernel_stats:

@@ -110,6 +110,38 @@ def test_graph_matches_direct_and_is_deterministic(ctx):
     assert i1.iters == i2.iters == i3.iters
 
 
+def test_profiler_sampling(ctx):
+    """With a sample period of 4 the CG graphs time one block of iterations in
+    four: the solution is bitwise the unprofiled one, the timed stencil
+    launches are about a quarter of those timed with period 1, and every
+    timed launch is accounted with its algorithmic bytes; period 0 is EINVAL."""
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = synth.gauge_pair(dims, seed=1)
+    b = synth.spinor(dims, 1001).numpy()
+    _, i0, x0 = solve(ctx, dims, fat, lng, m, b, "int20", use_graph=1)
+    counts = {}
+    try:
+        for every in (1, 4):
+            hisq.hisq_profile_sample(ctx, every)
+            hisq.hisq_profile_reset(ctx)
+            hisq.hisq_profile_enable(ctx, True)
+            _, i1, x1 = solve(ctx, dims, fat, lng, m, b, "int20", use_graph=1)
+            st = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+            hisq.hisq_profile_enable(ctx, False)
+            np.testing.assert_array_equal(x1, x0)
+            assert i1.iters == i0.iters
+            assert st.launches > 0 and st.ms > 0
+            assert abs(st.bytes / st.launches - counts.get("per", st.bytes / st.launches)) < 1e-6 * st.bytes / st.launches
+            counts["per"] = st.bytes / st.launches
+            counts[every] = st.launches
+    finally:
+        hisq.hisq_profile_sample(ctx, 1)
+    assert counts[4] < counts[1]
+    assert counts[4] >= counts[1] // 4 - 16  # one block in four (blocks of 8 iterations, 2 passes each)
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_profile_sample(ctx, 0)
+
+
 def test_host_pointers(ctx, orc):
     dims, m = (4, 4, 4, 8), 0.1
     fat, lng = synth.gauge_pair(dims, seed=0)
