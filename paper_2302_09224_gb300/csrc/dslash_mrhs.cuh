@@ -260,6 +260,11 @@ __device__ __forceinline__ TermIdx term_index(const Geom &g, int mu, int hop, in
     return r;
 }
 
+// Resident blocks per SM asked of the register allocator: five for tiles of up
+// to four (at most 96 registers: twenty warps keep the loads of neighbour
+// records in flight), no cap for larger tiles (their accumulators need more).
+__host__ __device__ constexpr int mrhs_min_blocks(int T) { return T <= 4 ? 5 : 1; }
+
 // ---------------------------------------------------------------------------
 // The kernel.  STAGED: neighbour records and links through shared memory
 // (16-byte spinor records); otherwise loaded into registers term by term.
@@ -267,11 +272,6 @@ __device__ __forceinline__ TermIdx term_index(const Geom &g, int mu, int hop, in
 // backward, one hop and three) are unrolled, so every term's link format and
 // product are fixed at compile time.
 // ---------------------------------------------------------------------------
-// Resident blocks per SM asked of the register allocator: five for tiles of up
-// to four (at most 96 registers: twenty warps keep the loads of neighbour
-// records in flight), no cap for larger tiles (their accumulators need more).
-__host__ __device__ constexpr int mrhs_min_blocks(int T) { return T <= 4 ? 5 : 1; }
-
 template <int GF, int SF, int LREC, int T, bool RED, bool STAGED>
 __global__ void __launch_bounds__(kMrhsBlock, mrhs_min_blocks(T)) dslash_mrhs_kernel(const __grid_constant__ DslashMArgs a)
 {
