@@ -476,12 +476,13 @@ __global__ void __launch_bounds__(kMrhsBlock, mrhs_min_blocks(T)) dslash_mrhs_ke
 }
 
 // After a reducing tile launch: one block sums the launch's block partials
-// and runs the finisher of each active right-hand side of the tile (512
-// threads for 32 sums, whose pair accumulators need more than 64 registers).
-__host__ __device__ constexpr int mrhs_finish_threads(int T) { return T >= 16 ? 512 : 1024; }
+// and runs the finisher of each active right-hand side of the tile.  The
+// same thread count for every tile keeps each right-hand side's summation
+// order, and so its iterates, independent of the tile.
+constexpr int kMrhsFinishThreads = 1024;
 
 template <int T>
-__global__ void __launch_bounds__(mrhs_finish_threads(T)) mrhs_finish_kernel(const __grid_constant__ DslashMArgs a, unsigned nblocks)
+__global__ void __launch_bounds__(kMrhsFinishThreads) mrhs_finish_kernel(const __grid_constant__ DslashMArgs a, unsigned nblocks)
 {
     if (a.active_any != nullptr && *(volatile const int *)a.active_any == 0) return;
     if (!tile_active<T>(a)) return;
@@ -506,7 +507,7 @@ bool launch_mrhs_kernel(const DslashMArgs &a, cudaStream_t s)
     }
     const int nb = (a.g.vh + kMrhsBlock - 1) / kMrhsBlock;
     kern<<<nb, kMrhsBlock, smem, s>>>(a);
-    if constexpr (RED) mrhs_finish_kernel<T><<<1, mrhs_finish_threads(T), 0, s>>>(a, (unsigned)nb);
+    if constexpr (RED) mrhs_finish_kernel<T><<<1, kMrhsFinishThreads, 0, s>>>(a, (unsigned)nb);
     return true;
 }
 

@@ -7,6 +7,8 @@ right-hand sides shares each link load (Sec. 1, block solvers).
   the same system solved in a batch of four and in a batch of two (same tile)
   gives bitwise identical solutions, and agrees with the single-RHS solver
   within ten times the tolerance;
+* nor on its tile or the kernel: tiles of 1, 2 and 4 with both kernels (and
+  1, 4 and 16 right-hand sides per tile) give bitwise identical solutions;
 * the batched stencil equals the single-RHS stencil through the oracle check of
   the solutions; bad tile sizes give EINVAL.
 """
@@ -80,6 +82,30 @@ def test_same_alone_and_in_the_mix(ctx):
     _, _, x1 = solve(ctx, dims, m, bs[:1], "int20")  # the single-RHS solver
     d = np.linalg.norm(x4[0] - x1[0]) / np.linalg.norm(x1[0])
     assert d <= 10 * 1e-10 * 1e3   # both meet 1e-10; x differs by at most kappa*tol
+
+
+def test_iterates_independent_of_tile(ctx):
+    """A right-hand side's iterates do not depend on its tile or on the
+    kernel: pairs of right-hand sides on the packed FP32 pipe and a tile of
+    one run the same operations per lane, both kernels share that arithmetic,
+    and every tile's partial sums are reduced in the same order, so the
+    solutions are bitwise identical for every tile size and kernel."""
+    dims, m = (8, 8, 8, 16), 0.02
+    bs = [synth.spinor(dims, synth.rhs_seed(k)).numpy() for k in range(4)]
+    ref = None
+    for tile in (1, 2, 4):
+        for kernel in (1, 2):
+            st, _, x = solve(ctx, dims, m, bs, "int20", tile=tile, rhs_kernel=kernel)
+            assert st == hisq.HISQ_OK
+            if ref is None:
+                ref = x
+            else:
+                np.testing.assert_array_equal(x, ref)
+    dims, m = (4, 4, 8, 8), 0.1
+    bs = [synth.spinor(dims, synth.rhs_seed(k)).numpy() for k in range(16)]
+    sols = [solve(ctx, dims, m, bs, "half", tile=t, rhs_kernel=2)[2] for t in (1, 4, 16)]
+    np.testing.assert_array_equal(sols[1], sols[0])
+    np.testing.assert_array_equal(sols[2], sols[0])
 
 
 def test_sixteen_rhs_and_invalid(ctx, orc):
