@@ -81,6 +81,14 @@ struct Server {
 
     explicit Server(hisq_ctx *c_) : c(c_) {}
 
+    // one reduction lane (partials, result, counters, error flag) per worker,
+    // allocated before the workers start: a worker never shares the
+    // context's own lane with another thread
+    static size_t lane_bytes()
+    {
+        return sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256 + sizeof(unsigned) * kSyncWords;
+    }
+
     void finish(const std::shared_ptr<Req> &q, hisq_status st, const hisq_solve_info &info)
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -110,7 +118,7 @@ struct Server {
         return out;
     }
 
-    void worker(int id);
+    void worker(void *lane_buf);
     void run_batch(const std::shared_ptr<Req> &first, cudaStream_t s);
     void run_single(const std::shared_ptr<Req> &q, cudaStream_t s);
 };
@@ -266,26 +274,20 @@ void Server::run_batch(const std::shared_ptr<Req> &first, cudaStream_t s)
     if (e) give_back(e);
 }
 
-void Server::worker(int id)
+void Server::worker(void *buf)
 {
-    (void)id;
     cudaSetDevice(c->device);
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     // this thread's reduction buffer and error flag
-    void *buf = nullptr;
-    const size_t red_bytes = sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256 +
-                             sizeof(unsigned) * kSyncWords;
+    const size_t red_bytes = lane_bytes();
     Lane lane{};
-    if (ctx_alloc(c, red_bytes, &buf) == HISQ_OK) {
-        cudaMemset(buf, 0, red_bytes);
-        lane.red.partials = (double *)buf;
-        lane.red.result = lane.red.partials + (size_t)kMaxRedBlocks * kMaxRed;
-        lane.red.counter = (unsigned *)(lane.red.result + kMaxRed);
-        lane.err = (int *)(lane.red.counter + 16);
-        lane.red.sync = lane.red.counter + 64;
-        set_thread_lane(&lane);
-    }
+    lane.red.partials = (double *)buf;
+    lane.red.result = lane.red.partials + (size_t)kMaxRedBlocks * kMaxRed;
+    lane.red.counter = (unsigned *)(lane.red.result + kMaxRed);
+    lane.err = (int *)(lane.red.counter + 16);
+    lane.red.sync = lane.red.counter + 64;
+    set_thread_lane(&lane);
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
         std::shared_ptr<Req> job;
@@ -319,7 +321,7 @@ void Server::worker(int id)
     lk.unlock();
     set_thread_lane(nullptr);
     cudaStreamSynchronize(s);
-    if (buf) ctx_free(c, buf, red_bytes);
+    ctx_free(c, buf, red_bytes);
     cudaStreamDestroy(s);
 }
 
@@ -371,8 +373,21 @@ hisq_status hisq_submit(hisq_ctx *c, const hisq_request *r, uint64_t *ticket)
     {
         std::lock_guard<std::mutex> lk(c->mu);
         if (!c->server) {
+            // a worker per reduction lane that fits the budget (at least one)
+            cudaSetDevice(c->device);
+            std::vector<void *> lanes;
+            for (int i = 0; i < kWorkers; i++) {
+                void *buf = nullptr;
+                if (ctx_alloc(c, Server::lane_bytes(), &buf) != HISQ_OK) break;
+                if (cudaMemset(buf, 0, Server::lane_bytes()) != cudaSuccess) {
+                    ctx_free(c, buf, Server::lane_bytes());
+                    break;
+                }
+                lanes.push_back(buf);
+            }
+            if (lanes.empty()) return fail(c, HISQ_ENOMEM, "no device memory for a request worker's reduction lane");
             c->server = new Server(c);
-            for (int i = 0; i < kWorkers; i++) c->server->workers.emplace_back(&Server::worker, c->server, i);
+            for (void *buf : lanes) c->server->workers.emplace_back(&Server::worker, c->server, buf);
         }
     }
     Server *sv = c->server;
