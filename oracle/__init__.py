@@ -70,6 +70,7 @@ def _load():
         "or_gauge_emulate": (None, [_p, _p, _i, _i, _i, _i, _i, _d, _p]),
         "or_spinor_emulate": (None, [_i64, _i, _p, _p]),
         "or_cg": (_i, [_p, _p, _p, _d, _d, _p, _p, _d, _i, _i, _p, _p]),
+        "or_mixed_cg": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _d, _d, _i, _i, _i, _p, _p, _p, _p]),
         "or_multishift_cg": (_i, [_p, _p, _p, _d, _i, _p, _p, _p, _p, _i, _p, _p, _p]),
         "or_bicgstabl": (_i, [_p, _p, _p, _d, _i, _p, _p, _d, _i, _p, _p]),
         "or_dense": (None, [_p, _p, _p, _d, _d, _i, _p]),
@@ -258,6 +259,26 @@ def cg(dims, fat, lng, m: float, b, tol: float, maxiter: int = 100000, sigma: fl
     st = _load().or_cg(_ptr(L), _ptr(f), _ptr(g), float(m), float(sigma), _ptr(bb), _ptr(x), float(tol),
                        int(maxiter), int(x0 is not None), ctypes.byref(it), ctypes.byref(tr))
     return x, int(st), it.value, tr.value
+
+
+def mixed_cg(dims, fat, lng, m: float, b, sfmt: str, tol: float, fat_s=None, lng_s=None, delta: float = 0.1,
+             nbuf: int = 8, pr: bool = True, reproject: bool = True, maxiter: int = 100000):
+    """Stabilised mixed-precision CG on M_ee x = b (Sec. 3.1) in FP64 with every sloppy vector write
+    rounded through ``sfmt`` and the sloppy operator applied with (fat_s, lng_s) (default: the exact
+    links).  Returns (x, status, iters, reliable_updates, true_res, history of |r_k|/|b|)."""
+    L = _dims(dims)
+    f, g, bb = _np(fat), _np(lng), _np(b)
+    fs = f if fat_s is None else _np(fat_s)
+    gs = g if lng_s is None else _np(lng_s)
+    x = np.zeros_like(bb)
+    hist = np.zeros(int(maxiter) + 1)
+    it, ru = ctypes.c_int(0), ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    opts = (1 if pr else 0) | (2 if reproject else 0)
+    st = _load().or_mixed_cg(_ptr(L), _ptr(f), _ptr(g), _ptr(fs), _ptr(gs), float(m), SFMT[sfmt], _ptr(bb),
+                             _ptr(x), float(tol), float(delta), int(nbuf), opts, int(maxiter), ctypes.byref(it),
+                             ctypes.byref(ru), ctypes.byref(tr), _ptr(hist))
+    return x, int(st), it.value, ru.value, tr.value, hist[: it.value + 1]
 
 
 def multishift_cg(dims, fat, lng, m: float, sigmas, tols, b, maxiter: int = 100000):

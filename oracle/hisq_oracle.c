@@ -621,6 +621,131 @@ int or_cg(const int *L, const double *fat, const double *lng, double m, double s
 }
 
 /* ------------------------------------------------------------------------ */
+/* O10 stabilised mixed-precision CG (Sec. 3.1), sloppy storage emulated      */
+/* ------------------------------------------------------------------------ */
+/* The reference for the algorithm's logic, not for the GPU's rounding: FP64
+ * arithmetic throughout, with every write of a sloppy vector (r, p, A p)
+ * rounded through spinor format sfmt (or_spinor_emulate), the sloppy operator
+ * applied with the links (fat_s, lng_s) -- for example the format-emulated
+ * copies of (fat, lng) -- and the true residuals with the exact (fat, lng).
+ * Sec. 3.1 and its footnote, in the readings used throughout:
+ *   reliable update (A13) when |r_k| < delta * max|r_j| over the iterations
+ *     since the last one, or when |r_k| <= tol |b|: x_hi is brought up to
+ *     date, the FP64 true residual r^ = b - A x_hi replaces r, and the solve
+ *     ends if |r^| <= tol |b|;
+ *   buffered x (A14): the directions p_j and steps alpha_j are kept in a ring
+ *     of nbuf entries and added to x_hi (FP64) when the ring is full and at
+ *     each reliable update;
+ *   re-projection (A15, opts bit 1): at a reliable update
+ *     p <- p - (r^+ p / r^+ r^) r^, beta = |r^|^2 / |r_old|^2 (Fletcher-Reeves),
+ *     p <- r^ + beta p;
+ *   Polak-Ribiere (A16, opts bit 0): beta = (|r_new|^2 - Re r_new^+ r_old)
+ *     / |r_old|^2; otherwise Fletcher-Reeves |r_new|^2 / |r_old|^2.
+ * x_ receives x_hi (starting from zero).  hist (NULL or maxiter + 1 entries)
+ * receives |r_k| / |b| of the iterated residual for k = 0..iters.  Returns 0
+ * on convergence, 1 at maxiter, 2 on breakdown (p^+ A p <= 0 or non-finite). */
+int or_mixed_cg(const int *L, const double *fat, const double *lng, const double *fat_s,
+                const double *lng_s, double m, int sfmt, const double *b_, double *x_, double tol,
+                double delta, int nbuf, int opts, int maxiter, int *iters, int *reliable,
+                double *true_res, double *hist)
+{
+    op_t op = {L, fat, lng, m, 0.0, 0}, ops = {L, fat_s, lng_s, m, 0.0, 0};
+    const int64_t n = op_len(&op), ns = n / 3;
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    if (nbuf < 1) nbuf = 1;
+    cplx *r = malloc(sizeof(cplx) * n), *r_old = malloc(sizeof(cplx) * n), *rh = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n), *Ap = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+    cplx *ring = malloc(sizeof(cplx) * n * nbuf);
+    double *al = malloc(sizeof(double) * nbuf);
+    int nring = 0;
+#define STORE(dst, src) or_spinor_emulate(ns, sfmt, (const double *)(src), (double *)(dst))
+#define FLUSH()                                                                 \
+    do {                                                                        \
+        for (int j_ = 0; j_ < nring; j_++)                                      \
+            for (int64_t i_ = 0; i_ < n; i_++) x[i_] += al[j_] * ring[(int64_t)j_ * n + i_]; \
+        nring = 0;                                                              \
+    } while (0)
+    memset(x, 0, sizeof(cplx) * n);
+    const double bb = nrm2(n, b);
+    memcpy(rh, b, sizeof(cplx) * n); /* r^ = b - A 0 */
+    STORE(r, rh);
+    memcpy(p, r, sizeof(cplx) * n);
+    double rr = nrm2(n, r), rmax = sqrt(rr);
+    int k = 0, ru = 0, status = 1;
+    if (hist) hist[0] = sqrt(rr / bb);
+    if (sqrt(nrm2(n, rh)) <= tol * sqrt(bb)) status = 0;
+    while (status == 1 && k < maxiter) {
+        op_apply(&ops, p, t);
+        STORE(Ap, t);
+        const double pAp = creal(cdot(n, p, Ap));
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            status = 2;
+            break;
+        }
+        const double alpha = rr / pAp;
+        memcpy(ring + (int64_t)nring * n, p, sizeof(cplx) * n);
+        al[nring++] = alpha;
+        memcpy(r_old, r, sizeof(cplx) * n);
+        for (int64_t i = 0; i < n; i++) t[i] = r[i] - alpha * Ap[i];
+        STORE(r, t);
+        const double rr_new = nrm2(n, r);
+        k++;
+        if (hist) hist[k] = sqrt(rr_new / bb);
+        if (nring == nbuf) FLUSH();
+        const int trigger = sqrt(rr_new) < delta * rmax || sqrt(rr_new) <= tol * sqrt(bb);
+        if (sqrt(rr_new) > rmax) rmax = sqrt(rr_new);
+        if (trigger) {
+            FLUSH();
+            op_apply(&op, x, t);
+            for (int64_t i = 0; i < n; i++) rh[i] = b[i] - t[i];
+            const double hh = nrm2(n, rh);
+            ru++;
+            if (sqrt(hh) <= tol * sqrt(bb)) {
+                status = 0;
+                break;
+            }
+            if (opts & 2) {
+                const cplx c = cdot(n, rh, p) / hh;
+                for (int64_t i = 0; i < n; i++) p[i] -= c * rh[i];
+            }
+            const double beta = hh / rr;
+            for (int64_t i = 0; i < n; i++) t[i] = rh[i] + beta * p[i];
+            STORE(p, t);
+            STORE(r, rh);
+            rr = hh;
+            rmax = sqrt(hh);
+            continue;
+        }
+        const double beta = (opts & 1) ? (rr_new - creal(cdot(n, r, r_old))) / rr : rr_new / rr;
+        if (!isfinite(beta)) {
+            status = 2;
+            break;
+        }
+        for (int64_t i = 0; i < n; i++) t[i] = r[i] + beta * p[i];
+        STORE(p, t);
+        rr = rr_new;
+    }
+    FLUSH();
+#undef STORE
+#undef FLUSH
+    op_apply(&op, x, t);
+    for (int64_t i = 0; i < n; i++) rh[i] = b[i] - t[i];
+    *true_res = sqrt(nrm2(n, rh) / bb);
+    *iters = k;
+    *reliable = ru;
+    free(r);
+    free(r_old);
+    free(rh);
+    free(p);
+    free(Ap);
+    free(t);
+    free(ring);
+    free(al);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* O7 multi-shift CG (Sec. 3.2; Jegerlehner, hep-lat/9612014), FP64          */
 /* ------------------------------------------------------------------------ */
 /* Solves (M_ee + sigma_i) x_i = b for i < nshift with sigma_0 the base shift.

@@ -7,7 +7,13 @@
   the single-shift case, which must reproduce CG;
 * BiCGStab(l) (Sec. 6.1) against a dense solve of the full ``2m + D`` and, at
   l = 1, against the textbook BiCGStab iterates written here from
-  van der Vorst's recurrences (a different algorithm that coincides at l = 1).
+  van der Vorst's recurrences (a different algorithm that coincides at l = 1);
+* the stabilised mixed-precision CG with emulated sloppy storage (Sec. 3.1):
+  with FP64 storage, exact links, no reliable update before convergence and
+  Fletcher-Reeves beta it is textbook CG, bit for bit; in every storage format
+  it reaches the FP64 true residual; and it reproduces the ordering Sec. 3.1
+  argues for: at a light mass the Polak-Ribiere, re-projected recurrence
+  converges where the plain Fletcher-Reeves one stalls.
 """
 import numpy as np
 import pytest
@@ -153,3 +159,51 @@ def test_bicgstabl_l1_is_bicgstab(orc, m, k):
     x, st, mv, tr = orc.bicgstabl(dims, fat, lng, m, b, 1, 0.0, max_matvecs=2 * k)
     assert mv == 2 * k
     assert np.linalg.norm(cvec(x) - xt) <= 1e-11 * np.linalg.norm(xt)
+
+
+def test_mixed_cg_reduces_to_textbook_cg(orc):
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    x0, st0, it0, _ = orc.cg(dims, fat, lng, m, b, 1e-10)
+    # FP64 storage, exact links, delta = 0 (one reliable update, at convergence), FR beta: the same recurrence
+    x, st, it, ru, tr, hist = orc.mixed_cg(dims, fat, lng, m, b, "f64", 1e-10, delta=0.0, pr=False,
+                                           reproject=False)
+    assert st == st0 == 0 and it == it0 and ru == 1
+    np.testing.assert_array_equal(x, x0)
+    assert hist[0] == pytest.approx(1.0) and hist[-1] <= 1e-10
+    # Polak-Ribiere equals Fletcher-Reeves in exact arithmetic (r_new is orthogonal to r_old)
+    x, st, it, ru, tr, _ = orc.mixed_cg(dims, fat, lng, m, b, "f64", 1e-10, delta=0.0, pr=True, reproject=True)
+    assert st == 0 and abs(it - it0) <= 1 and tr <= 1e-10
+    assert np.linalg.norm(x - x0) / np.linalg.norm(x0) <= 1e-9
+
+
+@pytest.mark.parametrize("sfmt", ["f32", "half", "int20", "int30"])
+def test_mixed_cg_emulated_formats_converge(orc, sfmt):
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    gf = "fix32" if sfmt == "int30" else ("f32" if sfmt == "f32" else "fix16")
+    fs = orc.gauge_emulate(dims, fat, gf, 18, False)
+    ls = orc.gauge_emulate(dims, lng, gf, 12, True)
+    _, _, it0, _ = orc.cg(dims, fat, lng, m, b, 1e-10)
+    x, st, it, ru, tr, hist = orc.mixed_cg(dims, fat, lng, m, b, sfmt, 1e-10, fat_s=fs, lng_s=ls)
+    assert st == 0 and tr <= 1e-10
+    assert ru >= 2  # delta = 0.1 fires before convergence
+    assert it <= 1.1 * it0
+    r = b - orc.mee(dims, fat, lng, m, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(tr, rel=1e-6)
+
+
+def test_mixed_cg_stabilisation_ordering(orc):
+    dims, m = (6, 6, 6, 6), 0.002
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    fs = orc.gauge_emulate(dims, fat, "fix16", 18, False)
+    ls = orc.gauge_emulate(dims, lng, "fix16", 12, True)
+    _, st_s, it_s, _, tr_s, _ = orc.mixed_cg(dims, fat, lng, m, b, "half", 1e-10, fat_s=fs, lng_s=ls, pr=True,
+                                             reproject=True, maxiter=8000)
+    _, st_p, it_p, _, tr_p, _ = orc.mixed_cg(dims, fat, lng, m, b, "half", 1e-10, fat_s=fs, lng_s=ls, pr=False,
+                                             reproject=False, maxiter=8000)
+    assert st_s == 0 and tr_s <= 1e-10
+    assert st_p == 1 and tr_p > 1e-10
