@@ -71,6 +71,7 @@ def _load():
         "or_spinor_emulate": (None, [_i64, _i, _p, _p]),
         "or_cg": (_i, [_p, _p, _p, _d, _d, _p, _p, _d, _i, _i, _p, _p]),
         "or_mixed_cg": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _d, _d, _i, _i, _i, _p, _p, _p, _p]),
+        "or_mixed_multishift": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _i, _d, _p, _p, _d, _i, _p, _p, _p, _p]),
         "or_multishift_cg": (_i, [_p, _p, _p, _d, _i, _p, _p, _p, _p, _i, _p, _p, _p]),
         "or_bicgstabl": (_i, [_p, _p, _p, _d, _i, _p, _p, _d, _i, _p, _p]),
         "or_dense": (None, [_p, _p, _p, _d, _d, _i, _p]),
@@ -295,6 +296,31 @@ def multishift_cg(dims, fat, lng, m: float, sigmas, tols, b, maxiter: int = 1000
     st = _load().or_multishift_cg(_ptr(L), _ptr(f), _ptr(g), float(m), ns, _ptr(s), _ptr(t), _ptr(bb),
                                   _ptr(x), int(maxiter), _ptr(its), _ptr(z), _ptr(r))
     return x, int(st), its, z, r
+
+
+# relative precision of each storage format (the freezing floor of A17)
+EPS_FMT = {"f64": 0.0, "f32": 2.0 ** -24, "half": 2.0 ** -15, "int20": 2.0 ** -19, "int30": 2.0 ** -29}
+
+
+def mixed_multishift(dims, fat, lng, m: float, sigmas, tols, b, sfmt: str, fat_s=None, lng_s=None,
+                     delta: float = 0.1, maxiter: int = 100000):
+    """The multi-shift stage with sloppy storage ``sfmt`` emulated (Sec. 3.2, A17).  ``sigmas`` ascending.
+    Returns (x [nshift][Vh][3][2], status, iters, reliable_updates, shift_iters, residuals after the stage)."""
+    L = _dims(dims)
+    f, g, bb = _np(fat), _np(lng), _np(b)
+    fs = f if fat_s is None else _np(fat_s)
+    gs = g if lng_s is None else _np(lng_s)
+    ns = len(sigmas)
+    s = np.ascontiguousarray(sigmas, dtype=np.float64)
+    t = np.ascontiguousarray(tols, dtype=np.float64)
+    x = np.zeros((ns,) + bb.shape)
+    its = np.zeros(ns, dtype=np.int32)
+    res = np.zeros(ns)
+    it, ru = ctypes.c_int(0), ctypes.c_int(0)
+    st = _load().or_mixed_multishift(_ptr(L), _ptr(f), _ptr(g), _ptr(fs), _ptr(gs), float(m), ns, _ptr(s),
+                                     _ptr(t), SFMT[sfmt], EPS_FMT[sfmt], _ptr(bb), _ptr(x), float(delta),
+                                     int(maxiter), ctypes.byref(it), ctypes.byref(ru), _ptr(its), _ptr(res))
+    return x, int(st), it.value, ru.value, its, res
 
 
 def bicgstabl(dims, fat, lng, m: float, b, l: int, tol: float, max_matvecs: int = 200000):

@@ -833,6 +833,123 @@ int or_multishift_cg(const int *L, const double *fat, const double *lng, double 
 }
 
 /* ------------------------------------------------------------------------ */
+/* O10 multi-shift stage with emulated sloppy storage (Sec. 3.2)              */
+/* ------------------------------------------------------------------------ */
+/* The multi-shift recurrences of or_multishift_cg with every write of a
+ * sloppy vector (r, A p, p_i) rounded through spinor format sfmt, the sloppy
+ * operator applied with (fat_s, lng_s) and, in the readings used throughout
+ * (A17): base system = sigma[0] (the smallest shift; the caller sorts); a
+ * reliable update of the base system when |r| < delta * max|r| since the
+ * last one (the FP64 true residual of x_0 with the exact links replaces r,
+ * Fletcher-Reeves beta, the shifted p_i kept); shift i > 0 stops updating
+ * once |zeta_i| |r| <= max(tol_i, 10 eps) |b| with eps the format's relative
+ * precision (eps_fmt); the stage ends when every shift but the base has
+ * stopped.  The x_i accumulate in FP64 here.  x is [nshift][Vh][3][2];
+ * shift_iters[i] the iteration at which shift i stopped (the stage's length
+ * for the base); resid[i] = |b - (M_ee + sigma_i) x_i| / |b| with the exact
+ * links after the stage (before any refinement).  Returns 0 when every
+ * shift but the base stopped, 1 at maxiter, 2 on breakdown or a bad shift
+ * count (1..64); *iters the stage's iterations, *reliable its reliable
+ * updates. */
+int or_mixed_multishift(const int *L, const double *fat, const double *lng, const double *fat_s,
+                        const double *lng_s, double m, int nshift, const double *sigma,
+                        const double *tol, int sfmt, double eps_fmt, const double *b_, double *x_,
+                        double delta, int maxiter, int *iters, int *reliable, int *shift_iters,
+                        double *resid)
+{
+    if (nshift < 1 || nshift > 64) return 2;
+    op_t op = {L, fat, lng, m, sigma[0], 0}, ops = {L, fat_s, lng_s, m, sigma[0], 0};
+    const int64_t n = op_len(&op), ns = n / 3;
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    cplx *r = malloc(sizeof(cplx) * n), *w = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+    cplx *p = malloc(sizeof(cplx) * n * nshift);
+    double z[64], zm[64], zn[64];
+    int live[64];
+#define STORE(dst, src) or_spinor_emulate(ns, sfmt, (const double *)(src), (double *)(dst))
+    STORE(r, b);
+    memset(x, 0, sizeof(cplx) * n * nshift);
+    for (int i = 0; i < nshift; i++) {
+        memcpy(p + i * n, r, sizeof(cplx) * n);
+        z[i] = zm[i] = 1.0;
+        live[i] = 1;
+        shift_iters[i] = 0;
+    }
+    const double bnorm = sqrt(nrm2(n, b));
+    double rr = nrm2(n, r), rmax = sqrt(rr), alpha_m = 1.0, beta_m = 0.0;
+    int k = 0, ru = 0, nlive = nshift - 1, status = 1;
+    if (nlive == 0) status = 0;
+    while (status == 1 && k < maxiter) {
+        op_apply(&ops, p, t);
+        STORE(w, t);
+        const double pAp = creal(cdot(n, p, w));
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            status = 2;
+            break;
+        }
+        const double alpha = rr / pAp;
+        for (int i = 0; i < nshift; i++) {
+            if (!live[i]) continue;
+            const double s = sigma[i] - sigma[0];
+            zn[i] = z[i] * zm[i] * alpha_m /
+                    (alpha * beta_m * (zm[i] - z[i]) + zm[i] * alpha_m * (1.0 + s * alpha));
+            const double ai = alpha * zn[i] / z[i];
+            for (int64_t j = 0; j < n; j++) x[i * n + j] += ai * p[i * n + j];
+        }
+        for (int64_t j = 0; j < n; j++) t[j] = r[j] - alpha * w[j];
+        STORE(r, t);
+        double rr_new = nrm2(n, r);
+        k++;
+        if (sqrt(rr_new) < delta * rmax) {
+            /* reliable update of the base system */
+            op_apply(&op, x, t);
+            for (int64_t j = 0; j < n; j++) t[j] = b[j] - t[j];
+            STORE(r, t);
+            rr_new = nrm2(n, t);
+            rmax = sqrt(rr_new);
+            ru++;
+        } else if (sqrt(rr_new) > rmax) {
+            rmax = sqrt(rr_new);
+        }
+        const double beta = rr_new / rr;
+        for (int i = 0; i < nshift; i++) {
+            if (!live[i]) continue;
+            const double bi = beta * (zn[i] / z[i]) * (zn[i] / z[i]);
+            for (int64_t j = 0; j < n; j++) t[j] = zn[i] * r[j] + bi * p[i * n + j];
+            STORE(p + i * n, t);
+            zm[i] = z[i];
+            z[i] = zn[i];
+            if (i > 0 && fabs(z[i]) * sqrt(rr_new) <= fmax(tol[i], 10.0 * eps_fmt) * bnorm) {
+                live[i] = 0;
+                shift_iters[i] = k;
+                nlive--;
+            }
+        }
+        rr = rr_new;
+        alpha_m = alpha;
+        beta_m = beta;
+        if (nlive == 0) status = 0;
+    }
+#undef STORE
+    shift_iters[0] = k;
+    for (int i = 1; i < nshift; i++)
+        if (live[i]) shift_iters[i] = k;
+    for (int i = 0; i < nshift; i++) {
+        op_t oi = {L, fat, lng, m, sigma[i], 0};
+        op_apply(&oi, x + i * n, t);
+        for (int64_t j = 0; j < n; j++) t[j] = b[j] - t[j];
+        resid[i] = sqrt(nrm2(n, t)) / bnorm;
+    }
+    *iters = k;
+    *reliable = ru;
+    free(r);
+    free(w);
+    free(t);
+    free(p);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* O8 BiCGStab(l) (Sec. 6.1; Sleijpen and Fokkema 1993), FP64                */
 /* ------------------------------------------------------------------------ */
 /* Solves (2m + D) x = b on the full lattice from x = 0 with shadow residual
