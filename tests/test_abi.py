@@ -53,3 +53,46 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(hisq, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         hisq.lib()
+
+
+def test_host_controls_and_refusals(lib):
+    """Calls that need no device: the launch-shape and fused-pass controls
+    return their previous value and refuse out-of-range values (-2) without
+    changing the setting; null contexts are refused, not dereferenced."""
+    from paper_2302_09224_gb300 import hisq
+
+    old = hisq.hisq_stencil_config(2)
+    try:
+        assert hisq.hisq_stencil_config(99) == -2 and hisq.hisq_stencil_config(-5) == -2
+        assert hisq.hisq_stencil_config(3) == 2  # the refused calls left 2 in place
+    finally:
+        hisq.hisq_stencil_config(old)
+    old = hisq.hisq_stencil_config_reduce(-1)
+    try:
+        assert hisq.hisq_stencil_config_reduce(99) == -2
+        assert hisq.hisq_stencil_config_reduce(old) == -1
+    finally:
+        hisq.hisq_stencil_config_reduce(old)
+    old = hisq.hisq_mee_fused(0)
+    try:
+        assert hisq.hisq_mee_fused(2) == -2 and hisq.hisq_mee_fused(-1) == -2
+        assert hisq.hisq_mee_fused(old) == 0
+    finally:
+        hisq.hisq_mee_fused(old)
+    assert hisq.hisq_mem_used(None) == 0 and hisq.hisq_launch_count(None) == 0
+    assert hisq.hisq_last_error(None) == "null context"
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_profile_sample(None, 1)
+
+
+def test_create_without_a_device_is_refused(lib):
+    """On a host without a GPU the library loads (every entry point is there)
+    and hisq_create refuses cleanly instead of falling back to the CPU."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(hisq.HisqError, match="EINVAL"):
+        hisq.hisq_create(0)
