@@ -71,6 +71,7 @@ def _load():
         "or_spinor_emulate": (None, [_i64, _i, _p, _p]),
         "or_cg": (_i, [_p, _p, _p, _d, _d, _p, _p, _d, _i, _i, _p, _p]),
         "or_mixed_cg": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _d, _d, _i, _i, _i, _p, _p, _p, _p]),
+        "or_mixed_bicgstabl": (_i, [_p, _p, _p, _p, _p, _d, _i, _i, _p, _p, _d, _d, _i, _p, _p, _p]),
         "or_mixed_multishift": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _i, _d, _p, _p, _d, _i, _p, _p, _p, _p]),
         "or_multishift_cg": (_i, [_p, _p, _p, _d, _i, _p, _p, _p, _p, _i, _p, _p, _p]),
         "or_bicgstabl": (_i, [_p, _p, _p, _d, _i, _p, _p, _d, _i, _p, _p]),
@@ -333,6 +334,23 @@ def bicgstabl(dims, fat, lng, m: float, b, l: int, tol: float, max_matvecs: int 
     st = _load().or_bicgstabl(_ptr(L), _ptr(f), _ptr(g), float(m), int(l), _ptr(bb), _ptr(x), float(tol),
                               int(max_matvecs), ctypes.byref(mv), ctypes.byref(tr))
     return x, int(st), mv.value, tr.value
+
+
+def mixed_bicgstabl(dims, fat, lng, m: float, b, l: int, sfmt: str, tol: float, fat_s=None, lng_s=None,
+                    delta: float = 0.1, max_matvecs: int = 200000):
+    """BiCGStab(l) on (2m + D) x = b with sloppy storage ``sfmt`` emulated and reliable updates at the end
+    of a cycle (Sec. 6.1, A19).  Returns (x, status, matvecs, reliable_updates, true_res)."""
+    L = _dims(dims)
+    f, g, bb = _np(fat), _np(lng), _np(b)
+    fs = f if fat_s is None else _np(fat_s)
+    gs = g if lng_s is None else _np(lng_s)
+    x = np.zeros_like(bb)
+    mv, ru = ctypes.c_int(0), ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    st = _load().or_mixed_bicgstabl(_ptr(L), _ptr(f), _ptr(g), _ptr(fs), _ptr(gs), float(m), int(l), SFMT[sfmt],
+                                    _ptr(bb), _ptr(x), float(tol), float(delta), int(max_matvecs),
+                                    ctypes.byref(mv), ctypes.byref(ru), ctypes.byref(tr))
+    return x, int(st), mv.value, ru.value, tr.value
 
 
 def dense(dims, fat, lng, which: str, m: float = 0.0, sigma: float = 0.0):

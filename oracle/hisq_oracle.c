@@ -1048,6 +1048,138 @@ int or_bicgstabl(const int *L, const double *fat, const double *lng, double m, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* O10 BiCGStab(l) with emulated sloppy storage (Sec. 6.1, Table 2)           */
+/* ------------------------------------------------------------------------ */
+/* The cycle of or_bicgstabl on M = 2m + D with every write of r_0..r_l and
+ * u_0..u_l rounded through spinor format sfmt and the operator applied with
+ * the sloppy links (fat_s, lng_s); x accumulates in FP64.  In the reading A19
+ * (the same trigger as A13): at the end of a cycle, when |r_0| < delta *
+ * max|r_0| since the last reliable update or |r_0| <= tol |b|, the FP64 true
+ * residual b - M x with the exact links replaces r_0 (u_0, rho, alpha and
+ * omega are kept) and the solve ends if it meets tol.  Returns 0 on
+ * convergence, 1 at max_matvecs, 2 on breakdown; *matvecs counts sloppy
+ * operator applications, *reliable the reliable updates. */
+int or_mixed_bicgstabl(const int *L, const double *fat, const double *lng, const double *fat_s,
+                       const double *lng_s, double m, int l, int sfmt, const double *b_, double *x_,
+                       double tol, double delta, int max_matvecs, int *matvecs, int *reliable,
+                       double *true_res)
+{
+    op_t op = {L, fat, lng, m, 0.0, 1}, ops = {L, fat_s, lng_s, m, 0.0, 1};
+    const int64_t n = op_len(&op), ns = n / 3;
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    if (l < 1 || l > 16) return 2;
+    cplx *R = malloc(sizeof(cplx) * n * (l + 1)); /* r_0..r_l */
+    cplx *U = malloc(sizeof(cplx) * n * (l + 1)); /* u_0..u_l */
+    cplx *rt = malloc(sizeof(cplx) * n), *t = malloc(sizeof(cplx) * n);
+#define STORE(dst) or_spinor_emulate(ns, sfmt, (const double *)(dst), (double *)(dst))
+    memset(x, 0, sizeof(cplx) * n);
+    memcpy(R, b, sizeof(cplx) * n);
+    STORE(R);
+    memcpy(rt, R, sizeof(cplx) * n);
+    memset(U, 0, sizeof(cplx) * n);
+    const double bnorm = sqrt(nrm2(n, b));
+    cplx rho0 = 1, alpha = 0, omega = 1;
+    cplx tau[17][17], gp[17], g[17], gpp[17];
+    double sig[17];
+    double rmax = sqrt(nrm2(n, R));
+    int mv = 0, ru = 0, status = 1;
+    if (rmax <= tol * bnorm) status = 0;
+    while (status == 1 && mv < max_matvecs) {
+        rho0 = -omega * rho0;
+        for (int j = 0; j < l; j++) {
+            cplx rho1 = cdot(n, rt, R + j * n);
+            if (cabs(rho0) == 0.0) { status = 2; break; }
+            cplx beta = alpha * rho1 / rho0;
+            rho0 = rho1;
+            for (int i = 0; i <= j; i++) {
+                for (int64_t k = 0; k < n; k++) U[i * n + k] = R[i * n + k] - beta * U[i * n + k];
+                STORE(U + i * n);
+            }
+            op_apply(&ops, U + j * n, U + (j + 1) * n);
+            STORE(U + (j + 1) * n);
+            mv++;
+            cplx gam = cdot(n, rt, U + (j + 1) * n);
+            if (cabs(gam) == 0.0) { status = 2; break; }
+            alpha = rho0 / gam;
+            for (int i = 0; i <= j; i++) {
+                for (int64_t k = 0; k < n; k++) R[i * n + k] -= alpha * U[(i + 1) * n + k];
+                STORE(R + i * n);
+            }
+            op_apply(&ops, R + j * n, R + (j + 1) * n);
+            STORE(R + (j + 1) * n);
+            mv++;
+            for (int64_t k = 0; k < n; k++) x[k] += alpha * U[k];
+        }
+        if (status == 2) break;
+        for (int j = 1; j <= l; j++) {
+            for (int i = 1; i < j; i++) {
+                tau[i][j] = cdot(n, R + i * n, R + j * n) / sig[i];
+                for (int64_t k = 0; k < n; k++) R[j * n + k] -= tau[i][j] * R[i * n + k];
+            }
+            STORE(R + j * n);
+            sig[j] = nrm2(n, R + j * n);
+            if (!(sig[j] > 0.0)) { status = 2; break; }
+            gp[j] = cdot(n, R + j * n, R) / sig[j];
+        }
+        if (status == 2) break;
+        g[l] = gp[l];
+        omega = g[l];
+        for (int j = l - 1; j >= 1; j--) {
+            cplx s = 0;
+            for (int i = j + 1; i <= l; i++) s += tau[j][i] * g[i];
+            g[j] = gp[j] - s;
+        }
+        for (int j = 1; j <= l - 1; j++) {
+            cplx s = 0;
+            for (int i = j + 1; i <= l - 1; i++) s += tau[j][i] * g[i + 1];
+            gpp[j] = g[j + 1] + s;
+        }
+        for (int64_t k = 0; k < n; k++) {
+            x[k] += g[1] * R[k];
+            R[k] -= gp[l] * R[l * n + k];
+            U[k] -= g[l] * U[l * n + k];
+        }
+        for (int j = 1; j <= l - 1; j++)
+            for (int64_t k = 0; k < n; k++) {
+                U[k] -= g[j] * U[j * n + k];
+                x[k] += gpp[j] * R[j * n + k];
+                R[k] -= gp[j] * R[j * n + k];
+            }
+        STORE(R);
+        STORE(U);
+        if (!isfinite(creal(omega)) || !isfinite(cimag(omega))) { status = 2; break; }
+        const double rn = sqrt(nrm2(n, R));
+        if (rn < delta * rmax || rn <= tol * bnorm) {
+            op_apply(&op, x, t);
+            for (int64_t k = 0; k < n; k++) t[k] = b[k] - t[k];
+            const double hn = sqrt(nrm2(n, t));
+            ru++;
+            if (hn <= tol * bnorm) {
+                status = 0;
+                break;
+            }
+            memcpy(R, t, sizeof(cplx) * n);
+            STORE(R);
+            rmax = hn;
+        } else if (rn > rmax) {
+            rmax = rn;
+        }
+    }
+#undef STORE
+    op_apply(&op, x, t);
+    for (int64_t k = 0; k < n; k++) t[k] = b[k] - t[k];
+    *true_res = sqrt(nrm2(n, t)) / bnorm;
+    *matvecs = mv;
+    *reliable = ru;
+    free(R);
+    free(U);
+    free(rt);
+    free(t);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* O9 dense reference                                                        */
 /* ------------------------------------------------------------------------ */
 /* Column k of the operator applied to unit vector e_k (complex, column-major
