@@ -299,13 +299,13 @@ def multishift_cg(dims, fat, lng, m: float, sigmas, tols, b, maxiter: int = 1000
     return x, int(st), its, z, r
 
 
-# relative precision of each storage format (the freezing floor of A17)
+# relative precision of each storage format (a shifted system's freezing floor is 10 times it)
 EPS_FMT = {"f64": 0.0, "f32": 2.0 ** -24, "half": 2.0 ** -15, "int20": 2.0 ** -19, "int30": 2.0 ** -29}
 
 
 def mixed_multishift(dims, fat, lng, m: float, sigmas, tols, b, sfmt: str, fat_s=None, lng_s=None,
                      delta: float = 0.1, maxiter: int = 100000):
-    """The multi-shift stage with sloppy storage ``sfmt`` emulated (Sec. 3.2, A17).  ``sigmas`` ascending.
+    """The multi-shift stage with sloppy storage ``sfmt`` emulated (Sec. 3.2).  ``sigmas`` ascending.
     Returns (x [nshift][Vh][3][2], status, iters, reliable_updates, shift_iters, residuals after the stage)."""
     L = _dims(dims)
     f, g, bb = _np(fat), _np(lng), _np(b)
@@ -339,7 +339,7 @@ def bicgstabl(dims, fat, lng, m: float, b, l: int, tol: float, max_matvecs: int 
 def mixed_bicgstabl(dims, fat, lng, m: float, b, l: int, sfmt: str, tol: float, fat_s=None, lng_s=None,
                     delta: float = 0.1, max_matvecs: int = 200000):
     """BiCGStab(l) on (2m + D) x = b with sloppy storage ``sfmt`` emulated and reliable updates at the end
-    of a cycle (Sec. 6.1, A19).  Returns (x, status, matvecs, reliable_updates, true_res)."""
+    of a cycle (Sec. 6.1).  Returns (x, status, matvecs, reliable_updates, true_res)."""
     L = _dims(dims)
     f, g, bb = _np(fat), _np(lng), _np(b)
     fs = f if fat_s is None else _np(fat_s)

@@ -629,17 +629,17 @@ int or_cg(const int *L, const double *fat, const double *lng, double m, double s
  * applied with the links (fat_s, lng_s) -- for example the format-emulated
  * copies of (fat, lng) -- and the true residuals with the exact (fat, lng).
  * Sec. 3.1 and its footnote, in the readings used throughout:
- *   reliable update (A13) when |r_k| < delta * max|r_j| over the iterations
+ *   reliable update when |r_k| < delta * max|r_j| over the iterations
  *     since the last one, or when |r_k| <= tol |b|: x_hi is brought up to
  *     date, the FP64 true residual r^ = b - A x_hi replaces r, and the solve
  *     ends if |r^| <= tol |b|;
- *   buffered x (A14): the directions p_j and steps alpha_j are kept in a ring
+ *   buffered x: the directions p_j and steps alpha_j are kept in a ring
  *     of nbuf entries and added to x_hi (FP64) when the ring is full and at
  *     each reliable update;
- *   re-projection (A15, opts bit 1): at a reliable update
+ *   re-projection (opts bit 1): at a reliable update
  *     p <- p - (r^+ p / r^+ r^) r^, beta = |r^|^2 / |r_old|^2 (Fletcher-Reeves),
  *     p <- r^ + beta p;
- *   Polak-Ribiere (A16, opts bit 0): beta = (|r_new|^2 - Re r_new^+ r_old)
+ *   Polak-Ribiere (opts bit 0): beta = (|r_new|^2 - Re r_new^+ r_old)
  *     / |r_old|^2; otherwise Fletcher-Reeves |r_new|^2 / |r_old|^2.
  * x_ receives x_hi (starting from zero).  hist (NULL or maxiter + 1 entries)
  * receives |r_k| / |b| of the iterated residual for k = 0..iters.  Returns 0
@@ -837,8 +837,8 @@ int or_multishift_cg(const int *L, const double *fat, const double *lng, double 
 /* ------------------------------------------------------------------------ */
 /* The multi-shift recurrences of or_multishift_cg with every write of a
  * sloppy vector (r, A p, p_i) rounded through spinor format sfmt, the sloppy
- * operator applied with (fat_s, lng_s) and, in the readings used throughout
- * (A17): base system = sigma[0] (the smallest shift; the caller sorts); a
+ * operator applied with (fat_s, lng_s) and, in the readings used throughout:
+ * base system = sigma[0] (the smallest shift; the caller sorts); a
  * reliable update of the base system when |r| < delta * max|r| since the
  * last one (the FP64 true residual of x_0 with the exact links replaces r,
  * Fletcher-Reeves beta, the shifted p_i kept); shift i > 0 stops updating
@@ -1052,8 +1052,8 @@ int or_bicgstabl(const int *L, const double *fat, const double *lng, double m, i
 /* ------------------------------------------------------------------------ */
 /* The cycle of or_bicgstabl on M = 2m + D with every write of r_0..r_l and
  * u_0..u_l rounded through spinor format sfmt and the operator applied with
- * the sloppy links (fat_s, lng_s); x accumulates in FP64.  In the reading A19
- * (the same trigger as A13): at the end of a cycle, when |r_0| < delta *
+ * the sloppy links (fat_s, lng_s); x accumulates in FP64.  In the reading used
+ * throughout (the CG trigger): at the end of a cycle, when |r_0| < delta *
  * max|r_0| since the last reliable update or |r_0| <= tol |b|, the FP64 true
  * residual b - M x with the exact links replaces r_0 (u_0, rho, alpha and
  * omega are kept) and the solve ends if it meets tol.  Returns 0 on
