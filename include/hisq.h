@@ -403,7 +403,10 @@ typedef struct {
  * starts only when the context's HBM budget has room for it; otherwise its
  * requests wait.  b and x stay owned by the caller and must stay valid until
  * the request is done; the gauge must not be freed while requests use it.
- * Errors: EINVAL (bad request), EBUSY (queue full). */
+ * The first call starts the workers, one per reduction lane (partial sums,
+ * counters, error flag; about 17 MB each) that fits the budget, up to four.
+ * Errors: EINVAL (bad request), EBUSY (queue full), ENOMEM (first call: not
+ * even one worker's lane fits the budget). */
 HISQ_API hisq_status hisq_submit(hisq_ctx *ctx, const hisq_request *req, uint64_t *ticket);
 
 /* Non-blocking: *done = 1 and info filled once the request finished (the
