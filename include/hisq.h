@@ -59,7 +59,10 @@ typedef enum {
     HISQ_ECUDA = 5,       /* a CUDA runtime call failed */
     HISQ_EBUSY = 6,       /* request queue full */
     HISQ_ETIMEOUT = 7,    /* bounded wait expired */
-    HISQ_ENOTFOUND = 8    /* unknown ticket or gauge */
+    HISQ_ENOTFOUND = 8,   /* unknown ticket or gauge */
+    HISQ_ERANGE = 9       /* a result could not be stored in its storage format (non-finite, or beyond
+                             the format's exponent range): the packed formats write such a site as
+                             zero, FP64 and FP32 keep the non-finite value */
 } hisq_status;
 
 /* Storage format of the gauge field (Sec. 4, the three-precision triplet). */
@@ -147,7 +150,10 @@ HISQ_API double hisq_gauge_scale(const hisq_gauge *g, int which);
  * output is the decoded storage-format result.  on_device selects device or
  * host pointers; stream is a cudaStream_t (NULL: the context's stream).
  * Errors: EINVAL (unsupported prec, r12 not possible, non-finite input),
- * ENOMEM, ECUDA. */
+ * ERANGE (some output sites could not be stored in the spinor format: the
+ * result overflowed the compute precision or the format's exponent range;
+ * out holds zero there for the packed formats, the non-finite value for FP64
+ * and FP32), ENOMEM, ECUDA. */
 HISQ_API hisq_status hisq_dslash(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec prec, int out_parity, double a,
                         const double *xpay_in, const double *in, double *out, int on_device,
                         void *stream);
@@ -170,13 +176,15 @@ HISQ_API hisq_status hisq_dslash(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec p
  *  - at most HISQ_NOALLOC_MAX_SITES sites per parity, else EINVAL;
  *  - the gauge field must already hold its stored copy for `prec` (any earlier
  *    hisq_dslash or solver call with that precision builds it), else EINVAL;
+ *  - the call copies a counter back to the host and synchronises `stream`,
+ *    so it must not be made while `stream` is being captured (EINVAL);
  *  - the first call on a device looks up the scratch array's device address
- *    once (cudaGetSymbolAddress); make that first call before any stream
- *    capture;
+ *    once (cudaGetSymbolAddress);
+ *  - output sites that cannot be stored in the spinor format return ERANGE,
+ *    as in hisq_dslash;
  *  - every call uses the same scratch array, which keeps the previous call's
  *    contents (the counter is cleared at each call): calls whose work overlaps
- *    on the GPU (several streams or host threads) race, so serialise them;
- *  - the call synchronises `stream` before returning. */
+ *    on the GPU (several streams or host threads) race, so serialise them. */
 HISQ_API hisq_status hisq_dslash_noalloc(hisq_ctx *ctx, const hisq_gauge *g, hisq_prec prec, int out_parity,
                                          double a, const double *xpay_in, const double *in, double *out,
                                          void *stream);
@@ -276,6 +284,13 @@ HISQ_API int hisq_mee_fused(int mode);
  * blocks asked per SM (0, the default: as many as fit).  Negative values leave
  * a setting unchanged.  For benchmarking. */
 HISQ_API void hisq_mee_fused_shape(int lag, int blocks_per_sm);
+/* Test control of the fused pass's bounded waits (a block waits for earlier
+ * t-slices of the same launch): polls = polls before a wait gives up (0: the
+ * default, 2^22 polls of at least 64 ns each); unreachable = 1 raises every
+ * wait's target past what the launch can reach, so each wait runs to its
+ * limit, the kernel flags the error and goes on, and the solver returns
+ * ECUDA.  Only for testing that a wait ends; 0 restores normal waits. */
+HISQ_API void hisq_mee_fused_wait_test(unsigned polls, int unreachable);
 HISQ_API int hisq_stencil_config_reduce(int cfg);
 /* The shape in use for triplet p on gauge g's lattice (plain pass, or the
  * reducing pass if reduce != 0): the forced one, else the tuned one, else -1

@@ -199,8 +199,9 @@ TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Ga
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         (void)cudaGetLastError();
+        // first result wins (a concurrent tuning of the same key keeps it)
         std::lock_guard<std::mutex> lk(tile_mu);
-        tile_cache[key] = best;
+        return tile_cache.emplace(key, best).first->second;
     }
     return best;
 }

@@ -274,6 +274,8 @@ hisq_status gauge_view_existing(hisq_ctx *c, const hisq_gauge *g, const hisq_pre
     hisq_status st = check_prec(c, p);
     if (st) return st;
     v->fat = v->lng = nullptr;
+    // another thread may be appending a copy (gauge_view_for): look up under its lock
+    std::lock_guard<std::mutex> lk(g->copy_mu);
     for (auto &lc : g->fat_copies)
         if (lc.gf == p.gauge && lc.recon == p.fat_recon) v->fat = lc.ptr;
     for (auto &lc : g->lng_copies)
@@ -656,9 +658,16 @@ hisq_status hisq_dslash(hisq_ctx *c, const hisq_gauge *gc, hisq_prec prec, int o
         launch_unpack_spinor(prec.spinor, prec.compute, vh, out_s + h * bs, dout + h * vh * 6, s);
     }
     if (!on_device) e = cudaMemcpyAsync(out, out64, b64, cudaMemcpyDeviceToHost, s);
+    // the stencil flags output sites it could not store
+    int bad_out = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_out, cur_err(c), sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash");
+    if (bad_out)
+        return fail(c, HISQ_ERANGE,
+                    "hisq_dslash: output sites not storable in the spinor format (overflow or beyond its exponent "
+                    "range)");
     return HISQ_OK;
 }
 

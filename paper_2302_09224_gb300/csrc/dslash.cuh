@@ -498,8 +498,8 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
                 for (int d = -3; d <= 3; d++) {
                     const int t = (slice + d + Lt) % Lt;
                     unsigned polls = 0;
-                    while (ld_acquire(done + t) < (unsigned)nch) {
-                        if (++polls > kMeeWaitPolls) {
+                    while (ld_acquire(done + t) < (unsigned)nch + m.wait_extra) {
+                        if (++polls > m.wait_polls) {
                             atomicOr(a2.err, 2);
                             break;
                         }

@@ -36,6 +36,7 @@ bool mee_fused_available(int gf, int sf, int cf, const Geom &g)
 }
 
 extern std::atomic<int> fused_lag, fused_bps;
+extern std::atomic<unsigned> fused_wait_polls, fused_wait_extra;
 
 bool launch_mee_fused(int gf, int sf, int cf, int long_recon, const MeeArgs &m_in, cudaStream_t s)
 {
@@ -43,6 +44,8 @@ bool launch_mee_fused(int gf, int sf, int cf, int long_recon, const MeeArgs &m_i
     MeeArgs m = m_in;
     m.lag = fused_lag.load();
     m.blocks_per_sm = fused_bps.load();
+    m.wait_polls = fused_wait_polls.load();
+    m.wait_extra = fused_wait_extra.load();
     const int cfg = 4;
     if (gf == G_F32) return launch_mee_f32(long_recon, cfg, m, s);
     if (sf == S_HALF) return launch_mee_half(long_recon, cfg, m, s);
@@ -158,8 +161,11 @@ void tune_variant(int gf, int sf, int cf, int lrec, bool red, const DslashArgs &
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     (void)cudaGetLastError();
+    // first result wins: a thread that tuned the same pair concurrently keeps
+    // the shape already in use, so every launch after the first insertion of a
+    // key (and hence every block-sum order) is the same for the whole process
     std::lock_guard<std::mutex> lk(tune_mu);
-    tune_cache[key] = best;
+    tune_cache.emplace(key, best);
 }
 
 }  // namespace
@@ -212,6 +218,13 @@ extern "C" int hisq_mee_fused(int mode)
 
 namespace hisq {
 std::atomic<int> fused_lag{4}, fused_bps{0};
+std::atomic<unsigned> fused_wait_polls{kMeeWaitPolls}, fused_wait_extra{0};
+}
+
+extern "C" void hisq_mee_fused_wait_test(unsigned polls, int unreachable)
+{
+    hisq::fused_wait_polls.store(polls > 0 ? polls : hisq::kMeeWaitPolls);
+    hisq::fused_wait_extra.store(unreachable ? 1u : 0u);
 }
 
 extern "C" void hisq_mee_fused_shape(int lag, int blocks_per_sm)

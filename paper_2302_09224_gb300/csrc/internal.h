@@ -190,6 +190,8 @@ struct MeeArgs {
     DslashArgs d2;
     int lag;            // slices between the last D_oe a D_eo slice reads and that D_eo
     int blocks_per_sm;  // resident blocks per SM asked (0: as many as fit)
+    unsigned wait_polls;    // polls before a wait gives up (set by the launcher)
+    unsigned wait_extra;    // added to every wait's target: nonzero only to test the bound
 };
 
 // A tile of right-hand sides for the batched stencil: right-hand side t lives
@@ -275,7 +277,7 @@ struct hisq_gauge {
     double fat_max = 0, lng_max = 0;
     bool fat_r12_ok = false, lng_r12_ok = false;
     std::vector<hisq::LinkCopy> fat_copies, lng_copies;
-    std::mutex copy_mu;        // lazily built reduced-format copies
+    mutable std::mutex copy_mu;  // guards fat_copies / lng_copies (built lazily)
 };
 
 namespace hisq {

@@ -57,20 +57,25 @@ extern "C" hisq_status hisq_dslash_noalloc(hisq_ctx *c, const hisq_gauge *g, his
     if (vh > kMaxSites)
         return fail(c, HISQ_EINVAL, "hisq_dslash_noalloc: %lld sites per parity exceed its fixed scratch (%lld)",
                     (long long)vh, (long long)kMaxSites);
-    cudaSetDevice(c->device);
+    if (c->device < 0 || c->device >= kMaxDevices) return fail(c, HISQ_EINVAL, "device index out of range");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash_noalloc: cudaSetDevice");
+    cudaStream_t s = pick_stream(c, stream);
+    // the counter read-back and the synchronisation below cannot be captured
+    if (stream_capturing(s))
+        return fail(c, HISQ_EINVAL, "hisq_dslash_noalloc cannot be called while its stream is being captured");
     GaugeView gv{};
     hisq_status st = gauge_view_existing(c, g, prec, &gv);
     if (st) return st;
     char *sc = nullptr;
     st = scratch_address(c, &sc);
     if (st) return st;
-    cudaStream_t s = pick_stream(c, stream);
     const int nhalf = out_parity == 2 ? 2 : 1;
     const size_t bs = spinor_field_bytes(prec.spinor, vh);
     char *in_s = sc, *y_s = sc + kFieldBytes, *out_s = sc + 2 * kFieldBytes;
     int *bad = reinterpret_cast<int *>(sc + 3 * kFieldBytes);
     // the array keeps the previous call's contents: the counter starts at zero
-    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    e = cudaMemsetAsync(bad, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash_noalloc");
     for (int h = 0; h < nhalf; h++) {
         launch_pack_spinor(prec.spinor, vh, in + h * vh * 6, in_s + h * bs, bad, s);
@@ -108,8 +113,15 @@ extern "C" hisq_status hisq_dslash_noalloc(hisq_ctx *c, const hisq_gauge *g, his
         launch_unpack_spinor(prec.spinor, prec.compute, vh, out_s + h * bs, out + h * vh * 6, s);
         c->launches++;
     }
-    e = cudaStreamSynchronize(s);
+    // the stencil flags output sites it could not store
+    int bad_out = 0;
+    e = cudaMemcpyAsync(&bad_out, bad, sizeof bad_out, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "hisq_dslash_noalloc");
+    if (bad_out)
+        return fail(c, HISQ_ERANGE,
+                    "hisq_dslash_noalloc: output sites not storable in the spinor format (overflow or beyond its "
+                    "exponent range)");
     return HISQ_OK;
 }

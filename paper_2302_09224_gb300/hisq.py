@@ -18,9 +18,9 @@ LIB_PATH = os.path.join(HERE, "libhisq.so")
 # enums (mirror include/hisq.h)
 # ---------------------------------------------------------------------------
 HISQ_OK, HISQ_EINVAL, HISQ_ENOMEM, HISQ_ENOTCONV, HISQ_EBREAKDOWN = 0, 1, 2, 3, 4
-HISQ_ECUDA, HISQ_EBUSY, HISQ_ETIMEOUT, HISQ_ENOTFOUND = 5, 6, 7, 8
+HISQ_ECUDA, HISQ_EBUSY, HISQ_ETIMEOUT, HISQ_ENOTFOUND, HISQ_ERANGE = 5, 6, 7, 8, 9
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ECUDA", 6: "EBUSY",
-                7: "ETIMEOUT", 8: "ENOTFOUND"}
+                7: "ETIMEOUT", 8: "ENOTFOUND", 9: "ERANGE"}
 
 HISQ_GAUGE_F64, HISQ_GAUGE_F32, HISQ_GAUGE_FIX16, HISQ_GAUGE_FIX32 = 0, 1, 2, 3
 HISQ_SPINOR_F64, HISQ_SPINOR_F32, HISQ_SPINOR_HALF16, HISQ_SPINOR_INT20, HISQ_SPINOR_INT30 = 0, 1, 2, 3, 4
@@ -134,6 +134,7 @@ _SIGS = {
     "hisq_stencil_config_reduce": (_I, [_I]),
     "hisq_mee_fused": (_I, [_I]),
     "hisq_mee_fused_shape": (None, [_I, _I]),
+    "hisq_mee_fused_wait_test": (None, [ctypes.c_uint, _I]),
     "hisq_stencil_config_in_use": (_I, [_P, hisq_prec, _I]),
     "hisq_default_params": (None, [ctypes.POINTER(hisq_solver_params)]),
     "hisq_cg": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P, ctypes.POINTER(hisq_solve_info)]),
@@ -326,6 +327,10 @@ def hisq_mee_fused(mode: int) -> int:
 
 def hisq_mee_fused_shape(lag: int, blocks_per_sm: int):
     lib().hisq_mee_fused_shape(int(lag), int(blocks_per_sm))
+
+
+def hisq_mee_fused_wait_test(polls: int, unreachable: bool):
+    lib().hisq_mee_fused_wait_test(int(polls) & 0xFFFFFFFF, int(bool(unreachable)))
 
 
 def hisq_stencil_config_reduce(cfg: int) -> int:

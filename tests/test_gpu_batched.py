@@ -5,8 +5,10 @@ right-hand sides shares each link load (Sec. 1, block solvers).
   meets the target, for each batched sloppy format and tile size;
 * a right-hand side's iterates do not depend on which others share its batch:
   the same system solved in a batch of four and in a batch of two (same tile)
-  gives bitwise identical solutions, and agrees with the single-RHS solver
-  within ten times the tolerance;
+  gives bitwise identical solutions; against the single-RHS solver (another
+  stencil kernel, so other rounding) both solutions meet the tolerance, so
+  their difference is within twice the tolerance in the residual norm
+  |M_ee (x_a - x_b)| / |b|;
 * nor on its tile or the kernel: tiles of 1, 2 and 4 with both kernels (and
   1, 4 and 16 right-hand sides per tile) give bitwise identical solutions;
 * the batched stencil equals the single-RHS stencil through the oracle check of
@@ -73,15 +75,18 @@ def test_batched_true_residuals(ctx, orc, name, tile):
     assert info.true_residual <= 1e-10
 
 
-def test_same_alone_and_in_the_mix(ctx):
-    dims, m = (8, 8, 8, 16), 0.02
+def test_same_alone_and_in_the_mix(ctx, orc):
+    dims, m, tol = (8, 8, 8, 16), 0.02, 1e-10
     bs = [synth.spinor(dims, synth.rhs_seed(k)).numpy() for k in range(4)]
-    _, _, x4 = solve(ctx, dims, m, bs, "int20", tile=2)
-    _, _, x2 = solve(ctx, dims, m, bs[:2], "int20", tile=2)
+    _, _, x4 = solve(ctx, dims, m, bs, "int20", tile=2, tol=tol)
+    _, _, x2 = solve(ctx, dims, m, bs[:2], "int20", tile=2, tol=tol)
     np.testing.assert_array_equal(x4[:2], x2)
-    _, _, x1 = solve(ctx, dims, m, bs[:1], "int20")  # the single-RHS solver
-    d = np.linalg.norm(x4[0] - x1[0]) / np.linalg.norm(x1[0])
-    assert d <= 10 * 1e-10 * 1e3   # both meet 1e-10; x differs by at most kappa*tol
+    _, _, x1 = solve(ctx, dims, m, bs[:1], "int20", tol=tol)  # the single-RHS solver
+    # x is fixed only up to the tolerance: both meet it, so in the residual
+    # norm the two solutions differ by at most 2 tol (triangle inequality)
+    fat, lng = lattice(dims)
+    d = np.linalg.norm(orc.mee(dims, fat, lng, m, x4[0] - x1[0])) / np.linalg.norm(bs[0])
+    assert d <= 2 * tol, d
 
 
 def test_iterates_independent_of_tile(ctx):

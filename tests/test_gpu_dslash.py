@@ -233,3 +233,33 @@ def test_launch_shape_controls(ctx):
         hisq.hisq_stencil_config(prev)
         hisq.hisq_stencil_config_reduce(prev_r)
         hisq.hisq_free_gauge(ctx, g)
+
+
+# largest input magnitude each triplet stores without loss of range: FP32 max
+# for the FP32-compute triplets (and the FP32-pair arithmetic of 30-bit/FP64),
+# FP64 max for plain FP64
+HUGE = {"f64": 1.7e308, "f32": 3.3e38, "half": 3.3e38, "int20": 3.3e38, "int30": 3.3e38, "int30f32": 3.3e38}
+
+
+@pytest.mark.parametrize("name", list(BOUND_EXACT))
+def test_unstorable_output_is_reported(ctx, name):
+    """Finite inputs whose stencil result overflows the compute precision:
+    the input packs, the output cannot be stored, and the call returns ERANGE
+    instead of a silently zeroed site; the next call on the context works."""
+    dims = (4, 4, 4, 8)
+    fat, lng = lattice(dims, False)
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    try:
+        p = hisq.prec(name, 12)
+        x = synth.spinor(dims, 1).cuda()
+        big = x / x.abs().max() * HUGE[name]
+        out = torch.empty_like(x)
+        with pytest.raises(hisq.HisqError, match="ERANGE"):
+            hisq.hisq_dslash(ctx, g, p, 0, 0.0, None, big, out, True)
+        ref = torch.empty_like(x)
+        hisq.hisq_dslash(ctx, g, p, 0, 0.0, None, x, ref, True)
+        hisq.hisq_dslash(ctx, g, p, 0, 0.0, None, x, out, True)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all() and torch.equal(out, ref)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)

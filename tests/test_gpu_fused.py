@@ -21,13 +21,13 @@ def ctx():
     hisq.hisq_destroy(c)
 
 
-def solve(ctx, dims, m, name, recon, fused, anti=False, tol=1e-10):
+def solve(ctx, dims, m, name, recon, fused, anti=False, tol=1e-10, maxiter=100000):
     fat, lng = synth.gauge_pair(dims, seed=0, antiperiodic_t=anti)
     g = hisq.hisq_load_gauge(ctx, dims, fat.cuda(), lng.cuda(), flags=1 if anti else 0)
     prev = hisq.hisq_mee_fused(1 if fused else 0)
     try:
         p = hisq.hisq_default_params()
-        p.mass, p.tol, p.on_device = m, tol, 1
+        p.mass, p.tol, p.on_device, p.maxiter = m, tol, 1, maxiter
         p.sloppy = hisq.prec(name, recon)
         b = synth.spinor(dims, synth.rhs_seed(0)).cuda()
         x = torch.zeros_like(b)
@@ -58,3 +58,22 @@ def test_fused_switch(ctx):
     prev = hisq.hisq_mee_fused(1)
     assert hisq.hisq_mee_fused(prev) == 1
     assert hisq.hisq_mee_fused(5) == -2
+
+
+def test_exhausted_wait_returns_ecuda_and_context_recovers(ctx, orc):
+    """The fused pass's waits are bounded: with every wait's target made
+    unreachable (a count no block ever reaches) and a short poll limit, each
+    wait gives up, the kernel flags the error and finishes, and the solver
+    returns ECUDA instead of hanging; with normal waits restored the same
+    context solves the system."""
+    dims, m = (8, 8, 8, 16), 0.05
+    hisq.hisq_mee_fused_wait_test(4, True)
+    try:
+        with pytest.raises(hisq.HisqError, match="ECUDA"):
+            solve(ctx, dims, m, "int20", 12, True, maxiter=64)
+    finally:
+        hisq.hisq_mee_fused_wait_test(0, False)
+    st, info, b, x, fat, lng = solve(ctx, dims, m, "int20", 12, True)
+    assert st == hisq.HISQ_OK
+    r = b - orc.mee(dims, fat, lng, m, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10

@@ -3,10 +3,13 @@
 A seeded Poisson-like stream of requests on two lattice volumes, with
 different masses and tolerances and some multi-shift requests, is queued at
 once; every result's FP64 true residual, recomputed by the CPU oracle, must
-meet its own target, and every CG result must equal the same request solved
-alone (same batch session shape), bitwise or at least within ten times its
-tolerance.  Bounded waits time out cleanly, unknown tickets and bad requests
-are refused, and the stats report latency percentiles and throughput.
+meet its own target, and every result must equal the same request solved
+alone, bitwise: a CG request's arithmetic does not depend on the batch
+session's other slots, its tile or when it joined (it always starts at a
+block boundary), and a multi-shift request runs the same kernels on the same
+grid whatever else is on the device.  Bounded waits time out cleanly,
+unknown tickets and bad requests are refused, and the stats report latency
+percentiles and throughput.
 """
 import time
 
@@ -87,15 +90,21 @@ def test_stream_in_the_mix_matches_alone(env, orc):
             for i, s in enumerate(sig):
                 r = bb - orc.mee(d, fat, lng, q["mass"], xx[i], sigma=s)
                 assert np.linalg.norm(r) / np.linalg.norm(bb) <= q["tol"]
-    # the same CG requests alone
-    for t, (q, b, x, sig) in list(results.items())[:6]:
-        if sig is not None:
-            continue
+    # every request again, alone: the same bits, shift by shift for multi-shift
+    n_cg = n_ms = 0
+    for t, (q, b, x, sig) in results.items():
         t2, b2, x2, _ = submit(ctx, gauges, q)
-        st, _ = hisq.hisq_wait(ctx, t2, 60.0)
+        st, _ = hisq.hisq_wait(ctx, t2, 120.0)
         assert st == hisq.HISQ_OK
-        a, m = as_np(x2), as_np(x)
-        assert np.linalg.norm(a - m) <= 10 * q["tol"] * 1e3 * np.linalg.norm(a)
+        alone, mixed = as_np(x2), as_np(x)
+        if sig is None:
+            n_cg += 1
+            np.testing.assert_array_equal(alone, mixed)
+        else:
+            n_ms += 1
+            for i in range(len(sig)):
+                np.testing.assert_array_equal(alone[i], mixed[i])
+    assert n_cg > 0 and n_ms > 0
     s = hisq.hisq_serve_stats(ctx)
     assert s.completed >= 24 and s.latency_p99_s >= s.latency_p50_s > 0 and s.solves_per_s > 0
 

@@ -3,7 +3,8 @@
 It must give the same result as hisq_dslash (the allocating entry point) on
 the same inputs, call after call, although all its calls share one fixed
 scratch array; sizes beyond its limit, missing gauge copies and non-finite
-inputs are refused with EINVAL and do not poison the next call.  This file is
+inputs are refused with EINVAL, a result that cannot be stored in the
+spinor format returns ERANGE, and none of these poisons the next call.  This file is
 collected last so that a failure here stops a -x run only after every other
 test has run.
 """
@@ -32,6 +33,8 @@ def rel(a, b):
     ("half", (16, 16, 16, 16), 2, 0.0),     # full lattice at the size limit
     ("f64", (4, 6, 8, 10), 1, 0.6),
     ("int30", (6, 4, 4, 10), 2, 0.3),
+    ("f64", (16, 16, 16, 16), 2, 0.7),      # widest format at the limit: the scratch filled to its end
+    ("int30", (16, 16, 16, 16), 2, -0.4),
 ])
 def test_matches_allocating_entry_point(ctx, name, dims, parity, a):
     fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
@@ -83,5 +86,28 @@ def test_refusals_and_recovery(ctx):
         hisq.hisq_dslash(ctx, g, hisq.prec("int20"), 0, 0.0, None, x, out, True)
         with pytest.raises(hisq.HisqError, match="exceed"):
             hisq.hisq_dslash_noalloc(ctx, g, hisq.prec("int20"), 0, 0.0, None, x, out)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+
+
+@pytest.mark.parametrize("name", ["f64", "f32", "int20", "int30"])
+def test_unstorable_output_is_reported(ctx, name):
+    """Finite inputs whose stencil result overflows the compute precision give
+    ERANGE (not a silently zeroed site), and the next call is correct."""
+    dims = (4, 4, 4, 8)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    try:
+        p = hisq.prec(name, 12)
+        x = synth.spinor(dims, 1, device="cuda")
+        big = x / x.abs().max() * (1.7e308 if name == "f64" else 3.3e38)
+        ref = torch.empty_like(x)
+        hisq.hisq_dslash(ctx, g, p, 0, 0.0, None, x, ref, True)
+        out = torch.empty_like(x)
+        with pytest.raises(hisq.HisqError, match="ERANGE"):
+            hisq.hisq_dslash_noalloc(ctx, g, p, 0, 0.0, None, big, out)
+        hisq.hisq_dslash_noalloc(ctx, g, p, 0, 0.0, None, x, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
     finally:
         hisq.hisq_free_gauge(ctx, g)
