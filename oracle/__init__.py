@@ -70,12 +70,15 @@ def _load():
         "or_gauge_emulate": (None, [_p, _p, _i, _i, _i, _i, _i, _d, _p]),
         "or_spinor_emulate": (None, [_i64, _i, _p, _p]),
         "or_cg": (_i, [_p, _p, _p, _d, _d, _p, _p, _d, _i, _i, _p, _p]),
-        "or_mixed_cg": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _d, _d, _i, _i, _i, _p, _p, _p, _p]),
+        "or_mixed_cg": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _d, _d, _d, _i, _i, _i, _p, _p, _p, _p]),
         "or_mixed_bicgstabl": (_i, [_p, _p, _p, _p, _p, _d, _i, _i, _p, _p, _d, _d, _i, _p, _p, _p]),
         "or_mixed_multishift": (_i, [_p, _p, _p, _p, _p, _d, _i, _p, _p, _i, _d, _p, _p, _d, _i, _p, _p, _p, _p]),
         "or_multishift_cg": (_i, [_p, _p, _p, _d, _i, _p, _p, _p, _p, _i, _p, _p, _p]),
         "or_bicgstabl": (_i, [_p, _p, _p, _d, _i, _p, _p, _d, _i, _p, _p]),
         "or_dense": (None, [_p, _p, _p, _d, _d, _i, _p]),
+        "or_schur_source": (None, [_p, _p, _p, _d, _p, _p]),
+        "or_reconstruct_odd": (None, [_p, _p, _p, _d, _p, _p, _p]),
+        "or_solve_full": (_i, [_p, _p, _p, _d, _p, _p, _d, _i, _p, _p]),
         "or_lu_solve": (_i, [_i64, _p, _p]),
     }
     for name, (res, args) in sig.items():
@@ -264,10 +267,12 @@ def cg(dims, fat, lng, m: float, b, tol: float, maxiter: int = 100000, sigma: fl
 
 
 def mixed_cg(dims, fat, lng, m: float, b, sfmt: str, tol: float, fat_s=None, lng_s=None, delta: float = 0.1,
-             nbuf: int = 8, pr: bool = True, reproject: bool = True, maxiter: int = 100000):
+             nbuf: int = 8, pr: bool = True, reproject: bool = True, maxiter: int = 100000, dyn_eps: float = 0.0):
     """Stabilised mixed-precision CG on M_ee x = b (Sec. 3.1) in FP64 with every sloppy vector write
     rounded through ``sfmt`` and the sloppy operator applied with (fat_s, lng_s) (default: the exact
-    links).  Returns (x, status, iters, reliable_updates, true_res, history of |r_k|/|b|)."""
+    links); ``dyn_eps > 0`` replaces the delta trigger by the error-estimate trigger with that
+    precision.  Returns (x, status, iters, reliable_updates, true_res, history of |r_k|/|b|, with the
+    recomputed true residual at reliable updates)."""
     L = _dims(dims)
     f, g, bb = _np(fat), _np(lng), _np(b)
     fs = f if fat_s is None else _np(fat_s)
@@ -278,9 +283,41 @@ def mixed_cg(dims, fat, lng, m: float, b, sfmt: str, tol: float, fat_s=None, lng
     tr = ctypes.c_double(0.0)
     opts = (1 if pr else 0) | (2 if reproject else 0)
     st = _load().or_mixed_cg(_ptr(L), _ptr(f), _ptr(g), _ptr(fs), _ptr(gs), float(m), SFMT[sfmt], _ptr(bb),
-                             _ptr(x), float(tol), float(delta), int(nbuf), opts, int(maxiter), ctypes.byref(it),
+                             _ptr(x), float(tol), float(delta), float(dyn_eps), int(nbuf), opts, int(maxiter),
+                             ctypes.byref(it),
                              ctypes.byref(ru), ctypes.byref(tr), _ptr(hist))
     return x, int(st), it.value, ru.value, tr.value, hist[: it.value + 1]
+
+
+def schur_source(dims, fat, lng, m: float, b):
+    """2m b_e - D_eo b_o: the even right-hand side of the reduced full system (b full-lattice)."""
+    L = _dims(dims)
+    f, g, bb = _np(fat), _np(lng), _np(b)
+    out = np.empty((vh_of(dims), 3, 2))
+    _load().or_schur_source(_ptr(L), _ptr(f), _ptr(g), float(m), _ptr(bb), _ptr(out))
+    return out
+
+
+def reconstruct_odd(dims, fat, lng, m: float, b_o, x_e):
+    """x_o = (b_o - D_oe x_e) / (2m)."""
+    L = _dims(dims)
+    f, g, bo, xe = _np(fat), _np(lng), _np(b_o), _np(x_e)
+    out = np.empty((vh_of(dims), 3, 2))
+    _load().or_reconstruct_odd(_ptr(L), _ptr(f), _ptr(g), float(m), _ptr(bo), _ptr(xe), _ptr(out))
+    return out
+
+
+def solve_full(dims, fat, lng, m: float, b, tol: float, maxiter: int = 100000):
+    """(2m + D) x = b on the full lattice by even/odd reduction, textbook CG and odd reconstruction.
+    Returns (x [2][Vh][3][2], status, iters, true_res)."""
+    L = _dims(dims)
+    f, g, bb = _np(fat), _np(lng), _np(b)
+    x = np.zeros_like(bb)
+    it = ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    st = _load().or_solve_full(_ptr(L), _ptr(f), _ptr(g), float(m), _ptr(bb), _ptr(x), float(tol), int(maxiter),
+                               ctypes.byref(it), ctypes.byref(tr))
+    return x, int(st), it.value, tr.value
 
 
 def multishift_cg(dims, fat, lng, m: float, sigmas, tols, b, maxiter: int = 100000):

@@ -23,9 +23,12 @@
  * with links that already carry the staggered phases, M = 2m + D on the full
  * lattice and M_ee = 4m^2 - D_eo D_oe on the even sites.
  *
- * Parity unpinned: none of the functions in this file; every one is checked
- * against closed forms, invariants, hand-derived bit patterns or a dense
- * direct solve by the tests.
+ * Parity unpinned: the iteration at which or_mixed_cg's error-estimate
+ * trigger fires (a heuristic the paper only names): it is checked through its
+ * limits (no update as its precision vanishes, more updates the coarser the
+ * precision) and through convergence, not against fixed counts.  Every other
+ * function is checked against closed forms, invariants, hand-derived bit
+ * patterns or a dense direct solve by the tests.
  */
 #include <complex.h>
 #include <math.h>
@@ -641,12 +644,24 @@ int or_cg(const int *L, const double *fat, const double *lng, double m, double s
  *     p <- r^ + beta p;
  *   Polak-Ribiere (opts bit 0): beta = (|r_new|^2 - Re r_new^+ r_old)
  *     / |r_old|^2; otherwise Fletcher-Reeves |r_new|^2 / |r_old|^2.
+ *   error-estimate trigger (dyn_eps > 0, in place of delta; the "more
+ *     dynamic choice based on explicit error estimation" of the Sec. 3
+ *     footnote, read after the residual replacement of van der Vorst and Ye,
+ *     SIAM J. Sci. Comput. 22 (2000) 835): d estimates the drift of the
+ *     iterated from the true residual, growing by the rounding of each sloppy
+ *     update, d_{k+1} = d_k + eps (|r_{k+1}| + |alpha_k| |A p_k|) with eps =
+ *     dyn_eps, the sloppy operator's relative precision; a reliable update
+ *     is made when d crosses sqrt(eps) |r| (d_k <= sqrt(eps) |r_k| and
+ *     d_{k+1} > sqrt(eps) |r_{k+1}|) and d_{k+1} > 1.1 d_init, or when
+ *     |r_k| <= tol |b|; after each update d = d_init = eps |r^|.
  * x_ receives x_hi (starting from zero).  hist (NULL or maxiter + 1 entries)
- * receives |r_k| / |b| of the iterated residual for k = 0..iters.  Returns 0
- * on convergence, 1 at maxiter, 2 on breakdown (p^+ A p <= 0 or non-finite). */
+ * receives |r_k| / |b| for k = 0..iters: the iterated residual, replaced by
+ * the recomputed true residual at the iterations that end with a reliable
+ * update (the jumps of Fig. 1).  Returns 0 on convergence, 1 at maxiter, 2
+ * on breakdown (p^+ A p <= 0 or non-finite). */
 int or_mixed_cg(const int *L, const double *fat, const double *lng, const double *fat_s,
                 const double *lng_s, double m, int sfmt, const double *b_, double *x_, double tol,
-                double delta, int nbuf, int opts, int maxiter, int *iters, int *reliable,
+                double delta, double dyn_eps, int nbuf, int opts, int maxiter, int *iters, int *reliable,
                 double *true_res, double *hist)
 {
     op_t op = {L, fat, lng, m, 0.0, 0}, ops = {L, fat_s, lng_s, m, 0.0, 0};
@@ -672,6 +687,8 @@ int or_mixed_cg(const int *L, const double *fat, const double *lng, const double
     STORE(r, rh);
     memcpy(p, r, sizeof(cplx) * n);
     double rr = nrm2(n, r), rmax = sqrt(rr);
+    const double eps_hat = sqrt(dyn_eps > 0.0 ? dyn_eps : 0.0);
+    double d = dyn_eps * sqrt(rr), d_init = d;
     int k = 0, ru = 0, status = 1;
     if (hist) hist[0] = sqrt(rr / bb);
     if (sqrt(nrm2(n, rh)) <= tol * sqrt(bb)) status = 0;
@@ -693,7 +710,15 @@ int or_mixed_cg(const int *L, const double *fat, const double *lng, const double
         k++;
         if (hist) hist[k] = sqrt(rr_new / bb);
         if (nring == nbuf) FLUSH();
-        const int trigger = sqrt(rr_new) < delta * rmax || sqrt(rr_new) <= tol * sqrt(bb);
+        int trigger = sqrt(rr_new) <= tol * sqrt(bb);
+        if (dyn_eps > 0.0) {
+            const double d_new = d + dyn_eps * (sqrt(rr_new) + fabs(alpha) * sqrt(nrm2(n, Ap)));
+            trigger = trigger ||
+                      (d <= eps_hat * sqrt(rr) && d_new > eps_hat * sqrt(rr_new) && d_new > 1.1 * d_init);
+            d = d_new;
+        } else {
+            trigger = trigger || sqrt(rr_new) < delta * rmax;
+        }
         if (sqrt(rr_new) > rmax) rmax = sqrt(rr_new);
         if (trigger) {
             FLUSH();
@@ -701,6 +726,8 @@ int or_mixed_cg(const int *L, const double *fat, const double *lng, const double
             for (int64_t i = 0; i < n; i++) rh[i] = b[i] - t[i];
             const double hh = nrm2(n, rh);
             ru++;
+            if (hist) hist[k] = sqrt(hh / bb);
+            d = d_init = dyn_eps * sqrt(hh);
             if (sqrt(hh) <= tol * sqrt(bb)) {
                 status = 0;
                 break;
@@ -946,6 +973,70 @@ int or_mixed_multishift(const int *L, const double *fat, const double *lng, cons
     free(w);
     free(t);
     free(p);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Full-system solve by even/odd reduction (Sec. 3; the step either side of  */
+/* the even/odd solvers)                                                     */
+/* ------------------------------------------------------------------------ */
+/* With M = 2m + D split into parity blocks [[2m, D_eo], [D_oe, 2m]], the odd
+ * unknowns are eliminated: from the odd rows x_o = (b_o - D_oe x_e) / (2m),
+ * and substituting into the even rows and multiplying by 2m gives
+ *   (4m^2 - D_eo D_oe) x_e = 2m b_e - D_eo b_o,
+ * i.e. M_ee x_e = bt_e.  For any x_e and x_o reconstructed from it, the full
+ * residual is zero on the odd sites and equals (bt_e - M_ee x_e) / (2m) on the
+ * even ones.  b, x: full-lattice fields [parity][cb][color]. */
+void or_schur_source(const int *L, const double *fat, const double *lng, double m, const double *b,
+                     double *bt)
+{
+    const int64_t n = vol_of(L) / 2 * 3;
+    const cplx *be = (const cplx *)b, *bo = be + n;
+    cplx *t = (cplx *)bt;
+    or_dslash(L, fat, lng, 0, (const double *)bo, bt); /* D_eo b_o */
+    for (int64_t i = 0; i < n; i++) t[i] = 2.0 * m * be[i] - t[i];
+}
+
+/* x_o = (b_o - D_oe x_e) / (2m); b_o, x_e, x_o are half-lattice fields. */
+void or_reconstruct_odd(const int *L, const double *fat, const double *lng, double m, const double *b_o,
+                        const double *x_e, double *x_o)
+{
+    const int64_t n = vol_of(L) / 2 * 3;
+    const cplx *bo = (const cplx *)b_o;
+    cplx *xo = (cplx *)x_o;
+    or_dslash(L, fat, lng, 1, x_e, x_o); /* D_oe x_e */
+    for (int64_t i = 0; i < n; i++) xo[i] = (bo[i] - xo[i]) / (2.0 * m);
+}
+
+/* Solves (2m + D) x = b on the full lattice: textbook CG (or_cg) on
+ * M_ee x_e = bt_e to the Schur tolerance tol * 2|m| |b| / |bt_e| (the even
+ * residual of the full system is the Schur residual over 2m, the odd one is
+ * zero), then the odd reconstruction.  *true_res = |b - M x| / |b|.  Returns
+ * or_cg's status (0 converged, 1 maxiter, 2 breakdown); m must be nonzero. */
+int or_solve_full(const int *L, const double *fat, const double *lng, double m, const double *b_,
+                  double *x_, double tol, int maxiter, int *iters, double *true_res)
+{
+    const int64_t n = vol_of(L) / 2 * 3;
+    const cplx *b = (const cplx *)b_;
+    cplx *x = (cplx *)x_;
+    cplx *bt = malloc(sizeof(cplx) * n), *r = malloc(sizeof(cplx) * 2 * n);
+    or_schur_source(L, fat, lng, m, b_, (double *)bt);
+    const double bb = nrm2(2 * n, b), btn = sqrt(nrm2(n, bt));
+    int status = 0;
+    double tr_schur = 0.0;
+    *iters = 0;
+    if (btn > 0.0) {
+        const double tol_s = tol * 2.0 * fabs(m) * sqrt(bb) / btn;
+        status = or_cg(L, fat, lng, m, 0.0, (const double *)bt, x_, tol_s, maxiter, 0, iters, &tr_schur);
+    } else {
+        memset(x, 0, sizeof(cplx) * n);
+    }
+    or_reconstruct_odd(L, fat, lng, m, (const double *)(b + n), x_, (double *)(x + n));
+    or_mfull(L, fat, lng, m, x_, (double *)r);
+    for (int64_t i = 0; i < 2 * n; i++) r[i] = b[i] - r[i];
+    *true_res = bb > 0.0 ? sqrt(nrm2(2 * n, r) / bb) : 0.0;
+    free(bt);
+    free(r);
     return status;
 }
 

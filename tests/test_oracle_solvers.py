@@ -275,3 +275,46 @@ def test_mixed_bicgstabl_int20_beats_half(orc):
                                                       max_matvecs=40000)
         assert st == 0 and tr <= 1e-10 and ru >= 2
     assert mv["int20"] < mv["half"]
+
+
+def test_mixed_cg_error_estimate_trigger_limits(orc):
+    """The error-estimate trigger (the footnote of Sec. 3, after van der Vorst
+    and Ye's residual replacement) with a vanishing precision never fires
+    before convergence, so the run is the delta = 0 run bit for bit.  With FP64
+    storage the estimate only grows with the precision it is given: the
+    coarser that precision, the earlier d crosses sqrt(eps) |r|, so the more
+    reliable updates, while the iterates (FP64 everywhere) stay those of CG."""
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    x0, st0, it0, ru0, tr0, h0 = orc.mixed_cg(dims, fat, lng, m, b, "f64", 1e-10, delta=0.0)
+    x1, st1, it1, ru1, tr1, h1 = orc.mixed_cg(dims, fat, lng, m, b, "f64", 1e-10, dyn_eps=1e-300)
+    assert st0 == st1 == 0 and it0 == it1 and ru0 == ru1 == 1
+    np.testing.assert_array_equal(x0, x1)
+    np.testing.assert_array_equal(h0, h1)
+    rus = []
+    for e in (2.0 ** -53, 2.0 ** -24, 2.0 ** -15):
+        _, st2, it2, ru2, tr2, _ = orc.mixed_cg(dims, fat, lng, m, b, "f64", 1e-10, dyn_eps=e)
+        assert st2 == 0 and abs(it2 - it0) <= 4 and tr2 <= 1e-10
+        rus.append(ru2)
+    assert rus[0] < rus[1] < rus[2]
+
+
+@pytest.mark.parametrize("sfmt,gf,eps", [("half", "fix16", 2.0 ** -15), ("int20", "fix16", 2.0 ** -15),
+                                         ("int30", "fix32", 2.0 ** -29)])
+def test_mixed_cg_error_estimate_trigger_converges(orc, sfmt, gf, eps):
+    """At the light mass where Fletcher-Reeves without re-projection stalls,
+    the stabilised CG driven by the error-estimate trigger reaches the FP64
+    true residual; its history shows the recomputed residual at each reliable
+    update, and updates come more often the coarser the sloppy format."""
+    dims, m = (6, 6, 6, 6), 0.002
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    fs = orc.gauge_emulate(dims, fat, gf, 18, False)
+    ls = orc.gauge_emulate(dims, lng, gf, 12, True)
+    x, st, it, ru, tr, hist = orc.mixed_cg(dims, fat, lng, m, b, sfmt, 1e-10, fat_s=fs, lng_s=ls, dyn_eps=eps,
+                                           maxiter=8000)
+    assert st == 0 and tr <= 1e-10 and ru >= 2
+    assert hist[-1] == pytest.approx(tr, rel=1e-12)
+    r = b - orc.mee(dims, fat, lng, m, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(tr, rel=1e-6)
