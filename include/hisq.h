@@ -292,6 +292,14 @@ HISQ_API void hisq_mee_fused_shape(int lag, int blocks_per_sm);
  * ECUDA.  Only for testing that a wait ends; 0 restores normal waits. */
 HISQ_API void hisq_mee_fused_wait_test(unsigned polls, int unreachable);
 HISQ_API int hisq_stencil_config_reduce(int cfg);
+/* Programmatic dependent launch of the solvers' kernel chains (stencil
+ * passes, their finish kernel and the fused BLAS kernels): 1 (default) lets
+ * each kernel's blocks be scheduled while its predecessor's last wave runs
+ * (every kernel waits for its predecessor's results before touching them, so
+ * results are identical either way); 0 launches them one after another.
+ * Returns the previous setting, or -2 for an invalid value.  For benchmarking;
+ * no counterpart in the paper. */
+HISQ_API int hisq_programmatic_launch(int mode);
 /* The shape in use for triplet p on gauge g's lattice (plain pass, or the
  * reducing pass if reduce != 0): the forced one, else the tuned one, else -1
  * when that pair has not been tuned yet. */
@@ -323,11 +331,25 @@ typedef struct {
     int32_t rhs_kernel;   /* batched stencil kernel: 0 tuned, 1 registers, 2 staged neighbour loads
                              (16-bit and 20-bit fermions only; EINVAL otherwise) */
     void *stream;         /* cudaStream_t; NULL: the context's stream */
+    double *history;      /* host array or NULL: with nrhs = 1, hisq_cg and hisq_solve_full write
+                             |r_k| / |b| of the CG's iterated residual for k = 0, 1, ... (at most
+                             history_len entries, up to the last iteration); at an iteration that
+                             ends with a reliable update the entry is the recomputed FP64 true
+                             residual instead (the jumps of Fig. 1) */
+    int32_t history_len;  /* entries of history (0: none kept) */
+    int32_t ru_trigger;   /* CG reliable-update trigger: 0 when |r| drops below delta times its
+                             maximum since the last update (Sec. 3 footnote); 1 an error estimate
+                             (the footnote's dynamic choice, after van der Vorst and Ye's residual
+                             replacement): the drift d of the iterated from the true residual grows
+                             by eps (|r_k+1| + |alpha_k| |A p_k|) per iteration, eps the sloppy
+                             triplet's coarsest unit roundoff, and an update is made when d
+                             crosses sqrt(eps) |r| (and exceeds 1.1 times its value after the last
+                             update) */
 } hisq_solver_params;
 
 /* Fills params with the defaults: delta 0.1, nbuf 8, pr_beta 1, reproject 1,
  * l 4, use_graph 1, nrhs 1, rhs_tile 0, rhs_kernel 0, maxiter 100000, tol 1e-10, sloppy
- * and refine FIX16/INT20/F32 with r12 long links. */
+ * and refine FIX16/INT20/F32 with r12 long links, no history, ru_trigger 0. */
 HISQ_API void hisq_default_params(hisq_solver_params *p);
 
 #define HISQ_MAX_SHIFTS 32
@@ -362,6 +384,25 @@ typedef struct {
  * EINVAL, ENOMEM, ECUDA. */
 HISQ_API hisq_status hisq_cg(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p, const double *b,
                     double *x, hisq_solve_info *info);
+
+/* Full-lattice solve of (2m + D) x = b (m != 0) by even/odd reduction
+ * around the CG of hisq_cg (Sec. 3: the solvers work on the even-site
+ * system; this is the step either side of them).  With M = [[2m, D_eo],
+ * [D_oe, 2m]] in parity blocks:
+ *   bt_e = 2m b_e - D_eo b_o                     (FP64 stencil),
+ *   (4m^2 - D_eo D_oe) x_e = bt_e                (hisq_cg with p),
+ *   x_o  = (b_o - D_oe x_e) / (2m)               (FP64 stencil).
+ * The even residual of the full system is the CG's residual over 2m and the
+ * odd one vanishes, so the CG runs to the tolerance tol * 2|m| |b| / |bt_e|,
+ * which makes |b - M x| / |b| <= tol.  b, x: full-lattice FP64 arrays
+ * ([parity][cb][color][re,im], even first), nrhs of them back to back;
+ * p->use_init_guess is ignored (the even CG starts from zero).
+ * info->true_residual is the FP64 |b - M x| / |b| (the largest over the
+ * right-hand sides); iters, matvecs and reliable updates are the CG's.
+ * Returns OK, ENOTCONV, EBREAKDOWN, EINVAL (m == 0 or as hisq_cg), ENOMEM,
+ * ECUDA. */
+HISQ_API hisq_status hisq_solve_full(hisq_ctx *ctx, const hisq_gauge *g, const hisq_solver_params *p,
+                                     const double *b, double *x, hisq_solve_info *info);
 
 /* Multi-shift CG (Sec. 3.2): solves (M_ee + sigma_i) x_i = b for nshift
  * shifts (<= HISQ_MAX_SHIFTS) in the sloppy precision with reliable updates on

@@ -143,8 +143,12 @@ __global__ void __launch_bounds__(kBlock) b_flush_kernel(BBArgs a)
     } while (0)
 
 using TileKey = std::array<int, 10>;
+// The fastest (T, variant) for a full batch, and per tile size (index log2 T)
+// the time of one tile launch with its fastest variant (ms; < 0: not timed).
 struct TileChoice {
     int T, variant;
+    float tile_ms[5];
+    int tile_var[5];
 };
 std::mutex tile_mu;
 std::map<TileKey, TileChoice> tile_cache;
@@ -162,7 +166,7 @@ TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Ga
         auto it = tile_cache.find(key);
         if (it != tile_cache.end()) return it->second;
     }
-    TileChoice best = {fixed > 0 ? fixed : 1, kernel == 2 ? 1 : 0};
+    TileChoice best = {fixed > 0 ? fixed : 1, kernel == 2 ? 1 : 0, {-1.f, -1.f, -1.f, -1.f, -1.f}, {0, 0, 0, 0, 0}};
     if (!thread_capturing() && !stream_capturing(s)) {
         cudaMemsetAsync(in, 0, fb * nrhs, s);
         DslashMArgs d{};
@@ -180,7 +184,7 @@ TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Ga
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
-        for (int T = 1; T <= 16; T *= 2) {
+        for (int T = 1, ti = 0; T <= 16; T *= 2, ti++) {
             if (nrhs % T || (fixed > 0 && T != fixed) || !red_fits(geom.vh, kMrhsBlock, 2 * T)) continue;
             for (int v = 0; v < 2; v++) {
                 if (kernel > 0 && v != kernel - 1) continue;
@@ -189,10 +193,16 @@ TileChoice tune_tile(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Ga
                 for (int r = 0; r < 2; r++) launch_dslash_mrhs(p.gauge, p.spinor, p.compute, p.long_recon, false, T, v, d, s);
                 cudaEventRecord(e1, s);
                 float ms = 0.f;
-                if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-                    ms < best_ms) {
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+                const float per_tile = ms / 2.0f / (float)(nrhs / T);
+                if (best.tile_ms[ti] < 0.f || per_tile < best.tile_ms[ti]) {
+                    best.tile_ms[ti] = per_tile;
+                    best.tile_var[ti] = v;
+                }
+                if (ms < best_ms) {
                     best_ms = ms;
-                    best = {T, v};
+                    best.T = T;
+                    best.variant = v;
                 }
             }
         }
@@ -224,7 +234,8 @@ BatchSession::BatchSession(hisq_ctx *c_, hisq_gauge *g_, const BCGConfig &cfg_, 
 
 BatchSession::~BatchSession()
 {
-    if (exec) cudaGraphExecDestroy(exec);
+    for (auto &kv : graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (sth) cudaFreeHost(sth);
 }
 
@@ -268,6 +279,7 @@ void BatchSession::stencil_pass(int parity_out, const char *in, char *out, const
     d.red = cur_red(c);
     d.st = st;
     d.slot = slot_i;
+    d.tile_mask = tile_mask;
     if (y) {
         d.xpay = 1;
         d.sign = -1;
@@ -386,6 +398,11 @@ hisq_status BatchSession::setup()
     const TileChoice tc = tune_tile(c, g->geom, cfg.sloppy, gv_s, nr, cfg.tile, cfg.kernel, ap_s, tmp_s, fb, s);
     T = tc.T;
     variant = tc.variant;
+    for (int i = 0; i < 5; i++) {
+        tile_ms[i] = tc.tile_ms[i];
+        tile_var[i] = tc.tile_var[i];
+    }
+    adapt = cfg.tile == 0 && cfg.kernel == 0;
     if (nr % T) return fail(c, HISQ_EINVAL, "RHS tile %d does not divide nrhs %d", T, nr);
     if (!red_fits(vh, kMrhsBlock, 2 * T) || !red_fits(vh, kBlock, 2 * kMaxRHS))
         return fail(c, HISQ_EINVAL, "lattice too large for a batched reduction over a tile of %d", T);
@@ -427,6 +444,9 @@ hisq_status BatchSession::load(int t, const double *b_planar, const double *x_pl
     occupied[t] = 1;
     CGState init{};
     init.delta2 = cfg.delta * cfg.delta;
+    init.dyn = cfg.dyn;
+    init.dyn_eps = cfg.dyn_eps;
+    init.dyn_hat = std::sqrt(cfg.dyn_eps);
     init.stop2 = stop2[t];
     init.pr = cfg.pr;
     init.reproject = cfg.reproject;
@@ -458,12 +478,58 @@ int BatchSession::active_slots() const
     return n;
 }
 
+// The tile for the next block of iterations.  Each right-hand side's
+// arithmetic is the same whatever its tile and kernel (lane-wise operations,
+// per-RHS partial sums over the same blocks), so the choice changes only the
+// cost: with the timed cost of one tile launch per tile size, pick the size
+// whose tiles holding an iterating system cost least, and launch only those
+// tiles (a session whose systems are finishing one by one then pays for the
+// systems left, not for the whole batch).
+void BatchSession::choose_tile()
+{
+    unsigned live = 0;
+    for (int t = 0; t < nr; t++)
+        if (occupied[t] && std::find(finished_now.begin(), finished_now.end(), t) == finished_now.end())
+            live |= 1u << t;
+    auto tiles_of = [&](int TT) {
+        unsigned m = 0;
+        for (int k = 0; k * TT < nr; k++)
+            if ((live >> (k * TT)) & ((1u << TT) - 1u)) m |= 1u << k;
+        return m;
+    };
+    if (adapt) {
+        float best = 1e30f;
+        int bT = T, bv = variant;
+        for (int TT = 1, ti = 0; TT <= kMaxRHS; TT *= 2, ti++) {
+            if (nr % TT || tile_ms[ti] < 0.f) continue;
+            const float cost = tile_ms[ti] * (float)__builtin_popcount(tiles_of(TT));
+            if (cost < best) {
+                best = cost;
+                bT = TT;
+                bv = tile_var[ti];
+            }
+        }
+        T = bT;
+        variant = bv;
+    }
+    tile_mask = tiles_of(T);
+}
+
 hisq_status BatchSession::step()
 {
     for (int t = 0; t < nr; t++) k0[t] = sth[t].k;
+    choose_tile();
     const bool graph = cfg.use_graph && !c->prof.on;
     if (graph) {
-        if (!exec) {
+        const uint64_t key = (uint64_t)T | ((uint64_t)variant << 8) | ((uint64_t)tile_mask << 16);
+        Graph &gg = graphs[key];
+        if (!gg.exec) {
+            if (graphs.size() > 64) {  // bound the cache: rebuild graphs as they are needed again
+                for (auto &kv : graphs)
+                    if (kv.second.exec && kv.first != key) cudaGraphExecDestroy(kv.second.exec);
+                graphs.clear();
+            }
+            Graph &ng = graphs[key];
             cudaGraph_t gr = nullptr;
             set_thread_capturing(true);
             cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -472,15 +538,16 @@ hisq_status BatchSession::step()
                 ce = cudaStreamEndCapture(s, &gr);
             }
             set_thread_capturing(false);
-            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, gr, 0);
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ng.exec, gr, 0);
             size_t nn = 0;
             if (ce == cudaSuccess) ce = graph_kernel_nodes(gr, &nn);
             if (gr) cudaGraphDestroy(gr);
             if (ce != cudaSuccess) return cuda_fail(c, ce, "batched CG graph capture");
-            nodes = (int64_t)nn;
+            ng.nodes = (int64_t)nn;
         }
-        cudaGraphLaunch(exec, s);
-        c->launches += nodes;
+        const Graph &run = graphs[key];
+        cudaGraphLaunch(run.exec, s);
+        c->launches += run.nodes;
     } else {
         iterate_block();
     }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <vector>
 
 #include "cg.h"
@@ -19,6 +20,8 @@ struct BCGConfig {
     int tile = 0;               // RHS per stencil launch (0: tuned)
     int kernel = 0;             // batched stencil: 0 tuned, 1 registers, 2 staged
     double delta = 0.1;
+    int dyn = 0;                // error-estimate trigger (every right-hand side)
+    double dyn_eps = 0.0;
 };
 
 // b64 / x64: nrhs FP64 planar half-lattice fields, 48*Vh bytes apart; infos:
@@ -42,8 +45,16 @@ struct BatchSession {
     std::vector<int> mv_hi, ru, k0, occupied, status;
     std::vector<double> bb, stop2, diag;
     std::vector<int> finished_now;
-    cudaGraphExec_t exec = nullptr;
-    int64_t nodes = 0;
+    // graphs of one block of iterations, per (tile, variant, launched tiles)
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t nodes = 0;
+    };
+    std::map<uint64_t, Graph> graphs;
+    float tile_ms[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};  // one tile launch per tile size (log2 T)
+    int tile_var[5] = {0, 0, 0, 0, 0};
+    bool adapt = false;      // the tile may change between blocks (not fixed by the caller)
+    unsigned tile_mask = 0;  // tiles launched in the current block
 
     BatchSession(hisq_ctx *c, hisq_gauge *g, const BCGConfig &cfg, cudaStream_t s);
     ~BatchSession();
@@ -64,6 +75,7 @@ struct BatchSession {
     char *slot(int j, int t);
     void stencil_pass(int parity_out, const char *in, char *out, const char *y, bool red, int slot_i);
     void iterate_block();
+    void choose_tile();
     hisq_status pull();
     void reliable_update(int t, int nslots, int j, bool x_zero);
 };

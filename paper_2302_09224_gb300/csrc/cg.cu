@@ -292,6 +292,17 @@ struct CGRun {
         init.pr = cfg.pr;
         init.reproject = cfg.reproject;
         init.active = 1;
+        init.dyn = cfg.dyn;
+        init.dyn_eps = cfg.dyn_eps;
+        init.dyn_hat = std::sqrt(cfg.dyn_eps);
+        double *hist = nullptr;
+        const int hlen = cfg.hist_host ? cfg.hist_len : 0;
+        if (hlen > 0) {
+            e = ws.alloc(sizeof(double) * hlen, (void **)&hist);
+            if (e) return e;
+            init.hist = hist;
+            init.hist_len = hlen;
+        }
         if (cfg.p_init) {
             // continue a previous recurrence: its gradient vector enters the
             // first restart (re-projected, with beta = |r_hi|^2 / rr_prev_init)
@@ -389,7 +400,14 @@ struct CGRun {
         }
         int herr = 0;
         cudaMemcpyAsync(&herr, cur_err(c), sizeof herr, cudaMemcpyDeviceToHost, s);
+        std::vector<double> hv;
+        if (hlen > 0) {
+            // entries 0..k (|r|^2 per iteration, the true residual at reliable updates)
+            hv.resize(std::min(hlen, st_h->k + 1));
+            cudaMemcpyAsync(hv.data(), hist, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, s);
+        }
         cudaStreamSynchronize(s);
+        for (size_t i = 0; i < hv.size(); i++) cfg.hist_host[i] = std::sqrt(hv[i] / bb);
         info->iters = st_h->k;
         info->matvecs += st_h->k;
         info->matvecs_hi += mv_hi;
@@ -418,7 +436,25 @@ hisq_status validate_params(hisq_ctx *c, const hisq_solver_params *p)
     if (!std::isfinite(p->mass) || !(p->tol > 0.0) || p->maxiter < 0 || !(p->delta >= 0.0 && p->delta < 1.0))
         return fail(c, HISQ_EINVAL, "bad solver parameters (mass, tol > 0, maxiter >= 0, 0 <= delta < 1)");
     if (p->nbuf < 1 || p->nbuf > kMaxBuf) return fail(c, HISQ_EINVAL, "nbuf must be in 1..%d", kMaxBuf);
+    if (p->ru_trigger < 0 || p->ru_trigger > 1) return fail(c, HISQ_EINVAL, "ru_trigger must be 0 or 1");
+    if (p->history_len < 0 || (p->history_len > 0 && !p->history))
+        return fail(c, HISQ_EINVAL, "history_len must be >= 0, with a history array when > 0");
     return check_prec(c, p->sloppy);
+}
+
+double sloppy_eps(const hisq_prec &p)
+{
+    double es = 0x1p-29;  // 30-bit
+    if (p.spinor == S_F64) es = 0x1p-53;
+    if (p.spinor == S_F32) es = 0x1p-24;
+    if (p.spinor == S_HALF) es = 0x1p-15;
+    if (p.spinor == S_INT20) es = 0x1p-19;
+    double eg = 0x1p-31;  // 32-bit fixed point
+    if (p.gauge == G_F64) eg = 0x1p-53;
+    if (p.gauge == G_F32) eg = 0x1p-24;
+    if (p.gauge == G_FIX16) eg = 0x1p-15;
+    const double ec = p.compute == HISQ_COMPUTE_F32 ? 0x1p-24 : 0x1p-53;
+    return std::max(es, std::max(eg, ec));
 }
 
 // Caller layout [site][6] (host or device) <-> FP64 planar device field.
@@ -477,6 +513,8 @@ CGConfig config_from(const hisq_solver_params *p, double sigma)
     cfg.pr = p->pr_beta;
     cfg.reproject = p->reproject;
     cfg.use_graph = p->use_graph;
+    cfg.dyn = p->ru_trigger;
+    cfg.dyn_eps = p->ru_trigger ? sloppy_eps(p->sloppy) : 0.0;
     return cfg;
 }
 
@@ -513,6 +551,9 @@ void hisq_default_params(hisq_solver_params *p)
     p->rhs_tile = 0;
     p->rhs_kernel = 0;
     p->stream = nullptr;
+    p->history = nullptr;
+    p->history_len = 0;
+    p->ru_trigger = 0;
 }
 
 hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params *p, const double *b, double *x,
@@ -548,9 +589,12 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
     if (e) return e;
     hisq_status st;
     if (nr == 1) {
-        const CGConfig cfg = config_from(p, 0.0);
+        CGConfig cfg = config_from(p, 0.0);
+        cfg.hist_host = p->history;
+        cfg.hist_len = p->history_len;
         st = run_cg(c, g, cfg, b64, x64, !p->use_init_guess, info, s);
     } else {
+        if (p->history_len > 0) return fail(c, HISQ_EINVAL, "a residual history is kept for nrhs = 1 only");
         BCGConfig bc;
         bc.nrhs = nr;
         for (int t = 0; t < nr; t++) {
@@ -566,6 +610,8 @@ hisq_status hisq_cg(hisq_ctx *c, const hisq_gauge *gc, const hisq_solver_params 
         bc.tile = p->rhs_tile;
         bc.kernel = p->rhs_kernel;
         bc.delta = p->delta;
+        bc.dyn = p->ru_trigger;
+        bc.dyn_eps = p->ru_trigger ? sloppy_eps(p->sloppy) : 0.0;
         std::vector<hisq_solve_info> infos(nr);
         st = run_bcg(c, g, bc, b64, x64, !p->use_init_guess, infos.data(), s);
         for (int t = 0; t < nr; t++) {

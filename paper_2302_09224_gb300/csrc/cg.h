@@ -33,7 +33,18 @@ struct CGConfig {
     const char *p_init = nullptr;
     int p_init_fmt = 0;
     double rr_prev_init = 0.0;
+    // error-estimate reliable-update trigger (dyn = 1) with the sloppy precision dyn_eps
+    int dyn = 0;
+    double dyn_eps = 0.0;
+    // residual history: host array of hist_len entries, |r_k|/|b| per iteration
+    double *hist_host = nullptr;
+    int hist_len = 0;
 };
+
+// Relative precision of the sloppy operator: the largest unit roundoff of the
+// triplet's gauge format, spinor format and compute precision (the precision
+// the error-estimate trigger accumulates).
+double sloppy_eps(const hisq_prec &p);
 
 // field conversion between any two storage formats (ms.cu)
 void launch_convert(int si, int so, int n, const char *in, char *out, int *err, cudaStream_t s);

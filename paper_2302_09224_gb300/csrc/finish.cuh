@@ -122,6 +122,7 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
             return;
         }
         st->pAp = pAp;
+        st->apap = sums[1];
         st->alpha = alpha;
         st->alpha_ring[slot] = alpha;
     } else if (fin == FIN_CG_BETA) {
@@ -138,10 +139,24 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
             stop_iterating(st, REASON_BREAKDOWN);
             return;
         }
+        if (st->hist != nullptr && st->k < st->hist_len) st->hist[st->k] = rr_new;
         if (rr_new > st->rr_max) st->rr_max = rr_new;
+        bool update;
+        if (st->dyn) {
+            // error estimate (the Sec. 3 footnote's dynamic choice, after van der
+            // Vorst and Ye's residual replacement): the drift of the iterated
+            // from the true residual grows by the rounding of this update; act
+            // when it crosses sqrt(eps) |r|
+            const double rn = sqrt(rr_new), ro = sqrt(st->rr_prev);
+            const double dn = st->dyn_d + st->dyn_eps * (rn + fabs(st->alpha) * sqrt(st->apap));
+            update = st->dyn_d <= st->dyn_hat * ro && dn > st->dyn_hat * rn && dn > 1.1 * st->dyn_d_init;
+            st->dyn_d = dn;
+        } else {
+            update = rr_new < st->delta2 * st->rr_max;  // |r| < delta max|r| (Sec. 3 footnote)
+        }
         if (rr_new <= st->stop2)
             stop_iterating(st, REASON_CONVERGED);
-        else if (rr_new < st->delta2 * st->rr_max)  // |r| < delta max|r| (Sec. 3 footnote)
+        else if (update)
             stop_iterating(st, REASON_RELIABLE);
     } else if (fin == FIN_CG_TRUE) {
         // sums = {|r_hi|^2, Re<r_hi, p>, Im<r_hi, p>}.  Re-projection (Sec. 3.1
@@ -163,6 +178,8 @@ __device__ __forceinline__ void run_finisher(int fin, const double *sums, void *
         st->coef_im = -beta * ci;
         st->rr = rr;
         st->rr_max = rr;
+        st->dyn_d = st->dyn_d_init = st->dyn_eps * sqrt(rr);
+        if (st->hist != nullptr && st->k < st->hist_len) st->hist[st->k] = rr;  // the recomputed residual
         st->reason = REASON_NONE;
         st->active = 1;
         if (!isfinite(rr)) stop_iterating(st, REASON_BREAKDOWN);

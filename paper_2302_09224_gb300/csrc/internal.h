@@ -109,12 +109,18 @@ struct CGState {
     double proj_re, proj_im;  // projection coefficient of p onto r_hi
     double coef_re, coef_im;  // p <- coef * r_hi + beta * p at a reliable update
     double diag;        // 4 m^2 + sigma of this system (read by the batched stencil)
+    double apap;        // |A p|^2 of the last operator application
+    // error-estimate reliable-update trigger (dyn = 1): drift estimate d and
+    // its value after the last update, the sloppy precision eps and sqrt(eps)
+    double dyn_d, dyn_d_init, dyn_eps, dyn_hat;
+    double *hist;       // device [hist_len]: |r_k|^2 per iteration (null: not kept)
+    int hist_len;
     int active;         // kernels of an iteration run only while 1
     int reason;         // why the iteration stopped (REASON_*)
     int k;              // iterations done
     int pr;             // Polak-Ribiere beta
     int reproject;
-    int pad;
+    int dyn;            // 1: error-estimate trigger instead of delta
 };
 
 enum { REASON_NONE = 0, REASON_RELIABLE = 1, REASON_CONVERGED = 2, REASON_BREAKDOWN = 3 };
@@ -212,6 +218,7 @@ struct DslashMArgs {
     int xpay;
     int nrhs;
     int t0;                 // first right-hand side of the tile (set by the launcher)
+    unsigned tile_mask;     // bit k: launch tile k (0: every tile)
     const int *active_any;  // skip when *active_any == 0 (null: always run)
     int *err;
     RedBuf red;

@@ -62,7 +62,8 @@ class hisq_solver_params(ctypes.Structure):
                 ("nbuf", ctypes.c_int32), ("use_init_guess", ctypes.c_int32), ("on_device", ctypes.c_int32),
                 ("pr_beta", ctypes.c_int32), ("reproject", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
-                ("rhs_kernel", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("rhs_kernel", ctypes.c_int32), ("stream", ctypes.c_void_p), ("history", ctypes.c_void_p),
+                ("history_len", ctypes.c_int32), ("ru_trigger", ctypes.c_int32)]
 
 
 class hisq_solve_info(ctypes.Structure):
@@ -132,6 +133,7 @@ _SIGS = {
     "hisq_launch_count": (_I64, [_P]),
     "hisq_stencil_config": (_I, [_I]),
     "hisq_stencil_config_reduce": (_I, [_I]),
+    "hisq_programmatic_launch": (_I, [_I]),
     "hisq_mee_fused": (_I, [_I]),
     "hisq_mee_fused_shape": (None, [_I, _I]),
     "hisq_mee_fused_wait_test": (None, [ctypes.c_uint, _I]),
@@ -142,6 +144,8 @@ _SIGS = {
                                 ctypes.POINTER(hisq_solve_info)]),
     "hisq_bicgstabl": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P,
                             ctypes.POINTER(hisq_solve_info)]),
+    "hisq_solve_full": (_I, [_P, _P, ctypes.POINTER(hisq_solver_params), _P, _P,
+                             ctypes.POINTER(hisq_solve_info)]),
     "hisq_submit": (_I, [_P, ctypes.POINTER(hisq_request), ctypes.POINTER(ctypes.c_uint64)]),
     "hisq_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(hisq_solve_info)]),
     "hisq_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(hisq_solve_info)]),
@@ -333,6 +337,10 @@ def hisq_mee_fused_wait_test(polls: int, unreachable: bool):
     lib().hisq_mee_fused_wait_test(int(polls) & 0xFFFFFFFF, int(bool(unreachable)))
 
 
+def hisq_programmatic_launch(mode: int) -> int:
+    return int(lib().hisq_programmatic_launch(int(mode)))
+
+
 def hisq_stencil_config_reduce(cfg: int) -> int:
     return int(lib().hisq_stencil_config_reduce(int(cfg)))
 
@@ -358,6 +366,21 @@ def hisq_cg(ctx, g, params: hisq_solver_params, b, x) -> tuple[int, hisq_solve_i
     if st not in (HISQ_OK, HISQ_ENOTCONV):
         _check(ctx, st)
     return st, info
+
+
+def hisq_solve_full(ctx, g, params: hisq_solver_params, b, x) -> tuple[int, hisq_solve_info]:
+    """Full-lattice (2m + D) x = b by even/odd reduction; returns (status, info) like hisq_cg."""
+    info = hisq_solve_info()
+    st = lib().hisq_solve_full(ctx, g, ctypes.byref(params), _ptr(b), _ptr(x), ctypes.byref(info))
+    if st not in (HISQ_OK, HISQ_ENOTCONV):
+        _check(ctx, st)
+    return st, info
+
+
+def set_history(params: hisq_solver_params, buf):
+    """Point params.history at a float64 numpy array (kept alive by the caller)."""
+    params.history = buf.ctypes.data
+    params.history_len = int(buf.size)
 
 
 def hisq_multishift_cg(ctx, g, params: hisq_solver_params, sigma, tol, b, xs) -> tuple[int, hisq_solve_info]:
