@@ -14,6 +14,7 @@
 #include "blas.h"
 #include "codecs.cuh"
 #include "finish.cuh"
+#include "launch.cuh"
 #include "reduce.cuh"
 
 namespace hisq {
@@ -38,6 +39,8 @@ constexpr int kPSites = 2;
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     constexpr int U = kRSites, C = Spinor<SF>::chunks;
     red_t<real> v[2] = {0, 0};
@@ -84,6 +87,8 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     constexpr int U = kPSites, C = Spinor<SF>::chunks;
     const int i0 = blockIdx.x * blockDim.x * U + threadIdx.x;
@@ -117,6 +122,8 @@ __global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -155,6 +162,8 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) true_residual_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
     if (i < a.n) {
@@ -192,6 +201,8 @@ __global__ void __launch_bounds__(kBlock) true_residual_kernel(BlasArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) p_reliable_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0)
         for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
@@ -211,6 +222,8 @@ __global__ void __launch_bounds__(kBlock) p_reliable_kernel(BlasArgs a)
 
 __global__ void __launch_bounds__(kBlock) norm2_kernel(BlasArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v[1] = {0.0};
     if (i < a.n) {
@@ -231,13 +244,13 @@ int nblk(int n) { return (n + kBlock - 1) / kBlock; }
     do {                                                                                    \
         const bool f64_ = (CF_) == HISQ_COMPUTE_F64;                                        \
         switch (SF_) {                                                                      \
-        case S_F64: KERNEL<S_F64, double><<<__VA_ARGS__>>>(a); break;                       \
-        case S_F32: KERNEL<S_F32, float><<<__VA_ARGS__>>>(a); break;                        \
-        case S_HALF: KERNEL<S_HALF, float><<<__VA_ARGS__>>>(a); break;                      \
-        case S_INT20: KERNEL<S_INT20, float><<<__VA_ARGS__>>>(a); break;                    \
+        case S_F64: launch_chained(KERNEL<S_F64, double>, __VA_ARGS__, a); break;           \
+        case S_F32: launch_chained(KERNEL<S_F32, float>, __VA_ARGS__, a); break;            \
+        case S_HALF: launch_chained(KERNEL<S_HALF, float>, __VA_ARGS__, a); break;          \
+        case S_INT20: launch_chained(KERNEL<S_INT20, float>, __VA_ARGS__, a); break;        \
         case S_INT30:                                                                       \
-            if (f64_) KERNEL<S_INT30, double><<<__VA_ARGS__>>>(a);                          \
-            else KERNEL<S_INT30, float><<<__VA_ARGS__>>>(a);                                \
+            if (f64_) launch_chained(KERNEL<S_INT30, double>, __VA_ARGS__, a);              \
+            else launch_chained(KERNEL<S_INT30, float>, __VA_ARGS__, a);                    \
             break;                                                                          \
         }                                                                                   \
     } while (0)
@@ -249,7 +262,7 @@ void r_update_t(const BlasArgs &a, cudaStream_t s)
 {
     static const int wave = wave_blocks(r_update_kernel<SF, real>, kBlock);
     const int need = (a.n + kBlock * kRSites - 1) / (kBlock * kRSites);
-    r_update_kernel<SF, real><<<need < wave ? need : wave, kBlock, 0, s>>>(a);
+    launch_chained(r_update_kernel<SF, real>, dim3(need < wave ? need : wave), dim3(kBlock), s, a);
 }
 
 }  // namespace
@@ -274,27 +287,30 @@ void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
     const int nb = (a.n + kBlock * kPSites - 1) / (kBlock * kPSites);
     if (sf == S_INT30 && cf == HISQ_COMPUTE_F64) {  // FP64-class compute in FP32 pairs
-        p_update_kernel<S_INT30, ff><<<nb, kBlock, 0, s>>>(a);
+        launch_chained(p_update_kernel<S_INT30, ff>, dim3(nb), dim3(kBlock), s, a);
         return;
     }
-    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, nb, kBlock, 0, s);
+    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, dim3(nb), dim3(kBlock), s);
 }
 
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, x_flush_kernel, nblk(a.n), kBlock, 0, s);
+    HISQ_SF_DISPATCH(sf, cf, x_flush_kernel, dim3(nblk(a.n)), dim3(kBlock), s);
 }
 
 void launch_true_residual(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, true_residual_kernel, nblk(a.n), kBlock, 0, s);
+    HISQ_SF_DISPATCH(sf, cf, true_residual_kernel, dim3(nblk(a.n)), dim3(kBlock), s);
 }
 
 void launch_p_reliable(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    HISQ_SF_DISPATCH(sf, cf, p_reliable_kernel, nblk(a.n), kBlock, 0, s);
+    HISQ_SF_DISPATCH(sf, cf, p_reliable_kernel, dim3(nblk(a.n)), dim3(kBlock), s);
 }
 
-void launch_norm2(const BlasArgs &a, cudaStream_t s) { norm2_kernel<<<nblk(a.n), kBlock, 0, s>>>(a); }
+void launch_norm2(const BlasArgs &a, cudaStream_t s)
+{
+    launch_chained(norm2_kernel, dim3(nblk(a.n)), dim3(kBlock), s, a);
+}
 
 }  // namespace hisq

@@ -20,6 +20,7 @@
 #include "codecs.cuh"
 #include "finish.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "reduce.cuh"
 
 namespace hisq {
@@ -327,6 +328,8 @@ template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)
 {
+    pdl_wait();  // the input, xpay and state fields come from the previous kernel
+    pdl_launch_dependents();
     if (a.active != nullptr && *(volatile const int *)a.active == 0) return;  // uniform over the grid
     const int vh = a.g.vh;
     const size_t pstride = (size_t)8 * vh * 16;
@@ -351,6 +354,8 @@ template <typename real>
 __global__ void __launch_bounds__(1024) stencil_finish_kernel(RedBuf red, unsigned nblocks, int fin, void *st,
                                                                int slot, const int *active)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (active != nullptr && *(volatile const int *)active == 0) return;
     __shared__ double tot[2];
     sum_partials<2, red_t<real>>(red, nblocks, tot);
@@ -366,8 +371,10 @@ void launch_cfg(const DslashArgs &a, cudaStream_t s)
 {
     constexpr int B = stencil_block(CFG);
     const int nb = (a.g.vh + B - 1) / B;
-    dslash_kernel<GF, SF, real, LREC, RED, CFG><<<nb, B, 0, s>>>(a);
-    if constexpr (RED) stencil_finish_kernel<real><<<1, 1024, 0, s>>>(a.red, (unsigned)nb, a.fin, a.st, a.slot, a.active);
+    launch_chained(dslash_kernel<GF, SF, real, LREC, RED, CFG>, dim3(nb), dim3(B), s, a);
+    if constexpr (RED)
+        launch_chained(stencil_finish_kernel<real>, dim3(1), dim3(1024), s, a.red, (unsigned)nb, a.fin, a.st, a.slot,
+                       a.active);
 }
 
 template <int GF, int SF, typename real, int LREC, bool RED>

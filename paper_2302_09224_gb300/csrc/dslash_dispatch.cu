@@ -233,6 +233,16 @@ extern "C" void hisq_mee_fused_shape(int lag, int blocks_per_sm)
     if (blocks_per_sm >= 0) hisq::fused_bps.store(blocks_per_sm);
 }
 
+namespace hisq {
+std::atomic<int> pdl_mode{1};
+}
+
+extern "C" int hisq_programmatic_launch(int mode)
+{
+    if (mode < 0 || mode > 1) return -2;
+    return hisq::pdl_mode.exchange(mode);
+}
+
 extern "C" int hisq_stencil_config(int cfg)
 {
     if (cfg < -1 || cfg >= hisq::kNumStencilConfigs) return -2;

@@ -541,6 +541,7 @@ bool launch_mrhs_t(int long_recon, bool reduce, int T, int variant, const Dslash
     static_assert(std::is_same<real, float>::value, "the batched stencil computes in FP32");
     if (reduce && !red_fits(args.g.vh, kMrhsBlock, 2 * T)) return false;
     for (int t0 = 0; t0 < args.nrhs; t0 += T) {
+        if (args.tile_mask != 0u && !((args.tile_mask >> (t0 / T)) & 1u)) continue;  // no system of it iterates
         DslashMArgs a = args;
         a.t0 = t0;
         bool ok;

@@ -179,3 +179,22 @@ def test_maxiter_and_invalid(ctx, orc):
         solve(ctx, dims, fat, lng, m, b, nbuf=0)
     st, info, x = solve(ctx, dims, fat, lng, m, np.zeros_like(b))
     assert st == hisq.HISQ_OK and not x.any()
+
+
+def test_programmatic_launch_same_bits(ctx):
+    """Kernels launched with programmatic dependent launch (each waiting for its
+    predecessor's results before touching them) give the same solution, bit
+    for bit, as kernels launched one after another, in graphs and directly."""
+    dims, m = (8, 8, 8, 16), 0.02
+    fat, lng = synth.gauge_pair(dims, seed=2)
+    b = synth.spinor(dims, 1002).numpy()
+    prev = hisq.hisq_programmatic_launch(0)
+    try:
+        ref = [solve(ctx, dims, fat, lng, m, b, name, use_graph=g)[2] for name in ("int20", "int30") for g in (0, 1)]
+        hisq.hisq_programmatic_launch(1)
+        got = [solve(ctx, dims, fat, lng, m, b, name, use_graph=g)[2] for name in ("int20", "int30") for g in (0, 1)]
+    finally:
+        hisq.hisq_programmatic_launch(prev)
+    for a, r in zip(got, ref):
+        np.testing.assert_array_equal(a, r)
+    assert hisq.hisq_programmatic_launch(3) == -2
