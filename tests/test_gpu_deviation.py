@@ -1,0 +1,69 @@
+"""Fig. 2 analogue (Sec. 5.2): the distribution of the per-component absolute
+deviation of the GPU stencil from the FP64 CPU oracle, per precision triplet,
+on a 16^4 lattice with a Gaussian source.
+
+The paper plots the deviation of the HISQ stencil for each storage triplet
+against a CPU FP64 reference and reports 30-bit storage with FP64 compute
+about two orders of magnitude below pure FP32, and the 20-bit fermion below
+the 16-bit one (the gauge field, 16-bit in both, then limits it).  Here the
+50th, 90th and 99th percentiles and the maximum of |y_gpu - y_oracle| over
+every real component must show those orderings, and the 30-bit / FP32-compute
+triplet must sit with pure FP32 (its compute precision limits it).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_09224_gb300 import hisq, synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (16, 16, 16, 16)
+NAMES = ("f32", "half", "int20", "int30", "int30f32")
+PCT = (50, 90, 99, 100)
+
+
+@pytest.fixture(scope="module")
+def deviations(orc):
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(DIMS, seed=0)
+    x = synth.spinor(DIMS, 1000)
+    exact = orc.dslash(DIMS, fat.numpy(), lng.numpy(), 0, x.numpy())
+    g = hisq.hisq_load_gauge(ctx, DIMS, fat.cuda(), lng.cuda())
+    out = {}
+    try:
+        xd = x.cuda()
+        for name in NAMES:
+            y = torch.empty_like(xd)
+            hisq.hisq_dslash(ctx, g, hisq.prec(name, 12), 0, 0.0, None, xd, y, True)
+            torch.cuda.synchronize()
+            dev = np.abs(y.cpu().numpy() - exact).reshape(-1)
+            out[name] = np.percentile(dev, PCT)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+        hisq.hisq_destroy(ctx)
+    print("\nper-component |y_gpu - y_oracle| percentiles", PCT)
+    for name in NAMES:
+        print(f"  {name:9s}", "  ".join(f"{v:.3e}" for v in out[name]))
+    return out
+
+
+def test_thirty_bit_fp64_two_orders_below_fp32(deviations):
+    for k in range(len(PCT)):
+        assert deviations["int30"][k] * 30 < deviations["f32"][k], (PCT[k], deviations["int30"][k])
+
+
+def test_twenty_bit_below_sixteen_bit(deviations):
+    for k in range(len(PCT)):
+        assert deviations["int20"][k] < deviations["half"][k], PCT[k]
+
+
+def test_thirty_bit_fp32_compute_sits_with_fp32(deviations):
+    for k in range(len(PCT) - 1):  # the maximum is a single sample
+        assert 0.3 < deviations["int30f32"][k] / deviations["f32"][k] < 3.0, PCT[k]
+
+
+def test_reduced_formats_ordered_by_precision(deviations):
+    # 16-bit fixed-point links limit both 16-bit-gauge triplets well above FP32
+    for k in range(len(PCT)):
+        assert deviations["f32"][k] < deviations["int20"][k] < deviations["half"][k]
