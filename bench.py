@@ -178,6 +178,17 @@ def sum_over_ranks(pg, v, device):
     return float(t.item())
 
 
+def config_dict(args, world=1):
+    """The workload's description, identical in both arms' lines."""
+    return {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL, "delta": DELTA,
+            "sloppy": "fix16/int20/f32 r12", "l2": "no flush: every step streams >1 GB per iteration "
+            "(links 0.5 GB per stencil pass), far above the 129 MB L2",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "m_ee": "one fused pass" if getattr(args, "fused", False) else "two stencil passes",
+            "kernel_chain": "sequential launches" if getattr(args, "no_pdl", False)
+            else "programmatic dependent launch"}
+
+
 def oracle_sample(fat_h, lng_h, b_h, iters):
     """Time `iters` FP64 CG iterations of the oracle on the host cores."""
     import oracle
@@ -200,24 +211,26 @@ def run_reference(args):
     b = synth.spinor(DIMS, synth.rhs_seed(0))
     fat_h, lng_h, b_h = fat.numpy(), lng.numpy(), b.numpy()
     sample_iters = args.ref_iters
-    times = []
+    # one step = a bounded sample of the workload: `sample_iters` iterations of the oracle's CG on the same
+    # system, timed whole (the initial and final residual operator applications included); its value counts
+    # the headline solve's algorithmic bytes per iteration for each iteration done
+    bytes_per_iter = args.solve_bytes / args.solve_iters
+    steps_s, iters_done, cores = [], [], 1
     for s in range(args.warmup + args.steps):
         dt, it, cores = oracle_sample(fat_h, lng_h, b_h, sample_iters)
         if s >= args.warmup:
-            times.append(dt / (it + 2))  # it iterations + the initial and final residual operator applications
-    per_iter = statistics.median(times)
-    # the GPU solve's iteration count and bytes are the unit of one step
-    gpu_iters = args.solve_iters
-    bytes_per_step = args.solve_bytes
-    step_s = per_iter * gpu_iters
-    value = bytes_per_step / step_s / 1e9
+            steps_s.append(dt)
+            iters_done.append(it)
+    total_s = sum(steps_s)
+    value = bytes_per_iter * sum(iters_done) / total_s / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / len(steps_s) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{sample_iters} FP64 CG iterations of the C oracle on the full 32^3x64 "
-                                       f"lattice per step, extrapolated to the GPU solve's {gpu_iters} iterations"},
+                             "sample": f"each step: {sample_iters} FP64 CG iterations of the C oracle (OpenMP) on "
+                                       f"the full 32^3x64 system, {bytes_per_iter / 1e9:.3f} GB of the GPU solve's "
+                                       f"algorithmic traffic per iteration"},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -235,6 +248,8 @@ def run_ours(args):
     force_shapes(args)
     if args.fused:
         hisq.hisq_mee_fused(1)
+    if args.no_pdl:
+        hisq.hisq_programmatic_launch(0)
     ctx = hisq.hisq_create(local)
     fat, lng = synth.gauge_pair(DIMS, seed=0, device=dev)
     g = hisq.hisq_load_gauge(ctx, DIMS, fat, lng)
@@ -393,6 +408,39 @@ def run_ours(args):
                                             "reliable_updates": infb.reliable_updates,
                                             "true_residual": infb.true_residual, "status": hisq.STATUS_NAMES[stb]}
 
+    # the FP64 baseline's stencil alone: a short profiled FP64 solve (its passes timed by events)
+    hisq.hisq_profile_reset(ctx)
+    hisq.hisq_profile_select(ctx, 1 << hisq.HISQ_PROF_STENCIL)
+    hisq.hisq_profile_enable(ctx, True)
+    p64s = params("f64", 0.0)
+    p64s.maxiter = 64
+    x64.zero_()
+    with torch.cuda.stream(stream):
+        hisq.hisq_cg(ctx, g, p64s, b, x64)
+    s64 = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+    hisq.hisq_profile_enable(ctx, False)
+    hisq.hisq_profile_select(ctx, 0xFFFFFFFF)
+    vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+    fp64_stencil = {"us_per_pass": 1e3 * s64.ms / max(s64.launches, 1),
+                    "gbs": s64.bytes / max(s64.ms, 1e-9) / 1e6,
+                    "tflops": FLOP_PER_SITE * vh * s64.launches / max(s64.ms, 1e-9) / 1e9,
+                    "launches": s64.launches, "note": "FP64/FP64/FP64 triplet, 18-real links, in a 64-iteration "
+                                                      "profiled solve"}
+
+    # the task's other configurations, at sizes that keep the default run within a few minutes
+    extras = {}
+    if not args.no_extras:
+        extras["multishift_12_shifts_32x32x32x64"] = multishift_results(ctx, g, b, args.ms_pairs.split(","))
+        extras["batched_16rhs_32x32x32x64"] = batched_results(ctx, g, DIMS, MASS, 16, ["int20"])
+        reqs = synth.poisson_requests(args.serve_requests, rate_hz=200.0, seed=1, volumes=SERVE_VOLUMES)
+        gauges, mine = load_volumes(ctx, reqs, {DIMS: g})
+        extras["serving"] = serve_results(ctx, gauges, reqs, True)
+        extras["serving"]["workload"] = (f"{args.serve_requests} Poisson requests at 200/s (seed 1), volumes "
+                                         "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts), against the same "
+                                         "requests solved one after another")
+        for gm in mine:
+            hisq.hisq_free_gauge(ctx, gm)
+
     peak, peak_kind = measured_peak()
     achieved = stencil.bytes / (stencil.ms / 1e3) / 1e9 if stencil.ms > 0 else 0.0
     per_launch_bytes = stencil.bytes / max(1, stencil.launches)
@@ -401,11 +449,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "tol": TOL, "delta": DELTA,
-                   "sloppy": "fix16/int20/f32 r12", "l2": "no flush: every step streams >1 GB per iteration "
-                   "(links 0.5 GB per stencil pass), far above the 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "m_ee": "one fused pass" if args.fused else "two stencil passes"},
+        "config": config_dict(args, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": ("mee_fused_kernel<FIX16, INT20, float, r12> (M_ee in one pass, links once)"
@@ -427,6 +471,8 @@ def run_ours(args):
         "stencil_gflops": FLOP_PER_SITE * (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2) * stencil.launches
                           / (stencil.ms / 1e3) / 1e9 if stencil.ms > 0 else 0.0,
         "formats_time_to_solution": formats,
+        "fp64_stencil": fp64_stencil,
+        "configs": extras,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(bh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes), "s_per_step": e2e_s},
         "gpu_launches": int(sum_over_ranks(pg, launches, dev)),
@@ -554,34 +600,31 @@ def run_batched_solve(args):
     return 0
 
 
-def run_multishift(args):
-    """12 shifts log-spaced in [1e-4, 1] on 32^3x64, base m = 0.005, per-shift targets 1e-10..1e-7: the
-    multi-shift stage (all shifts in one fused update kernel per iteration) plus refinement, per format."""
+MS_SHIFTS, MS_MASS = 12, 0.005
+
+
+def multishift_results(ctx, g, b, pairs):
+    """Config 3: 12 shifts log-spaced in [1e-4, 1] on g's lattice, base m = 0.005, per-shift targets
+    1e-10..1e-7; the multi-shift stage (all shifts in one fused update kernel per iteration) plus refinement,
+    per (stage / refinement) format pair.  Each pair runs once untimed (gauge copy, tuning), then timed."""
     import torch
 
     from paper_2302_09224_gb300 import hisq, synth
 
-    dims, m = (32, 32, 32, 64), 0.005
-    sig = synth.shifts_logspaced(12, 1e-4, 1.0)
-    tols = synth.shift_tolerances(12, 1e-10, 1e-7)
-    ctx = hisq.hisq_create(0)
-    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
-    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
-    b = synth.spinor(dims, synth.rhs_seed(0), device="cuda")
+    sig = synth.shifts_logspaced(MS_SHIFTS, 1e-4, 1.0)
+    tols = synth.shift_tolerances(MS_SHIFTS, 1e-10, 1e-7)
     res = {}
-    # (multi-shift stage, refinement) pairs: the paper's Table 3 pairs a higher-precision multi-shift
-    # stage with a lower-precision refinement (single/half and 30-bit/20-bit), plus 20-bit for both;
-    # the FP64-class 30-bit triplet runs with 18-real long links (see the headline formats)
-    for pair in args.ms_pairs.split(","):
+    # Table 3 pairs a higher-precision multi-shift stage with a lower-precision refinement (single/half
+    # and 30-bit/20-bit), plus 20-bit for both; the FP64-class 30-bit triplet runs with 18-real long links
+    for pair in pairs:
         ms_name, ref_name = pair.split("/")
         p = hisq.hisq_default_params()
-        p.mass, p.tol, p.delta, p.on_device = m, min(tols), DELTA, 1
+        p.mass, p.tol, p.delta, p.on_device = MS_MASS, min(tols), DELTA, 1
         p.sloppy = hisq.prec(ms_name, 18 if ms_name in ("f64", "int30") else 12)
         p.refine = hisq.prec(ref_name, 18 if ref_name in ("f64", "int30") else 12)
         p.maxiter = 100000
-        name = pair
         xs = [torch.zeros_like(b) for _ in sig]
-        hisq.hisq_multishift_cg(ctx, g, p, sig, tols, b, xs)  # warm-up: gauge copy, tuning
+        hisq.hisq_multishift_cg(ctx, g, p, sig, tols, b, xs)
         for x in xs:
             x.zero_()
         torch.cuda.synchronize()
@@ -589,85 +632,75 @@ def run_multishift(args):
         st, info = hisq.hisq_multishift_cg(ctx, g, p, sig, tols, b, xs)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        tr = list(info.shift_resid)[:12]  # FP64 true residuals computed on the GPU after refinement
-        res[name] = {"s": dt, "status": hisq.STATUS_NAMES[st], "iters_multishift": info.iters,
-                     "shift_iters": list(info.shift_iters)[:12], "refine_iters": list(info.refine_iters)[:12],
-                     "residual_after_multishift": list(info.shift_resid_ms)[:12], "true_residual": tr,
+        tr = list(info.shift_resid)[:MS_SHIFTS]  # FP64 true residuals computed on the GPU after refinement
+        res[pair] = {"s": dt, "status": hisq.STATUS_NAMES[st], "iters_multishift": info.iters,
+                     "refine_iters_total": int(sum(list(info.refine_iters)[:MS_SHIFTS])),
+                     "shift_iters": list(info.shift_iters)[:MS_SHIFTS],
+                     "refine_iters": list(info.refine_iters)[:MS_SHIFTS],
+                     "residual_after_multishift": list(info.shift_resid_ms)[:MS_SHIFTS], "true_residual": tr,
                      "targets_met": all(r <= t for r, t in zip(tr, tols))}
-    print(json.dumps({"workload": "multi-shift CG, 12 shifts log-spaced 1e-4..1, 32^3x64, m=0.005, "
-                      "targets 1e-10..1e-7; results per (multi-shift stage / refinement) format pair",
-                      "results": res}))
-    hisq.hisq_free_gauge(ctx, g)
-    hisq.hisq_destroy(ctx)
-    return 0
+    return res
 
 
-def run_batched(args):
-    """16 right-hand sides on 48^3x96 (m = 0.002): one batched solve (autotuned RHS tile) against the same
-    16 systems solved one after another with the single-RHS solver."""
+def batched_results(ctx, g, dims, m, nr, names, profile_iters=200):
+    """Config 4's batched CG: nr Gaussian right-hand sides solved together (autotuned tile; each stencil
+    launch loads every link once per tile) against the same systems solved one after another; the batched
+    stencil's time per right-hand side and pass comes from a short profiled batched solve."""
     import torch
 
     from paper_2302_09224_gb300 import hisq, synth
 
-    dims, m, nr = (48, 48, 48, 96), 0.002, 16
-    ctx = hisq.hisq_create(0)
-    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
-    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
-    del fat, lng
-    torch.cuda.empty_cache()
     b = torch.stack([synth.spinor(dims, synth.rhs_seed(k), device="cuda") for k in range(nr)]).contiguous()
     res = {}
-    for name in args.formats.split(","):
-        p = hisq.hisq_default_params()
-        p.mass, p.tol, p.delta, p.on_device = m, TOL, DELTA, 1
-        p.sloppy = hisq.prec(name, 12)
-        p.maxiter = 100000
-        p.nrhs = nr
+    for name in names:
+        def params(n, maxiter=100000):
+            p = hisq.hisq_default_params()
+            p.mass, p.tol, p.delta, p.on_device = m, TOL, DELTA, 1
+            p.sloppy = hisq.prec(name, 12)
+            p.maxiter = maxiter
+            p.nrhs = n
+            return p
+
         x = torch.zeros_like(b)
+        hisq.hisq_cg(ctx, g, params(nr, 16), b, x)  # untimed: gauge copy, tile and shape tuning
+        x.zero_()
+        hisq.hisq_profile_reset(ctx)
+        hisq.hisq_profile_enable(ctx, True)
+        hisq.hisq_cg(ctx, g, params(nr, profile_iters), b, x)
+        sten = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+        hisq.hisq_profile_enable(ctx, False)
+        x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, info = hisq.hisq_cg(ctx, g, p, b, x)
+        st, info = hisq.hisq_cg(ctx, g, params(nr), b, x)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
-        p1 = hisq.hisq_default_params()
-        p1.mass, p1.tol, p1.delta, p1.on_device = m, TOL, DELTA, 1
-        p1.sloppy = hisq.prec(name, 12)
-        p1.maxiter = 100000
         x1 = torch.zeros_like(b[0])
         iters1 = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(nr):
             x1.zero_()
-            _, i1 = hisq.hisq_cg(ctx, g, p1, b[k], x1)
+            _, i1 = hisq.hisq_cg(ctx, g, params(1), b[k], x1)
             iters1.append(i1.iters)
         torch.cuda.synchronize()
         t_single = time.perf_counter() - t0
         res[name] = {"batched_s": t_batch, "sequential_s": t_single, "speedup": t_single / t_batch,
-                     "status": hisq.STATUS_NAMES[st], "iters_max_batched": info.iters,
-                     "iters_single": iters1, "true_residual_max": info.true_residual}
-    print(json.dumps({"workload": "batched CG, 16 Gaussian RHS on 48^3x96, m=0.002, tol 1e-10, autotuned tile",
-                      "results": res}))
-    hisq.hisq_free_gauge(ctx, g)
-    hisq.hisq_destroy(ctx)
-    return 0
+                     "status": hisq.STATUS_NAMES[st], "iters_max_batched": info.iters, "iters_single": iters1,
+                     "true_residual_max": info.true_residual,
+                     "stencil_us_per_rhs_pass": 1e3 * sten.ms / max(sten.launches, 1) / nr,
+                     "stencil_gbs": sten.bytes / max(sten.ms, 1e-9) / 1e6}
+    return res
 
 
-def run_serve(args):
-    """A seeded Poisson stream (200 requests/s) of CG and 8-shift multi-shift requests over four lattice
-    volumes, masses log-uniform in [1e-3, 1e-1], tolerances {1e-6, 1e-8, 1e-10}, submitted at their arrival
-    times to the library's request loop; latency percentiles and throughput."""
+def serve_results(ctx, gauges, reqs, sequential):
+    """Config 5: the seeded Poisson stream submitted at its arrival times to the library's request loop
+    (continuous batching); latency percentiles, throughput and, optionally, the same requests solved one
+    after another on one stream."""
     import torch
 
     from paper_2302_09224_gb300 import hisq, synth
 
-    reqs = synth.poisson_requests(args.requests, rate_hz=200.0, seed=1)
-    ctx = hisq.hisq_create(0)
-    gauges = {}
-    for d in sorted({r["dims"] for r in reqs}):
-        fat, lng = synth.gauge_pair(d, seed=0, device="cuda")
-        gauges[d] = hisq.hisq_load_gauge(ctx, d, fat, lng)
-        del fat, lng
     live = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -690,12 +723,10 @@ def run_serve(args):
         statuses[hisq.STATUS_NAMES[st]] = statuses.get(hisq.STATUS_NAMES[st], 0) + 1
     wall = time.perf_counter() - t0
     s = hisq.hisq_serve_stats(ctx)
-    line = {"workload": f"serving: {args.requests} Poisson requests at 200/s (seed 1), volumes "
-                        "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts)",
-            "completed": s.completed, "statuses": statuses, "latency_p50_s": s.latency_p50_s,
-            "latency_p99_s": s.latency_p99_s, "solves_per_s": s.solves_per_s, "wall_s": wall}
-    if args.serve_sequential:
-        # the same requests solved one after another on one stream, no batching or overlap
+    line = {"requests": len(reqs), "completed": s.completed, "statuses": statuses,
+            "latency_p50_s": s.latency_p50_s, "latency_p99_s": s.latency_p99_s, "solves_per_s": s.solves_per_s,
+            "wall_s": wall}
+    if sequential:
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         for r in reqs:
@@ -704,14 +735,82 @@ def run_serve(args):
             p.mass, p.tol, p.on_device = r["mass"], r["tol"], 1
             if r["multishift"]:
                 xs = [torch.zeros_like(b) for _ in r["shifts"]]
-                hisq.hisq_multishift_cg(ctx, gauges[r["dims"]], p, r["shifts"], [r["tol"]] * len(r["shifts"]), b, xs)
+                hisq.hisq_multishift_cg(ctx, gauges[r["dims"]], p, r["shifts"], [r["tol"]] * len(r["shifts"]), b,
+                                        xs)
             else:
                 hisq.hisq_cg(ctx, gauges[r["dims"]], p, b, torch.zeros_like(b))
         torch.cuda.synchronize()
         seq = time.perf_counter() - t1
         line.update({"sequential_s": seq, "throughput_vs_sequential": seq / wall})
+    return line
+
+
+SERVE_VOLUMES = ((8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64))
+
+
+def load_volumes(ctx, reqs, have=None):
+    """Resident gauge fields for the requests' volumes (reusing `have`: {dims: gauge})."""
+    from paper_2302_09224_gb300 import hisq, synth
+
+    gauges, mine = dict(have or {}), []
+    for d in sorted({r["dims"] for r in reqs}):
+        if d not in gauges:
+            fat, lng = synth.gauge_pair(d, seed=0, device="cuda")
+            gauges[d] = hisq.hisq_load_gauge(ctx, d, fat, lng)
+            mine.append(gauges[d])
+            del fat, lng
+    return gauges, mine
+
+
+def run_multishift(args):
+    """Config 3 alone, every pair of --ms-pairs (the default run reports it too)."""
+    from paper_2302_09224_gb300 import hisq, synth
+
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(DIMS, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, DIMS, fat, lng)
+    b = synth.spinor(DIMS, synth.rhs_seed(0), device="cuda")
+    res = multishift_results(ctx, g, b, args.ms_pairs.split(","))
+    print(json.dumps({"workload": "multi-shift CG, 12 shifts log-spaced 1e-4..1, 32^3x64, m=0.005, "
+                      "targets 1e-10..1e-7; results per (multi-shift stage / refinement) format pair",
+                      "results": res}))
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
+def run_batched(args):
+    """Config 4: 16 right-hand sides on 48^3x96 (m = 0.002), batched against one after another."""
+    import torch
+
+    from paper_2302_09224_gb300 import hisq, synth
+
+    dims, m, nr = (48, 48, 48, 96), 0.002, 16
+    ctx = hisq.hisq_create(0)
+    fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
+    g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
+    del fat, lng
+    torch.cuda.empty_cache()
+    res = batched_results(ctx, g, dims, m, nr, args.formats.split(","))
+    print(json.dumps({"workload": "batched CG, 16 Gaussian RHS on 48^3x96, m=0.002, tol 1e-10, autotuned tile",
+                      "results": res}))
+    hisq.hisq_free_gauge(ctx, g)
+    hisq.hisq_destroy(ctx)
+    return 0
+
+
+def run_serve(args):
+    """Config 5 with --requests requests (the default run reports a shorter stream)."""
+    from paper_2302_09224_gb300 import hisq, synth
+
+    reqs = synth.poisson_requests(args.requests, rate_hz=200.0, seed=1, volumes=SERVE_VOLUMES)
+    ctx = hisq.hisq_create(0)
+    gauges, mine = load_volumes(ctx, reqs)
+    line = serve_results(ctx, gauges, reqs, args.serve_sequential)
+    line["workload"] = (f"serving: {args.requests} Poisson requests at 200/s (seed 1), volumes "
+                        "8^4/16^4/24^3x48/32^3x64, 30% multi-shift (8 shifts)")
     print(json.dumps(line))
-    for g in gauges.values():
+    for g in mine:
         hisq.hisq_free_gauge(ctx, g)
     hisq.hisq_destroy(ctx)
     return 0
@@ -727,7 +826,12 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=12, help="oracle CG iterations per CPU sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-formats", action="store_true", help="skip the other storage formats' solves")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the multi-shift, batched and serving configurations of the default line")
+    ap.add_argument("--serve-requests", type=int, default=30, help="requests of the default line's serving stream")
     ap.add_argument("--fused", action="store_true", help="M_ee as one fused pass (hisq_mee_fused)")
+    ap.add_argument("--no-pdl", action="store_true", help="launch the solver kernels without programmatic "
+                    "dependent launch (hisq_programmatic_launch(0))")
     ap.add_argument("--solve-iters", type=int, default=2866,
                     help="reference arm: iterations of one GPU solve (extrapolation unit)")
     ap.add_argument("--solve-bytes", type=float, default=3.605e12,
