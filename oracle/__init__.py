@@ -77,6 +77,8 @@ def _load():
         "or_bicgstabl": (_i, [_p, _p, _p, _d, _i, _p, _p, _d, _i, _p, _p]),
         "or_dense": (None, [_p, _p, _p, _d, _d, _i, _p]),
         "or_schur_source": (None, [_p, _p, _p, _d, _p, _p]),
+        "or_link_r8_pack": (None, [_i64, _p, _p, _p]),
+        "or_link_r8_unpack": (None, [_i64, _p, _p, _p]),
         "or_reconstruct_odd": (None, [_p, _p, _p, _d, _p, _p, _p]),
         "or_solve_full": (_i, [_p, _p, _p, _d, _p, _p, _d, _i, _p, _p]),
         "or_lu_solve": (_i, [_i64, _p, _p]),
@@ -240,6 +242,25 @@ def gauge_emulate(dims, g, gfmt: str, recon: int, long_link: bool, antiperiodic_
     out = np.empty_like(a)
     _load().or_gauge_emulate(_ptr(L), _ptr(a), GFMT[gfmt], int(recon), 3 if long_link else 1,
                              int(antiperiodic_t), int(compute_f32), float(gmax), _ptr(out))
+    return out
+
+
+def link_r8_pack(links, signs):
+    """Links [n][3][3][2] (sign times SU(3)) and their signs -> the 8 reals of each ``V = sign * U``:
+    (arg V00/pi, arg V20/pi, V01, V02, V10)."""
+    a = _np(links).reshape(-1, 18)
+    sg = _np(signs).reshape(-1)
+    p = np.empty((a.shape[0], 8))
+    _load().or_link_r8_pack(a.shape[0], _ptr(a), _ptr(sg), _ptr(p))
+    return p
+
+
+def link_r8_unpack(p, signs):
+    """The 8 reals of each link (see link_r8_pack) -> links [n][3][3][2], rebuilt in FP64."""
+    pp = _np(p).reshape(-1, 8)
+    sg = _np(signs).reshape(-1)
+    out = np.empty((pp.shape[0], 3, 3, 2))
+    _load().or_link_r8_unpack(pp.shape[0], _ptr(pp), _ptr(sg), _ptr(out))
     return out
 
 

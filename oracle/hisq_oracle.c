@@ -41,6 +41,8 @@
 
 typedef double _Complex cplx;
 
+static const double kPi = 3.14159265358979323846264338327950288;
+
 /* ------------------------------------------------------------------------ */
 /* threads                                                                   */
 /* ------------------------------------------------------------------------ */
@@ -466,13 +468,117 @@ static void rebuild_row2(cplx *U, double sign)
     U[8] = sign * conj(U[0] * U[4] - U[1] * U[3]);
 }
 
+/* An angle stored as a fraction t of pi in [-1, 1] (the phases of the 13- and
+ * 8-real link formats): FP64 as is, FP32 rounded, fixed point
+ * q = rint(t * qmax) with qmax = 2^15-1 or 2^31-1 (no global scale: |t| <= 1). */
+static double angle_round(double t, int gfmt)
+{
+    if (gfmt == 1) return (double)(float)t;
+    if (gfmt >= 2) {
+        const double qm = gfmt == 2 ? 32767.0 : 2147483647.0;
+        return rint(t * qm) / qm;
+    }
+    return t;
+}
+
+static double round_elem(double x, int gfmt, double gmax, int compute_f32)
+{
+    if (gfmt == 0) return x;
+    if (gfmt == 1) return (double)(float)x;
+    int32_t q;
+    const int bits = gfmt == 2 ? 16 : 32;
+    double out;
+    or_fix_pack(1, &x, gmax, bits, &q);
+    or_fix_unpack(1, &q, gmax, bits, compute_f32, &out);
+    return out;
+}
+
+/* 13-real link (12 + 1, for long links in U(3)): rows 0 and 1 and the phase
+ * theta = arg det U, stored as t = theta/pi; for a unitary U the cofactor rule
+ * gives row2 = det(U) conj(row0 x row1), i.e. row2 = e^{i pi t} conj(row0 x row1).
+ * U: 9 complex elements (row-major) in and out, rows 0 and 1 already rounded. */
+static void rebuild_r13(cplx *U, double t)
+{
+    const cplx ph = cos(kPi * t) + I * sin(kPi * t);
+    U[6] = ph * conj(U[1] * U[5] - U[2] * U[4]);
+    U[7] = ph * conj(U[2] * U[3] - U[0] * U[5]);
+    U[8] = ph * conj(U[0] * U[4] - U[1] * U[3]);
+}
+
+/* 8-real link (Sec. 1: 18 -> 8 for SU(3) links; for U = sign * V with V in
+ * SU(3)): the parameters of V are t1 = arg(V00)/pi, t2 = arg(V20)/pi and the
+ * complex V01, V02, V10.  Rebuilding V from them (unitarity and det V = 1):
+ *   N = |V01|^2 + |V02|^2 = 1 - |V00|^2,  V00 = sqrt(1 - N) e^{i pi t1},
+ *   V20 = sqrt(N - |V10|^2) e^{i pi t2},
+ *   V11 = -(conj(V00) V01 V10 + conj(V02) conj(V20)) / N,
+ *   V12 = (conj(V01) conj(V20) - conj(V00) V02 V10) / N,
+ *   V21 = conj(V02 V10 - V00 V12),  V22 = conj(V00 V11 - V01 V10)
+ * (rows 1 and 2 orthogonal to row 0, row 2 = conj(row0 x row1)).  Needs
+ * N > 0; precision falls as N or |V20| become small (links near diagonal).
+ * p: the 8 reals {t1, t2, Re V01, Im V01, Re V02, Im V02, Re V10, Im V10}. */
+void or_link_r8_pack(int64_t n, const double *links, const double *sign, double *p)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const cplx *U = (const cplx *)(links + 18 * i);
+        cplx V[9];
+        for (int e = 0; e < 9; e++) V[e] = sign[i] * U[e];
+        double *q = p + 8 * i;
+        q[0] = carg(V[0]) / kPi;
+        q[1] = carg(V[6]) / kPi;
+        q[2] = creal(V[1]); q[3] = cimag(V[1]);
+        q[4] = creal(V[2]); q[5] = cimag(V[2]);
+        q[6] = creal(V[3]); q[7] = cimag(V[3]);
+    }
+}
+
+void or_link_r8_unpack(int64_t n, const double *p, const double *sign, double *links)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *q = p + 8 * i;
+        const cplx a2 = q[2] + I * q[3], a3 = q[4] + I * q[5], b1 = q[6] + I * q[7];
+        const double N = creal(a2 * conj(a2)) + creal(a3 * conj(a3));
+        const double ra = sqrt(fmax(1.0 - N, 0.0)), rc = sqrt(fmax(N - creal(b1 * conj(b1)), 0.0));
+        const cplx a1 = ra * (cos(kPi * q[0]) + I * sin(kPi * q[0]));
+        const cplx c1 = rc * (cos(kPi * q[1]) + I * sin(kPi * q[1]));
+        const cplx b2 = -(conj(a1) * a2 * b1 + conj(a3) * conj(c1)) / N;
+        const cplx b3 = (conj(a2) * conj(c1) - conj(a1) * a3 * b1) / N;
+        const cplx c2 = conj(a3 * b1 - a1 * b3);
+        const cplx c3 = conj(a1 * b2 - a2 * b1);
+        const cplx V[9] = {a1, a2, a3, b1, b2, b3, c1, c2, c3};
+        cplx *U = (cplx *)(links + 18 * i);
+        for (int e = 0; e < 9; e++) U[e] = sign[i] * V[e];
+    }
+}
+
 /* Format emulation (O4): a link field as the computation sees it after storage
- * in format gfmt (0 FP64, 1 FP32, 2 fixed-16, 3 fixed-32) with recon 18 or 12;
- * r12 rebuilds row 2 in FP64 from the decoded rows 0, 1 and the link's sign
- * (long links: k = 3, fat links: k = 1).  gmax is the field's scale. */
+ * in format gfmt (0 FP64, 1 FP32, 2 fixed-16, 3 fixed-32) with recon 18, 12, 13
+ * or 8 (the compressions rebuild in FP64 from the rounded stored reals); r12
+ * and r8 use the link's sign (long links: k = 3, fat links: k = 1).  gmax is
+ * the field's scale (max |element| over all 18 reals of every link). */
 void or_gauge_emulate(const int *L, const double *g, int gfmt, int recon, int k,
                       int antiperiodic_t, int compute_f32, double gmax, double *out)
 {
+    if (recon == 8) {
+        const int64_t V = vol_of(L);
+        double *sg = malloc(sizeof(double) * 4 * V);
+        for (int mu = 0; mu < 4; mu++)
+            for (int64_t lex = 0; lex < V; lex++) {
+                int c[4];
+                coords_of(L, lex, c);
+                sg[(int64_t)mu * V + lex] = link_sign(L, c, mu, k, antiperiodic_t);
+            }
+        double *p = malloc(sizeof(double) * 8 * 4 * V);
+        or_link_r8_pack(4 * V, g, sg, p);
+        for (int64_t i = 0; i < 4 * V; i++) {
+            p[8 * i] = angle_round(p[8 * i], gfmt);
+            p[8 * i + 1] = angle_round(p[8 * i + 1], gfmt);
+            for (int j = 2; j < 8; j++) p[8 * i + j] = round_elem(p[8 * i + j], gfmt, gmax, compute_f32);
+        }
+        or_link_r8_unpack(4 * V, p, sg, out);
+        free(p);
+        free(sg);
+        return;
+    }
     const int64_t V = vol_of(L);
     const int64_t n = 4 * V * 18;
     if (gfmt == 0) {
@@ -494,6 +600,13 @@ void or_gauge_emulate(const int *L, const double *g, int gfmt, int recon, int k,
                 cplx *U = (cplx *)(out + ((int64_t)mu * V + lex) * 18);
                 rebuild_row2(U, link_sign(L, c, mu, k, antiperiodic_t));
             }
+    } else if (recon == 13) {
+        for (int64_t i = 0; i < 4 * V; i++) {
+            const cplx *G = (const cplx *)(g + 18 * i);
+            const cplx det = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                             G[2] * (G[3] * G[7] - G[4] * G[6]);
+            rebuild_r13((cplx *)(out + 18 * i), angle_round(carg(det) / kPi, gfmt));
+        }
     }
 }
 
