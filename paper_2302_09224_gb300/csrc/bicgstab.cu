@@ -40,6 +40,8 @@ struct BState {
     double g_re[kMaxL + 1], g_im[kMaxL + 1];      // gamma
     double gpp_re[kMaxL + 1], gpp_im[kMaxL + 1];  // gamma''
     double rr, rr_max, delta2, stop2, tiny2;
+    double rt2;   // |rt|^2 of the shadow residual
+    double brk2;  // breakdown when |<rt, v>|^2 <= brk2 |rt|^2 |v|^2
     int active, reason, cycles, l;
 };
 
@@ -81,8 +83,12 @@ __device__ void b_finish(BArgs &a, const double *s)
 {
     BState *b = a.b;
     if (a.op == OP_RHO) {
-        // rho1 = <rt, r_j>; beta = alpha rho1 / rho0; rho0 = rho1
-        if (b->rho_re * b->rho_re + b->rho_im * b->rho_im <= b->tiny2) {
+        // rho1 = <rt, r_j>; beta = alpha rho1 / rho0; rho0 = rho1.  Breakdown:
+        // rho1 (nearly) orthogonal relative to |rt| |r_j| (sums[2] = |r_j|^2),
+        // or a rho0 too small to divide by
+        const double n2 = s[0] * s[0] + s[1] * s[1];
+        if (b->rho_re * b->rho_re + b->rho_im * b->rho_im <= b->tiny2 ||
+            (s[2] > 0.0 && !(n2 > b->brk2 * b->rt2 * s[2])) || !isfinite(n2)) {
             b_stop(b, REASON_BREAKDOWN);
             return;
         }
@@ -93,8 +99,9 @@ __device__ void b_finish(BArgs &a, const double *s)
         b->rho_re = s[0];
         b->rho_im = s[1];
     } else if (a.op == OP_GAMMA) {
-        // gamma = <rt, u_{j+1}>; alpha = rho0 / gamma
-        if (s[0] * s[0] + s[1] * s[1] <= b->tiny2 || !isfinite(s[0]) || !isfinite(s[1])) {
+        // gamma = <rt, u_{j+1}>; alpha = rho0 / gamma; breakdown relative to |rt| |u_{j+1}|
+        const double n2 = s[0] * s[0] + s[1] * s[1];
+        if (n2 <= b->tiny2 || !(n2 > b->brk2 * b->rt2 * s[2]) || !isfinite(s[0]) || !isfinite(s[1])) {
             b_stop(b, REASON_BREAKDOWN);
             return;
         }
@@ -605,7 +612,9 @@ struct BRun {
         init.rr_max = rr;
         init.delta2 = p.delta * p.delta;
         init.stop2 = p.tol * p.tol * bb;
-        init.tiny2 = 1e-300;
+        init.tiny2 = 1e-300;  // only guards the divisions
+        init.rt2 = rr;        // rt = r_0
+        init.brk2 = 1e-60;    // |<rt, v>| <= 1e-30 |rt| |v|
         init.active = 1;
         init.l = l;
         *bh = init;
