@@ -624,6 +624,8 @@ hisq_status run_bcg(hisq_ctx *c, hisq_gauge *g, const BCGConfig &cfg, const doub
     if (cfg.sloppy.compute != HISQ_COMPUTE_F32 ||
         !(cfg.sloppy.spinor == S_F32 || cfg.sloppy.spinor == S_HALF || cfg.sloppy.spinor == S_INT20))
         return fail(c, HISQ_EINVAL, "batched solves support the FP32, half and 20-bit sloppy triplets");
+    if (cfg.sloppy.long_recon != 12 && cfg.sloppy.long_recon != 18)
+        return fail(c, HISQ_EINVAL, "batched solves support 18- and 12-real long links");
     BatchSession bs(c, g, cfg, s);
     hisq_status e = bs.setup();
     if (e) return e;

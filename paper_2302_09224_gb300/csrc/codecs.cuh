@@ -551,11 +551,34 @@ __device__ __forceinline__ void gather_coherent(const char *b, int n, int i, uin
     }
 }
 
+// Row 2 of a 13-real link: f * conj(row0 x row1) with the complex factor
+// f = (fr, fi) (the det phase e^{i pi t}, times the fixed-point scale).
+template <typename real>
+__device__ __forceinline__ void rebuild_row2_phase(real U[18], real fr, real fi)
+{
+#define RE(k) U[2 * (k)]
+#define IM(k) U[2 * (k) + 1]
+    const real c0r = RE(1) * RE(5) - IM(1) * IM(5) - (RE(2) * RE(4) - IM(2) * IM(4));
+    const real c0i = RE(1) * IM(5) + IM(1) * RE(5) - (RE(2) * IM(4) + IM(2) * RE(4));
+    const real c1r = RE(2) * RE(3) - IM(2) * IM(3) - (RE(0) * RE(5) - IM(0) * IM(5));
+    const real c1i = RE(2) * IM(3) + IM(2) * RE(3) - (RE(0) * IM(5) + IM(0) * RE(5));
+    const real c2r = RE(0) * RE(4) - IM(0) * IM(4) - (RE(1) * RE(3) - IM(1) * IM(3));
+    const real c2i = RE(0) * IM(4) + IM(0) * RE(4) - (RE(1) * IM(3) + IM(1) * RE(3));
+    RE(6) = fr * c0r + fi * c0i; IM(6) = fi * c0r - fr * c0i;
+    RE(7) = fr * c1r + fi * c1i; IM(7) = fi * c1r - fr * c1i;
+    RE(8) = fr * c2r + fi * c2i; IM(8) = fi * c2r - fr * c2i;
+#undef RE
+#undef IM
+}
+
 template <int GF, int RECON>
 struct Link {
     static constexpr int n16 = link_n16(GF, RECON);
     static constexpr int tail = link_tail(GF, RECON);
-    static constexpr int chunks = n16 + (tail ? 1 : 0);  // the tail chunk holds its 4 or 8 bytes first
+    static constexpr int rows = link_rows_reals(RECON);  // reals in the row planes
+    static constexpr bool kPhase = RECON == 13;           // a phase plane after the tail plane
+    static constexpr int row_chunks = n16 + (tail ? 1 : 0);  // the tail chunk holds its 4 or 8 bytes first
+    static constexpr int chunks = row_chunks + (kPhase ? 1 : 0);  // the phase chunk holds its real first
 
     // li = (parity*4 + mu)*Vh + cb; pstride = bytes of one plane (8*Vh*16).
     // Links are read once per pass: evict-first loads, unless KEEP (a link
@@ -572,6 +595,35 @@ struct Link {
             const uint2 t = ld(reinterpret_cast<const uint2 *>(base + n16 * pstride) + li);
             c[n16] = make_uint4(t.x, t.y, 0u, 0u);
         }
+        if constexpr (kPhase) {
+            // phase plane: after the tail plane (tail bytes per link), one real per link
+            const char *pp = base + n16 * pstride + (size_t)tail * (pstride / 16);
+            if constexpr (gauge_real_bytes(GF) == 2) {
+                c[row_chunks] = make_uint4((unsigned)ld(reinterpret_cast<const unsigned short *>(pp) + li), 0u, 0u, 0u);
+            } else if constexpr (gauge_real_bytes(GF) == 4) {
+                c[row_chunks] = make_uint4(ld(reinterpret_cast<const unsigned int *>(pp) + li), 0u, 0u, 0u);
+            } else {
+                const uint2 t = ld(reinterpret_cast<const uint2 *>(pp) + li);
+                c[row_chunks] = make_uint4(t.x, t.y, 0u, 0u);
+            }
+        }
+    }
+
+    // The stored phase of a 13-real link as a fraction t of pi (t in [-1, 1]).
+    template <typename real>
+    __device__ static real phase(const uint4 c[chunks])
+    {
+        static_assert(kPhase, "13-real links only");
+        const uint4 w = c[row_chunks];
+        if constexpr (GF == G_F64) {
+            return (real)__hiloint2double((int)w.y, (int)w.x);
+        } else if constexpr (GF == G_F32) {
+            return (real)__uint_as_float(w.x);
+        } else if constexpr (GF == G_FIX16) {
+            return (real)__fmul_rn(__int2float_rn((int)(short)(w.x & 0xffffu)), 1.0f / 32767.0f);
+        } else {
+            return (real)((double)(int)w.x * (1.0 / 2147483647.0));
+        }
     }
 
     template <typename real>
@@ -579,7 +631,7 @@ struct Link {
     {
         if constexpr (GF == G_F64) {
 #pragma unroll
-            for (int k = 0; k < RECON / 2; k++) {
+            for (int k = 0; k < rows / 2; k++) {
                 U[2 * k] = (real)__hiloint2double((int)c[k].y, (int)c[k].x);
                 U[2 * k + 1] = (real)__hiloint2double((int)c[k].w, (int)c[k].z);
             }
@@ -594,7 +646,7 @@ struct Link {
                 U[4 * n16 + 1] = __uint_as_float(c[n16].y);
             }
         } else if constexpr (GF == G_FIX16) {
-            uint32_t w[RECON / 2];
+            uint32_t w[rows / 2];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
                 w[4 * k] = c[k].x; w[4 * k + 1] = c[k].y; w[4 * k + 2] = c[k].z; w[4 * k + 3] = c[k].w;
@@ -606,7 +658,7 @@ struct Link {
                 w[4 * n16 + 1] = c[n16].y;
             }
 #pragma unroll
-            for (int k = 0; k < RECON / 2; k++) {
+            for (int k = 0; k < rows / 2; k++) {
                 if constexpr (sizeof(real) == 8) {
                     U[2 * k] = (double)(int)(short)(w[k] & 0xffffu);
                     U[2 * k + 1] = (double)((int)w[k] >> 16);
@@ -616,7 +668,7 @@ struct Link {
                 }
             }
         } else {  // G_FIX32
-            int q[RECON];
+            int q[rows];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
                 q[4 * k] = (int)c[k].x; q[4 * k + 1] = (int)c[k].y; q[4 * k + 2] = (int)c[k].z; q[4 * k + 3] = (int)c[k].w;
@@ -626,7 +678,7 @@ struct Link {
                 q[4 * n16 + 1] = (int)c[n16].y;
             }
 #pragma unroll
-            for (int k = 0; k < RECON; k++) {
+            for (int k = 0; k < rows; k++) {
                 if constexpr (is_ff<real>::value)
                     U[k] = ff_from_int(q[k]);
                 else if constexpr (sizeof(real) == 8)
@@ -637,12 +689,15 @@ struct Link {
         }
     }
 
+    // decoded rows; for the 13-real format U[12] receives the phase (the
+    // caller rebuilds row 2 over it)
     template <typename real, bool KEEP = false>
     __device__ static void load(const char *base, size_t pstride, int li, real U[18])
     {
         uint4 c[chunks];
         gather<KEEP>(base, pstride, li, c);
         decode(c, U);
+        if constexpr (kPhase) U[12] = phase<real>(c);
     }
 };
 

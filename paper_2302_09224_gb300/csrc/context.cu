@@ -231,7 +231,10 @@ hisq_status check_prec(hisq_ctx *c, const hisq_prec &p)
         return fail(c, HISQ_EINVAL, "unsupported precision triplet gauge=%d spinor=%d compute=%d", p.gauge,
                     p.spinor, p.compute);
     if (p.fat_recon != 18) return fail(c, HISQ_EINVAL, "fat links must be stored with 18 reals");
-    if (p.long_recon != 18 && p.long_recon != 12) return fail(c, HISQ_EINVAL, "long_recon must be 18 or 12");
+    if (p.long_recon != 18 && p.long_recon != 12 && p.long_recon != 13)
+        return fail(c, HISQ_EINVAL, "long_recon must be 18, 13 or 12");
+    if (p.long_recon == 13 && !(p.compute == HISQ_COMPUTE_F32 && (p.gauge == G_FIX16 || p.gauge == G_F32)))
+        return fail(c, HISQ_EINVAL, "13-real long links need an FP32-compute triplet with 16-bit or FP32 links");
     return HISQ_OK;
 }
 
@@ -246,6 +249,8 @@ static hisq_status get_copy(hisq_ctx *c, hisq_gauge *g, bool lng, int gf, int re
     if (recon == 12 && !(lng ? g->lng_r12_ok : g->fat_r12_ok))
         return fail(c, HISQ_EINVAL, "%s links are not a sign times SU(3): 12-real compression refused",
                     lng ? "long" : "fat");
+    if (recon == 13 && !(lng && g->lng_u3_ok))
+        return fail(c, HISQ_EINVAL, "%s links are not unitary: 13-real compression refused", lng ? "long" : "fat");
     LinkCopy lc;
     lc.gf = gf;
     lc.recon = recon;
@@ -411,16 +416,17 @@ hisq_status hisq_load_gauge(hisq_ctx *c, const int dims[4], const double *fat, c
     const cudaMemcpyKind kind = (flags & HISQ_GAUGE_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(g->fat64, fat, bytes, kind, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->lng64, lng, bytes, kind, c->stream);
-    double *scal = cur_red(c).result;  // 4 scratch doubles: fat max, long max, fat dev, long dev
-    if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 4 * sizeof(double), c->stream);
+    double *scal = cur_red(c).result;  // 5 scratch doubles: fat max, long max, fat dev, long dev, long U(3) dev
+    if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, 5 * sizeof(double), c->stream);
     if (e == cudaSuccess) {
         LaunchScope ls(c, c->stream, PROF_CONVERT, 0.0);
         launch_absmax(18 * 4 * V, g->fat64, scal + 0, c->stream);
         launch_absmax(18 * 4 * V, g->lng64, scal + 1, c->stream);
         launch_r12_check(g->geom, g->fat64, 1, scal + 2, c->stream);
         launch_r12_check(g->geom, g->lng64, 3, scal + 3, c->stream);
+        launch_u3_check(g->geom, g->lng64, scal + 4, c->stream);
     }
-    double h[4] = {0, 0, 0, 0};
+    double h[5] = {0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -439,6 +445,7 @@ hisq_status hisq_load_gauge(hisq_ctx *c, const int dims[4], const double *fat, c
     g->lng_max = h[1];
     g->fat_r12_ok = std::isfinite(h[2]) && h[2] <= 1e-6;
     g->lng_r12_ok = std::isfinite(h[3]) && h[3] <= 1e-6;
+    g->lng_u3_ok = std::isfinite(h[4]) && h[4] <= 1e-6;
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->gauges.push_back(g);

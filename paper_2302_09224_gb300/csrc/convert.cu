@@ -192,6 +192,65 @@ __global__ void quantise_kernel(Geom g, const double *links, double inv, char *o
                 reinterpret_cast<int2 *>(out + n16 * pstride)[li] = make_int2(q[4 * n16], q[4 * n16 + 1]);
         }
     }
+    if constexpr (RECON == 13) {
+        // the 13th real: arg det U as a fraction of pi (row 2 = det(U) conj(row0 x row1) for unitary U)
+        double u[18];
+        for (int k = 0; k < 18; k++) u[k] = src[k];
+        auto mre = [&](int i, int j) { return u[2 * (3 * i + j)]; };
+        auto mim = [&](int i, int j) { return u[2 * (3 * i + j) + 1]; };
+        auto cof = [&](int a, int b, int c, int d, double &r, double &im) {  // m(1,a) m(2,b) - m(1,c) m(2,d)
+            r = mre(1, a) * mre(2, b) - mim(1, a) * mim(2, b) - (mre(1, c) * mre(2, d) - mim(1, c) * mim(2, d));
+            im = mre(1, a) * mim(2, b) + mim(1, a) * mre(2, b) - (mre(1, c) * mim(2, d) + mim(1, c) * mre(2, d));
+        };
+        double c0r, c0i, c1r, c1i, c2r, c2i;
+        cof(1, 2, 2, 1, c0r, c0i);
+        cof(2, 0, 0, 2, c1r, c1i);
+        cof(0, 1, 1, 0, c2r, c2i);
+        const double dr = mre(0, 0) * c0r - mim(0, 0) * c0i + mre(0, 1) * c1r - mim(0, 1) * c1i + mre(0, 2) * c2r -
+                          mim(0, 2) * c2i;
+        const double di = mre(0, 0) * c0i + mim(0, 0) * c0r + mre(0, 1) * c1i + mim(0, 1) * c1r + mre(0, 2) * c2i +
+                          mim(0, 2) * c2r;
+        const double t = atan2(di, dr) * 0.31830988618379067154;  // 1/pi
+        char *pp = out + n16 * pstride + (size_t)tail * n;
+        if constexpr (GF == G_F64)
+            reinterpret_cast<double *>(pp)[li] = t;
+        else if constexpr (GF == G_F32)
+            reinterpret_cast<float *>(pp)[li] = (float)t;
+        else if constexpr (GF == G_FIX16)
+            reinterpret_cast<short *>(pp)[li] = (short)rint(t * 32767.0);
+        else
+            reinterpret_cast<int *>(pp)[li] = (int)rint(t * 2147483647.0);
+    }
+}
+
+// Largest |(U U^+)_ij - delta_ij| over all links of a field: zero to rounding
+// when every link is unitary (the 13-real format applies).
+__global__ void u3_check_kernel(Geom g, const double *links, double *out)
+{
+    const int V = 2 * g.vh;
+    double m = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < 4LL * V;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const double *u = links + idx * 18;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double re = 0.0, im = 0.0;  // sum_k U_ik conj(U_jk)
+                for (int k = 0; k < 3; k++) {
+                    const double ar = u[2 * (3 * i + k)], ai = u[2 * (3 * i + k) + 1];
+                    const double br = u[2 * (3 * j + k)], bi = u[2 * (3 * j + k) + 1];
+                    re += ar * br + ai * bi;
+                    im += ai * br - ar * bi;
+                }
+                const double d = fmax(fabs(re - (i == j ? 1.0 : 0.0)), fabs(im));
+                m = (d > m || d != d) ? d : m;
+            }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, m, off);
+        m = (o > m || o != o) ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
 int nblocks(int64_t n, int b) { return (int)((n + b - 1) / b); }
@@ -258,6 +317,12 @@ void launch_absmax(int64_t n, const double *x, double *out, cudaStream_t s)
     absmax_kernel<<<nb, kBlock, 0, s>>>(n, x, out);
 }
 
+void launch_u3_check(const Geom &g, const double *links, double *out, cudaStream_t s)
+{
+    const int nb = (int)std::min<int64_t>(nblocks(8LL * g.vh, kBlock), 4096);
+    u3_check_kernel<<<nb, kBlock, 0, s>>>(g, links, out);
+}
+
 void launch_r12_check(const Geom &g, const double *links, int k, double *out, cudaStream_t s)
 {
     const int nb = (int)std::min<int64_t>(nblocks(8LL * g.vh, kBlock), 4096);
@@ -275,6 +340,13 @@ void launch_quantise_links(const Geom &g, int gf, int recon, const double *links
         case G_F32: Q(G_F32, 18); break;
         case G_FIX16: Q(G_FIX16, 18); break;
         case G_FIX32: Q(G_FIX32, 18); break;
+        }
+    } else if (recon == 13) {
+        switch (gf) {
+        case G_F64: Q(G_F64, 13); break;
+        case G_F32: Q(G_F32, 13); break;
+        case G_FIX16: Q(G_FIX16, 13); break;
+        case G_FIX32: Q(G_FIX32, 13); break;
         }
     } else {
         switch (gf) {

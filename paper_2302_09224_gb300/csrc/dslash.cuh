@@ -207,6 +207,18 @@ __device__ __forceinline__ void load_neighbour(const char *b, int n, int i, real
     }
 }
 
+// Row 2 of a 13-real link whose phase t (as a fraction of pi) the loader left
+// in U[12]: e^{i pi t} scale conj(row0 x row1), scale the long links'
+// fixed-point scale (rows 0 and 1 are unscaled integers) or 1.
+template <typename real>
+__device__ __forceinline__ void rebuild_row2_r13(real U[18], real scale)
+{
+    static_assert(std::is_same<real, float>::value, "13-real links with FP32 compute");
+    float sp, cp;
+    sincospif(U[12], &sp, &cp);
+    rebuild_row2_phase(U, scale * cp, scale * sp);
+}
+
 template <int GF, int SF, typename real, int LREC, bool COH = false, bool KEEP = false>
 __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, int cmu, int c3, int lex, int cb,
                                                   int po, size_t pstride, real lsc, real ratio, int phase_sum,
@@ -237,6 +249,8 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     if constexpr (LREC == 12) {
         const bool flip = g.antiperiodic_t && mu == 3 && c3 + 3 >= L;
         rebuild_row2(U, flip ? -eta : eta);
+    } else if constexpr (LREC == 13) {
+        rebuild_row2_r13(U, lsc);
     }
     load_neighbour<real, SF, COH>(a.in, vh, np3, s);
     if constexpr (kScaled)
@@ -248,6 +262,8 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     if constexpr (LREC == 12) {
         const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
         rebuild_row2(U, flip ? -eta : eta);
+    } else if constexpr (LREC == 13) {
+        rebuild_row2_r13(U, lsc);
     }
     load_neighbour<real, SF, COH>(a.in, vh, nm3, s);
     if constexpr (kScaled)
@@ -392,6 +408,17 @@ void launch_any(int cfg, const DslashArgs &a, cudaStream_t s)
 template <int GF, int SF, typename real>
 bool launch_dslash_t(int long_recon, bool reduce, int cfg, const DslashArgs &a, cudaStream_t s)
 {
+    if (long_recon == 13) {  // FP32 compute with 16-bit or FP32 links
+        if constexpr (std::is_same<real, float>::value && (GF == G_FIX16 || GF == G_F32)) {
+            if (reduce)
+                launch_any<GF, SF, real, 13, true>(cfg, a, s);
+            else
+                launch_any<GF, SF, real, 13, false>(cfg, a, s);
+            return true;
+        }
+        return false;
+    }
+    if (long_recon != 12 && long_recon != 18) return false;
     if (long_recon == 12) {
         if (reduce)
             launch_any<GF, SF, real, 12, true>(cfg, a, s);
@@ -547,6 +574,7 @@ bool launch_mee_fused_t(int long_recon, int cfg, const MeeArgs &m, cudaStream_t 
 {
     // the unrolled 64-register shape only (the one the separate passes pick)
     (void)cfg;
+    if (long_recon != 12 && long_recon != 18) return false;  // other long-link formats: two passes
     if (long_recon == 12)
         launch_mee_cfg<GF, SF, real, 12, 4>(m, s);
     else

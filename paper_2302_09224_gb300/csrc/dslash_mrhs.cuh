@@ -539,6 +539,7 @@ template <int GF, int SF, typename real>
 bool launch_mrhs_t(int long_recon, bool reduce, int T, int variant, const DslashMArgs &args, cudaStream_t s)
 {
     static_assert(std::is_same<real, float>::value, "the batched stencil computes in FP32");
+    if (long_recon != 12 && long_recon != 18) return false;  // 18- and 12-real long links only
     if (reduce && !red_fits(args.g.vh, kMrhsBlock, 2 * T)) return false;
     for (int t0 = 0; t0 < args.nrhs; t0 += T) {
         if (args.tile_mask != 0u && !((args.tile_mask >> (t0 / T)) & 1u)) continue;  // no system of it iterates

@@ -34,16 +34,20 @@ __host__ __device__ constexpr int gauge_real_bytes(int gf)
 {
     return gf == G_F64 ? 8 : gf == G_FIX16 ? 2 : 4;
 }
+// Reals of a link kept in its row planes: 18, 12, and 12 for the 13-real
+// format, whose 13th real (the phase of det U) lives in a plane of its own.
+__host__ __device__ constexpr int link_rows_reals(int recon) { return recon == 13 ? 12 : recon; }
 __host__ __device__ constexpr int link_bytes(int gf, int recon) { return gauge_real_bytes(gf) * recon; }
-__host__ __device__ constexpr int link_n16(int gf, int recon) { return link_bytes(gf, recon) / 16; }
-__host__ __device__ constexpr int link_tail(int gf, int recon) { return link_bytes(gf, recon) % 16; }
+__host__ __device__ constexpr int link_n16(int gf, int recon) { return gauge_real_bytes(gf) * link_rows_reals(recon) / 16; }
+__host__ __device__ constexpr int link_tail(int gf, int recon) { return gauge_real_bytes(gf) * link_rows_reals(recon) % 16; }
 
 // Bytes of a half-lattice field of n sites in the planar layout: 16-B planes
 // [plane][site], then the tail plane [site] (all planes of one field are
 // contiguous and start 16-B aligned).
 inline size_t spinor_field_bytes(int sf, int64_t n) { return (size_t)spinor_site_bytes(sf) * (size_t)n; }
 
-// Bytes of one stored link field: [plane][parity][mu][Vh] chunks.
+// Bytes of one stored link field: [plane][parity][mu][Vh] chunks (the
+// 13-real format's phase plane follows the tail plane).
 inline size_t link_field_bytes(int gf, int recon, int64_t vh)
 {
     return (size_t)link_bytes(gf, recon) * 8u * (size_t)vh;
@@ -260,6 +264,8 @@ void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out
 // out_max / out_maxdev must be zeroed before the launch (atomic max)
 void launch_absmax(int64_t n, const double *x, double *out_max, cudaStream_t s);
 void launch_r12_check(const Geom &g, const double *links, int k, double *out_maxdev, cudaStream_t s);
+// max over links of |U U^+ - 1| (out_maxdev zeroed before the launch)
+void launch_u3_check(const Geom &g, const double *links, double *out_maxdev, cudaStream_t s);
 void launch_quantise_links(const Geom &g, int gf, int recon, const double *links, double inv, char *out,
                            cudaStream_t s);
 
@@ -283,6 +289,7 @@ struct hisq_gauge {
     double *lng64 = nullptr;
     double fat_max = 0, lng_max = 0;
     bool fat_r12_ok = false, lng_r12_ok = false;
+    bool lng_u3_ok = false;    // long links unitary: the 13-real format applies
     std::vector<hisq::LinkCopy> fat_copies, lng_copies;
     mutable std::mutex copy_mu;  // guards fat_copies / lng_copies (built lazily)
 };

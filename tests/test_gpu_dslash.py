@@ -263,3 +263,69 @@ def test_unstorable_output_is_reported(ctx, name):
         assert torch.isfinite(out).all() and torch.equal(out, ref)
     finally:
         hisq.hisq_free_gauge(ctx, g)
+
+
+@pytest.mark.parametrize("name", ["f32", "half", "int20"])
+@pytest.mark.parametrize("dims,anti,parity,a", CASES)
+def test_dslash_r13_parity(ctx, orc, name, dims, anti, parity, a):
+    """13-real long links (rows 0, 1 and the phase of det U; row 2 rebuilt as
+    e^{i pi t} conj(row0 x row1) in registers) against the exact stencil and
+    the oracle's emulation of the same storage, within the 12-real bounds."""
+    fat, lng = lattice(dims, anti)
+    x, y, out = run_gpu(ctx, dims, anti, name, 13, parity, a)
+    exact = oracle_apply(orc, dims, fat, lng, parity, a, x, y)
+    assert rel(out, exact) <= BOUND_EXACT[name], (name, rel(out, exact))
+    fe = orc.gauge_emulate(dims, fat, GAUGE[name], 18, long_link=False, antiperiodic_t=anti)
+    le = orc.gauge_emulate(dims, lng, GAUGE[name], 13, long_link=True, antiperiodic_t=anti)
+    xe = orc.spinor_emulate(x, SPINOR[name]).reshape(x.shape)
+    ye = orc.spinor_emulate(y, SPINOR[name]).reshape(y.shape)
+    emul = oracle_apply(orc, dims, fe, le, parity, a, xe, ye)
+    assert rel(out, emul) <= BOUND_EMUL[name], (name, rel(out, emul))
+
+
+def u3_long_links(lng, seed):
+    """Long links times a random phase per link: unitary, no longer a sign times SU(3)."""
+    u = lng[..., 0] + 1j * lng[..., 1]
+    g = np.random.Generator(np.random.Philox(key=seed))
+    ph = np.exp(1j * g.uniform(-np.pi, np.pi, u.shape[:-2]))[..., None, None]
+    w = u * ph
+    return np.ascontiguousarray(np.stack([w.real, w.imag], axis=-1))
+
+
+@pytest.mark.parametrize("name", ["f32", "int20"])
+def test_r13_u3_links_and_refusals(ctx, orc, name):
+    """U(3) long links (a random phase on each): 12-real compression is refused,
+    13 reals reproduce them; a 13-real request on FP64 or 30-bit triplets, or
+    for a batched solve, is refused; a CG solve with 13-real links meets the
+    oracle's true residual."""
+    dims = (4, 6, 4, 8)
+    fat, lng0 = lattice(dims, False)
+    lng = u3_long_links(lng0, 17)
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    try:
+        x = synth.spinor(dims, 1000)
+        out = torch.empty_like(x).cuda()
+        with pytest.raises(hisq.HisqError, match="12-real"):
+            hisq.hisq_dslash(ctx, g, hisq.prec(name, 12), 0, 0.0, None, x.cuda(), out, True)
+        hisq.hisq_dslash(ctx, g, hisq.prec(name, 13), 0, 0.0, None, x.cuda(), out, True)
+        torch.cuda.synchronize()
+        exact = orc.dslash(dims, fat, lng, 0, x.numpy())
+        assert rel(out.cpu().numpy(), exact) <= BOUND_EXACT[name]
+        for bad in ("f64", "int30"):
+            with pytest.raises(hisq.HisqError, match="EINVAL"):
+                hisq.hisq_dslash(ctx, g, hisq.prec(bad, 13), 0, 0.0, None, x.cuda(), out, True)
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.on_device = 0.05, 1e-10, 1
+        p.sloppy = hisq.prec(name, 13)
+        b = x.cuda()
+        sol = torch.zeros_like(b)
+        st, info = hisq.hisq_cg(ctx, g, p, b, sol)
+        assert st == hisq.HISQ_OK
+        r = x.numpy() - orc.mee(dims, fat, lng, 0.05, sol.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(x.numpy()) <= 1e-10
+        p.nrhs = 2
+        b2 = torch.stack([b, b]).contiguous()
+        with pytest.raises(hisq.HisqError, match="EINVAL"):
+            hisq.hisq_cg(ctx, g, p, b2, torch.zeros_like(b2))
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
