@@ -542,7 +542,7 @@ def run_solve_only(args):
     x = torch.zeros_like(b)
     p = hisq.hisq_default_params()
     p.mass, p.tol, p.delta, p.on_device = MASS, TOL, DELTA, 1
-    p.sloppy = hisq.prec(args.prec, 12)
+    p.sloppy = hisq.prec(args.prec, args.recon)
     p.maxiter = args.maxiter
     st, info = hisq.hisq_cg(ctx, g, p, b, x)
     torch.cuda.synchronize()
@@ -838,6 +838,7 @@ def main():
                     help="reference arm: algorithmic bytes of one GPU solve")
     ap.add_argument("--stencil", default=None, help="LX,LY,LZ,LT: only run stencil applications (profiling)")
     ap.add_argument("--prec", default="int20")
+    ap.add_argument("--recon", type=int, default=12, help="long-link storage (12 or 18) of --solve")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--stencil-config", default="",
                     help="force the stencil launch shapes: A (both passes) or A,B (plain, reducing), each 0..4")

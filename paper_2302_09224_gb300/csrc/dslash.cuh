@@ -272,6 +272,156 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     acc.adj_sub(U, s);
 }
 
+// ---------------------------------------------------------------------------
+// The 30-bit triplet's FP64-class compute on exact integer products.  A
+// 32-bit fixed-point link element u (|u| < 2^31) times a 30-bit field integer
+// q (|q| < 2^29) is exact in 64 bits (mad.wide.s32, half the FP32 FMA rate on
+// GB300), and one term's colour component, a sum of six such products, stays
+// below 6 2^60 < 2^63.  So each term (one link, one neighbour) is formed
+// exactly in integers, in units of the link field's scale times the
+// neighbour's power of two 2^(E-127); it then enters an FP32-pair accumulator
+// per link field: the 64-bit sum is cut into three pieces of at most 22 bits,
+// each exact in FP32 and scaled by an exact power of two (one fma against the
+// magic 2^23 each), the top piece added with an error-free TwoSum and the two
+// lower pieces to the low word.  Instead of twelve FP32 operations per real
+// multiply-add (a pair TwoProd and TwoSum), a term costs 36 integer
+// multiply-adds and about 17 operations per colour component.
+// ---------------------------------------------------------------------------
+struct SiteAccI30 {
+    float h[2][6], l[2][6];  // [fat, long][component]: unevaluated hi + lo
+
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int f = 0; f < 2; f++)
+#pragma unroll
+            for (int k = 0; k < 6; k++) h[f][k] = l[f][k] = 0.0f;
+    }
+
+    // acc[f][k] += P 2^e (P exact in 64 bits)
+    __device__ __forceinline__ void add(int f, int k, long long P, float p0, float p21, float p42)
+    {
+        const unsigned lo = (unsigned)P, hi = (unsigned)((unsigned long long)P >> 32);
+        const unsigned c0 = lo & 0x1FFFFFu;
+        const unsigned c1 = __funnelshift_r(lo, hi, 21) & 0x1FFFFFu;
+        const int c2 = (int)hi >> 10;  // bits 42..63 with the sign: |c2| < 2^21
+        // 2^23 + c (or 2^23 + 2^22 + c2) is an exact float; one fma removes the offset and scales
+        const float f0 = __fmaf_rn(__uint_as_float(0x4B000000u | c0), p0, -8388608.0f * p0);
+        const float f1 = __fmaf_rn(__uint_as_float(0x4B000000u | c1), p21, -8388608.0f * p21);
+        const float f2 = __fmaf_rn(__uint_as_float(0x4B000000u | (unsigned)(c2 + 0x400000)), p42, -12582912.0f * p42);
+        const float s = __fadd_rn(h[f][k], f2);
+        const float bb = __fsub_rn(s, h[f][k]);
+        const float e = __fadd_rn(__fsub_rn(h[f][k], __fsub_rn(s, bb)), __fsub_rn(f2, bb));
+        h[f][k] = s;
+        l[f][k] = __fadd_rn(l[f][k], __fadd_rn(e, __fadd_rn(f1, f0)));
+    }
+
+    // one term: U s (BWD: -U^+ s) with u the link's 18 integers and q the
+    // neighbour's 6 integers at the power of two 2^(E-127)
+    template <bool BWD>
+    __device__ __forceinline__ void term(int f, const int u[18], const int q[6], unsigned E)
+    {
+        // 2^(E-127), 2^(E-106), 2^(E-85) as exact floats (exponent fields clamped at 255: a term that
+        // large overflows the FP32-range pairs anyway and the store reports it)
+        const float p0 = __uint_as_float(E << 23);
+        const float p21 = __uint_as_float(min(E + 21u, 255u) << 23);
+        const float p42 = __uint_as_float(min(E + 42u, 255u) << 23);
+        int sr[3], si[3], nsr[3], nsi[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            sr[j] = q[2 * j];
+            si[j] = q[2 * j + 1];
+            nsr[j] = -sr[j];
+            nsi[j] = -si[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            long long re = 0, im = 0;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                // forward: Re += Ur sr - Ui si, Im += Ur si + Ui sr       (U_ij)
+                // backward: Re += -Ur sr - Ui si, Im += -Ur si + Ui sr   (U_ji, conjugated, subtracted)
+                const int e = BWD ? 3 * j + i : 3 * i + j;
+                const int ur = u[2 * e], ui = u[2 * e + 1];
+                asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(re) : "r"(ur), "r"(BWD ? nsr[j] : sr[j]));
+                asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(re) : "r"(ui), "r"(nsi[j]));
+                asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(im) : "r"(ur), "r"(BWD ? nsi[j] : si[j]));
+                asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(im) : "r"(ui), "r"(sr[j]));
+            }
+            add(f, 2 * i, re, p0, p21, p42);
+            add(f, 2 * i + 1, im, p0, p21, p42);
+        }
+    }
+
+    // the total fsc * fat + lsc * long of component k
+    __device__ __forceinline__ ff get(int k, ff fsc, ff lsc) const
+    {
+        const ff a = ff_fast_two_sum(h[0][k], l[0][k]) * fsc;
+        const ff b = ff_fast_two_sum(h[1][k], l[1][k]) * lsc;
+        return a + b;
+    }
+};
+
+// A link of 18 32-bit fixed-point integers, raw.
+template <bool KEEP>
+__device__ __forceinline__ void load_link_ints(const char *base, size_t pstride, int li, int u[18])
+{
+    uint4 c[Link<G_FIX32, 18>::chunks];
+    Link<G_FIX32, 18>::template gather<KEEP>(base, pstride, li, c);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        u[4 * k] = (int)c[k].x; u[4 * k + 1] = (int)c[k].y; u[4 * k + 2] = (int)c[k].z; u[4 * k + 3] = (int)c[k].w;
+    }
+    u[16] = (int)c[4].x;
+    u[17] = (int)c[4].y;
+}
+
+// A 30-bit record, raw: its six integers and its exponent field.
+template <bool COH>
+__device__ __forceinline__ unsigned load_int30_raw(const char *b, int n, int i, int q[6])
+{
+    uint4 c[2];
+    if constexpr (COH)
+        gather_coherent<S_INT30>(b, n, i, c);
+    else
+        Spinor<S_INT30>::gather(b, n, i, c);
+    q[0] = sext_bits(c[0].x, 30); q[1] = sext_bits(c[0].y, 30);
+    q[2] = sext_bits(c[0].z, 30); q[3] = sext_bits(c[0].w, 30);
+    q[4] = sext_bits(c[1].x, 30); q[5] = sext_bits(c[1].y, 30);
+    return (c[0].x >> 30) | ((c[0].y >> 30) << 2) | ((c[0].z >> 30) << 4) | ((c[0].w >> 30) << 6);
+}
+
+template <bool COH, bool KEEP>
+__device__ __forceinline__ void stencil_direction_i30(const DslashArgs &a, int mu, int cmu, int lex, int cb, int po,
+                                                      size_t pstride, SiteAccI30 &acc)
+{
+    const Geom &g = a.g;
+    const int vh = g.vh, pi = 1 - po;
+    const int L = g.L[mu], st = g.stride[mu];
+    const int base = lex - cmu * st;
+    const int np1 = (base + wrap_coord(cmu + 1, L) * st) >> 1, nm1 = (base + wrap_coord(cmu - 1, L) * st) >> 1;
+    const int np3 = (base + wrap_coord(cmu + 3, L) * st) >> 1, nm3 = (base + wrap_coord(cmu - 3, L) * st) >> 1;
+    int u[18], q[6];
+    unsigned E;
+    load_link_ints<KEEP>(a.gv.fat, pstride, (po * 4 + mu) * vh + cb, u);
+    E = load_int30_raw<COH>(a.in, vh, np1, q);
+    acc.term<false>(0, u, q, E);
+    load_link_ints<KEEP>(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, u);
+    E = load_int30_raw<COH>(a.in, vh, nm1, q);
+    acc.term<true>(0, u, q, E);
+    load_link_ints<KEEP>(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, u);
+    E = load_int30_raw<COH>(a.in, vh, np3, q);
+    acc.term<false>(1, u, q, E);
+    load_link_ints<KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, u);
+    E = load_int30_raw<COH>(a.in, vh, nm3, q);
+    acc.term<true>(1, u, q, E);
+}
+
+template <int GF, int SF, typename real, int LREC>
+struct UsesIntPath {
+    static constexpr bool value = GF == G_FIX32 && SF == S_INT30 && is_ff<real>::value && LREC == 18;
+};
+
 // One output site cb: the stencil, the optional xpay, the store and, when
 // reducing, this site's Re<y, out> and |out|^2 added to rv (in the compute
 // precision; reduce_grid sums the threads).
@@ -291,6 +441,24 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
     const int x = 2 * xh + ((y + z + t + po) & 1);
     const int c[4] = {x, y, z, t};
     const int lex = 2 * cb + (x & 1);
+    real o[6];
+    if constexpr (UsesIntPath<GF, SF, real, LREC>::value) {
+        SiteAccI30 acc;
+        acc.zero();
+        if constexpr (stencil_unrolled(CFG)) {
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) stencil_direction_i30<COH, KEEP>(a, mu, c[mu], lex, cb, po, pstride, acc);
+        } else {
+#pragma unroll 1
+            for (int mu = 0; mu < 4; mu++) {
+                const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+                stencil_direction_i30<COH, KEEP>(a, mu, cmu, lex, cb, po, pstride, acc);
+            }
+        }
+        const ff sgn((float)a.sign);
+#pragma unroll
+        for (int k = 0; k < 6; k++) o[k] = acc.get(k, fsc, lsc) * sgn;
+    } else {
     SiteAcc<real> acc;
     acc.zero();
     if constexpr (stencil_unrolled(CFG)) {
@@ -313,9 +481,9 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
     }
 
     const real sf = (real)a.sign * fsc;
-    real o[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) o[k] = sf * acc.get(k);
+    }
     if (a.xpay) {
         real yv[6];
         Spinor<SF>::load(a.y, vh, cb, yv);
