@@ -28,6 +28,10 @@ __device__ __forceinline__ bool skip(const int *active)
     return active != nullptr && *(volatile const int *)active == 0;
 }
 
+__device__ __forceinline__ bool nonzero(float v) { return v != 0.0f; }
+__device__ __forceinline__ bool nonzero(double v) { return v != 0.0; }
+__device__ __forceinline__ bool nonzero(ff v) { return v.hi != 0.0f || v.lo != 0.0f; }
+
 // Sites per thread of the two per-iteration BLAS kernels: every load of a
 // thread's sites is issued before any of them is used (memory-level
 // parallelism for these short, latency-bound kernels).  Four sites a thread
@@ -140,11 +144,11 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
         for (int g = 0; g < G; g++) {
             const int j = j0 + g;
             al[g] = j < a.nslots ? (real)a.st->alpha_ring[j] : real(0);
-            if (al[g] != real(0)) Spinor<SF>::gather(a.v0 + (size_t)j * a.slot_bytes, a.n, i, cp[g]);
+            if (nonzero(al[g])) Spinor<SF>::gather(a.v0 + (size_t)j * a.slot_bytes, a.n, i, cp[g]);
         }
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            if (al[g] == real(0)) continue;
+            if (!nonzero(al[g])) continue;
             real p[6];
             Spinor<SF>::decode(cp[g], p);
 #pragma unroll
@@ -295,6 +299,10 @@ void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
+    if (sf == S_INT30 && cf == HISQ_COMPUTE_F64) {  // the increment in FP32 pairs, not on the FP64 pipe
+        launch_chained(x_flush_kernel<S_INT30, ff>, dim3(nblk(a.n)), dim3(kBlock), s, a);
+        return;
+    }
     HISQ_SF_DISPATCH(sf, cf, x_flush_kernel, dim3(nblk(a.n)), dim3(kBlock), s);
 }
 

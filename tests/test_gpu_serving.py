@@ -131,3 +131,59 @@ def test_wait_timeout_poll_and_refusals(env):
     assert done and st == hisq.HISQ_OK
     with pytest.raises(hisq.HisqError, match="EINVAL"):
         hisq.hisq_submit(ctx, gauges[VOLS[0]], 7, 0.1, b, x, True)
+
+
+def test_admission_by_budget():
+    """A context whose HBM budget holds the resident gauge fields, the workers'
+    reduction lanes and about one batch session at a time: sessions that do not
+    fit wait for memory to free up instead of failing, every request finishes
+    OK with the same bits as on an unconstrained context, and the context never
+    holds more than its budget."""
+    big = hisq.hisq_create(0)
+    d = VOLS[0]
+    fat, lng = synth.gauge_pair(d, seed=0)
+    qs = [dict(dims=d, mass=m, tol=1e-10, ms=False, seed=synth.rhs_seed(40 + i))
+          for i, m in enumerate([0.05, 0.1, 0.03, 0.2, 0.08, 0.04, 0.15, 0.06, 0.12, 0.09])]
+    try:
+        gb = {d: hisq.hisq_load_gauge(big, d, fat.cuda(), lng.cuda())}
+        ref = [submit(big, gb, q) for q in qs]
+        for t, b, x, _ in ref:
+            assert hisq.hisq_wait(big, t, 120.0)[0] == hisq.HISQ_OK
+        # resident fields and their stored copies, measured on a warm context
+        probe = hisq.hisq_create(0)
+        g0 = hisq.hisq_load_gauge(probe, d, fat.cuda(), lng.cuda())
+        b0 = synth.spinor(d, 1).cuda()
+        p = hisq.hisq_default_params()
+        p.mass, p.on_device = 0.1, 1
+        hisq.hisq_cg(probe, g0, p, b0, torch.zeros_like(b0))
+        resident = hisq.hisq_mem_used(probe)
+        hisq.hisq_destroy(probe)
+        lane = 8 * ((1 << 16) * 32 + 32) + 256 + 4 * (32 + 4096)
+        budget = resident + 2 * lane + (6 << 20)   # two workers, room for about one 8-slot session of 8^4
+        small = hisq.hisq_create(0, budget)
+        try:
+            gs = {d: hisq.hisq_load_gauge(small, d, fat.cuda(), lng.cuda())}
+            # each request on its own key (maxiter differs), so the sessions compete for memory
+            live = []
+            for i, q in enumerate(qs):
+                b = synth.spinor(d, q["seed"]).cuda()
+                x = torch.zeros_like(b)
+                t = hisq.hisq_submit(small, gs[d], hisq.HISQ_REQ_CG, q["mass"], b, x, True, tol=q["tol"],
+                                     maxiter=100000 - i)
+                live.append((t, b, x))
+            peak = 0
+            for t, b, x in live:
+                while True:
+                    peak = max(peak, hisq.hisq_mem_used(small))
+                    done, st, _ = hisq.hisq_poll(small, t)
+                    if done:
+                        assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+                        break
+                    time.sleep(0.002)
+            assert peak <= budget
+            for (t, b, x), (_, _, xr, _) in zip(live, ref):
+                np.testing.assert_array_equal(as_np(x), as_np(xr))
+        finally:
+            hisq.hisq_destroy(small)
+    finally:
+        hisq.hisq_destroy(big)
