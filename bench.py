@@ -396,7 +396,27 @@ def run_ours(args):
         formats["int20"] = {"s": ms / args.steps / 1e3, "speedup_vs_fp64": fp64_s / (ms / args.steps / 1e3),
                             "iters": infos[-1][1], "reliable_updates": infos[-1][3],
                             "true_residual": infos[-1][2], "status": hisq.STATUS_NAMES[infos[-1][0]]}
+        # the same int20 solve with the error-estimate reliable-update trigger instead of delta = 0.1
+        pd = params(SLOPPY, DELTA)
+        pd.ru_trigger = 1
+        xd = torch.zeros_like(b)
+        with torch.cuda.stream(stream):
+            hisq.hisq_cg(ctx, g, pd, b, xd)
+        xd.zero_()
+        (std, infd), secd = timed(lambda: hisq.hisq_cg(ctx, g, pd, b, xd))
+        formats["int20_error_estimate_trigger"] = {"s": secd, "iters": infd.iters,
+                                                   "reliable_updates": infd.reliable_updates,
+                                                   "true_residual": infd.true_residual,
+                                                   "status": hisq.STATUS_NAMES[std]}
+        # the full-lattice system (2m + D) x = b by even/odd reduction around the same CG
         bf = synth.spinor(DIMS, synth.rhs_seed(rank), full=True, device=dev)
+        xs = torch.zeros_like(bf)
+        with torch.cuda.stream(stream):
+            hisq.hisq_solve_full(ctx, g, params(SLOPPY, DELTA), bf, xs)
+        xs.zero_()
+        (stf2, inf2), secf = timed(lambda: hisq.hisq_solve_full(ctx, g, params(SLOPPY, DELTA), bf, xs))
+        formats["full_system_int20"] = {"s": secf, "iters": inf2.iters, "reliable_updates": inf2.reliable_updates,
+                                        "true_residual_full": inf2.true_residual, "status": hisq.STATUS_NAMES[stf2]}
         xb = torch.zeros_like(bf)
         pb = params(SLOPPY, DELTA)
         pb.l = 4
