@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
     if constexpr (RED) {  // summed by stencil_finish_kernel
         const red_t<real> r2[2] = {(red_t<real>)rv[0], (red_t<real>)rv[1]};
-        store_block_partial<2, red_t<real>>(r2, a.red);
+        store_block_partial<2>(r2, a.red);
     }
 }
 
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(1024) stencil_finish_kernel(RedBuf red, unsign
     pdl_launch_dependents();
     if (active != nullptr && *(volatile const int *)active == 0) return;
     __shared__ double tot[2];
-    sum_partials<2, red_t<real>>(red, nblocks, tot);
+    sum_partials<2, part_t<real>>(red, nblocks, tot);
     if (threadIdx.x == 0) {
         red.result[0] = tot[0];
         red.result[1] = tot[1];

@@ -17,10 +17,13 @@
 
 namespace hisq {
 
-// Type of the per-block sums: FP32 pairs are summed as FP64 (one conversion
-// per thread; shuffles and partials take plain scalars).
+// Type of a thread's sums: the compute type (FP32 pairs stay pairs; their
+// block sums run in pair arithmetic, see below).  Type of the block partials:
+// the compute type, FP64 for pairs (hi + lo is exact in FP64).
 template <typename real>
-using red_t = std::conditional_t<is_ff<real>::value, double, real>;
+using red_t = real;
+template <typename real>
+using part_t = std::conditional_t<is_ff<real>::value, double, real>;
 
 template <int NR, typename T>
 __device__ __forceinline__ void warp_sum(T v[NR])
@@ -190,6 +193,73 @@ __device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
     }
     __syncthreads();
     return true;
+}
+
+// FP32-pair values (the FP64-class kernels): the block sums them in pair
+// arithmetic (TwoSum at every level of the same fixed tree, nothing on the
+// narrow FP64 pipe) and stores one FP64 partial, hi + lo, exact; the last
+// block sums the partials in FP64.
+template <int NR>
+__device__ __forceinline__ void block_sum_pairs(const ff vin[NR], FF v[NR])
+{
+    __shared__ FF sh[32][NR];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; k++) v[k] = FF{vin[k].hi, vin[k].lo};
+    warp_sum_ff<NR>(v);
+    __syncthreads();  // sh may be reused from a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NR; k++) sh[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) v[k] = lane < nw ? sh[lane][k] : FF{0.0f, 0.0f};
+        warp_sum_ff<NR>(v);
+    }
+}
+
+template <int NR>
+__device__ bool reduce_grid(const ff vin[NR], const RedBuf &rb, double *tot)
+{
+    __shared__ int is_last;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    FF v[NR];
+    block_sum_pairs<NR>(vin, v);
+    if (threadIdx.x == 0) {
+        double *part = reinterpret_cast<double *>(rb.partials);
+#pragma unroll
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = (double)v[k].hi + (double)v[k].lo;
+        __threadfence();
+        const unsigned prev = atomicAdd(rb.counter, 1u);
+        is_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    sum_partials<NR, double>(rb, nblocks, tot);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k++) rb.result[k] = tot[k];
+        *rb.counter = 0u;
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int NR>
+__device__ void store_block_partial(const ff vin[NR], const RedBuf &rb)
+{
+    FF v[NR];
+    block_sum_pairs<NR>(vin, v);
+    if (threadIdx.x == 0) {
+        double *part = reinterpret_cast<double *>(rb.partials);
+        const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = (double)v[k].hi + (double)v[k].lo;
+    }
 }
 
 // Blocks of one full wave of a kernel on the current device: the grid of a
