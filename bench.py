@@ -427,6 +427,31 @@ def run_ours(args):
         formats["bicgstab4_int20_full_M"] = {"s": secb, "cycles": infb.iters, "matvecs": infb.matvecs,
                                             "reliable_updates": infb.reliable_updates,
                                             "true_residual": infb.true_residual, "status": hisq.STATUS_NAMES[stb]}
+        # the headline solve with the long links in the other storages (Sec. 1: 18 reals, 8 reals; 13 reals
+        # for U(3) links): time to solution, and the stencil's passes in a short profiled solve
+        for recon in (18, 13, 8):
+            pr = params(SLOPPY, DELTA, recon=recon)
+            xr = torch.zeros_like(b)
+            with torch.cuda.stream(stream):
+                hisq.hisq_cg(ctx, g, pr, b, xr)
+            xr.zero_()
+            (str_, infr), secr = timed(lambda: hisq.hisq_cg(ctx, g, pr, b, xr))
+            hisq.hisq_profile_reset(ctx)
+            hisq.hisq_profile_select(ctx, 1 << hisq.HISQ_PROF_STENCIL)
+            hisq.hisq_profile_enable(ctx, True)
+            ps = params(SLOPPY, DELTA, recon=recon)
+            ps.maxiter = 64
+            xr.zero_()
+            with torch.cuda.stream(stream):
+                hisq.hisq_cg(ctx, g, ps, b, xr)
+            sr = hisq.hisq_profile_read(ctx, hisq.HISQ_PROF_STENCIL)
+            hisq.hisq_profile_enable(ctx, False)
+            hisq.hisq_profile_select(ctx, 0xFFFFFFFF)
+            formats[f"int20_long_r{recon}"] = {
+                "s": secr, "iters": infr.iters, "reliable_updates": infr.reliable_updates,
+                "true_residual": infr.true_residual, "status": hisq.STATUS_NAMES[str_],
+                "stencil_us_per_pass": 1e3 * sr.ms / max(sr.launches, 1),
+                "stencil_gbs": sr.bytes / max(sr.ms, 1e-9) / 1e6}
 
     # the FP64 baseline's stencil alone: a short profiled FP64 solve (its passes timed by events)
     hisq.hisq_profile_reset(ctx)

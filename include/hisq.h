@@ -89,14 +89,24 @@ typedef enum { HISQ_COMPUTE_F32 = 0, HISQ_COMPUTE_F64 = 1 } hisq_compute_fmt;
  * 18 -> 12 reals by SU(3) unitarity).  Supported combinations:
  *   F64/F64/F64, F32/F32/F32, FIX16/HALF16/F32, FIX16/INT20/F32,
  *   FIX32/INT30/F64, FIX32/INT30/F32;
- * fat_recon must be 18 (smeared fat links are not unitary); long_recon 18 or
- * 12 (12 needs long links that are a sign times SU(3), checked at load). */
+ * fat_recon must be 18 (smeared fat links are not unitary); long_recon 18,
+ * 12, 13 or 8:
+ *   12: rows 0 and 1; needs long links that are a sign times SU(3) (checked
+ *       at load, EINVAL otherwise);
+ *   13: rows 0, 1 and arg(det U)/pi; needs unitary long links (U(3));
+ *   8:  arg V00, arg V20, V01, V02, V10 of V = sign * U in SU(3), rebuilt
+ *       from unitarity and det V = 1; needs a sign times SU(3), and the first
+ *       use of a format builds the copy, rebuilds it in FP64 and returns
+ *       EINVAL when its root-mean-square error per real exceeds 4 storage
+ *       steps or is not finite (links with V00 = 1, e.g. a free field);
+ *   13 and 8 are supported on FP32-compute triplets with FIX16 or F32 links
+ *   and in the single-right-hand-side solvers (EINVAL elsewhere). */
 typedef struct {
     int32_t gauge;      /* hisq_gauge_fmt */
     int32_t spinor;     /* hisq_spinor_fmt */
     int32_t compute;    /* hisq_compute_fmt */
     int32_t fat_recon;  /* 18 */
-    int32_t long_recon; /* 18 or 12 */
+    int32_t long_recon; /* 18, 12, 13 or 8 */
 } hisq_prec;
 
 typedef struct hisq_ctx hisq_ctx;

@@ -231,10 +231,12 @@ hisq_status check_prec(hisq_ctx *c, const hisq_prec &p)
         return fail(c, HISQ_EINVAL, "unsupported precision triplet gauge=%d spinor=%d compute=%d", p.gauge,
                     p.spinor, p.compute);
     if (p.fat_recon != 18) return fail(c, HISQ_EINVAL, "fat links must be stored with 18 reals");
-    if (p.long_recon != 18 && p.long_recon != 12 && p.long_recon != 13)
-        return fail(c, HISQ_EINVAL, "long_recon must be 18, 13 or 12");
-    if (p.long_recon == 13 && !(p.compute == HISQ_COMPUTE_F32 && (p.gauge == G_FIX16 || p.gauge == G_F32)))
-        return fail(c, HISQ_EINVAL, "13-real long links need an FP32-compute triplet with 16-bit or FP32 links");
+    if (p.long_recon != 18 && p.long_recon != 12 && p.long_recon != 13 && p.long_recon != 8)
+        return fail(c, HISQ_EINVAL, "long_recon must be 18, 13, 12 or 8");
+    if ((p.long_recon == 13 || p.long_recon == 8) &&
+        !(p.compute == HISQ_COMPUTE_F32 && (p.gauge == G_FIX16 || p.gauge == G_F32)))
+        return fail(c, HISQ_EINVAL, "%d-real long links need an FP32-compute triplet with 16-bit or FP32 links",
+                    p.long_recon);
     return HISQ_OK;
 }
 
@@ -251,6 +253,9 @@ static hisq_status get_copy(hisq_ctx *c, hisq_gauge *g, bool lng, int gf, int re
                     lng ? "long" : "fat");
     if (recon == 13 && !(lng && g->lng_u3_ok))
         return fail(c, HISQ_EINVAL, "%s links are not unitary: 13-real compression refused", lng ? "long" : "fat");
+    if (recon == 8 && !(lng && g->lng_r12_ok))
+        return fail(c, HISQ_EINVAL, "%s links are not a sign times SU(3): 8-real compression refused",
+                    lng ? "long" : "fat");
     LinkCopy lc;
     lc.gf = gf;
     lc.recon = recon;
@@ -264,10 +269,38 @@ static hisq_status get_copy(hisq_ctx *c, hisq_gauge *g, bool lng, int gf, int re
         LaunchScope ls(c, c->stream, PROF_CONVERT, 0.0);
         launch_quantise_links(g->geom, gf, recon, lng ? g->lng64 : g->fat64, inv, lc.ptr, c->stream);
     }
-    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         ctx_free(c, lc.ptr, lc.bytes);
         return cuda_fail(c, e, "quantise links");
+    }
+    if (recon == 8) {
+        // the 8-real rebuild divides by N = 1 - |V00|^2 and takes sqrt(N - |V10|^2), so single links near
+        // those points come back far off; refuse a field whose rebuilt links are off by more than 4 storage
+        // steps per real in the root mean square (or not finite: N = 0, e.g. a free field)
+        const double step = gf == G_FIX16 ? 0x1p-15 : gf == G_FIX32 ? 0x1p-31 : gf == G_F32 ? 0x1p-24 : 0x1p-52;
+        const double el = (gf == G_FIX16 || gf == G_FIX32) ? gmax / qmax : 1.0;
+        const double an = (gf == G_FIX16 || gf == G_FIX32) ? 1.0 / qmax : 1.0;
+        double *dev = cur_red(c).result, err[2] = {0.0, 0.0};
+        e = cudaMemsetAsync(dev, 0, 2 * sizeof(double), c->stream);
+        if (e == cudaSuccess) {
+            launch_r8_check(g->geom, gf, g->lng64, lc.ptr, el, an, dev, c->stream);
+            e = cudaMemcpyAsync(err, dev, sizeof err, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            ctx_free(c, lc.ptr, lc.bytes);
+            return cuda_fail(c, e, "8-real link check");
+        }
+        const double rms = std::sqrt(err[1] / (18.0 * 8.0 * (double)g->geom.vh));
+        const double bound = 4.0 * step * std::max(gmax, 1.0);
+        if (!(rms <= bound)) {
+            ctx_free(c, lc.ptr, lc.bytes);
+            return fail(c, HISQ_EINVAL,
+                        "8-real long links come back %.2e off in the root mean square (bound %.2e, largest %.2e): "
+                        "too many links where the 8-real rebuild is ill-conditioned; use 12 or 13 reals",
+                        rms, bound, err[0]);
+        }
     }
     copies.push_back(lc);
     *out = lc.ptr;

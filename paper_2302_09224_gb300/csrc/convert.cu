@@ -149,6 +149,46 @@ __global__ void quantise_kernel(Geom g, const double *links, double inv, char *o
     const double *src = links + ((int64_t)mu * 2 * vh + lex) * 18;
     const size_t pstride = (size_t)n * 16;
     constexpr int n16 = link_n16(GF, RECON), tail = link_tail(GF, RECON);
+    if constexpr (RECON == 8) {
+        // 8 reals of V = sign U (V in SU(3); sign: the long link's staggered phase and boundary
+        // sign): arg V00 / pi, arg V20 / pi, V01, V02, V10.  Angles are stored as the format
+        // stores a real in [-1, 1] (fixed point: rint(t qmax)), elements as every other element.
+        int ps = 0;
+        const int cc[4] = {x, y, z, t};
+        for (int nu = 0; nu < mu; nu++) ps += cc[nu];
+        double sg = (ps & 1) ? -1.0 : 1.0;
+        if (g.antiperiodic_t && mu == 3 && t + 3 >= g.L[3]) sg = -sg;
+        const double inv_pi = 0.31830988618379067154;
+        const double pv[8] = {atan2(sg * src[1], sg * src[0]) * inv_pi, atan2(sg * src[13], sg * src[12]) * inv_pi,
+                              sg * src[2], sg * src[3], sg * src[4], sg * src[5], sg * src[6], sg * src[7]};
+        if constexpr (GF == G_F64) {
+            for (int k = 0; k < 4; k++)
+                reinterpret_cast<double2 *>(out + k * pstride)[li] = make_double2(pv[2 * k], pv[2 * k + 1]);
+        } else if constexpr (GF == G_F32) {
+            for (int k = 0; k < 2; k++)
+                reinterpret_cast<float4 *>(out + k * pstride)[li] =
+                    make_float4((float)pv[4 * k], (float)pv[4 * k + 1], (float)pv[4 * k + 2], (float)pv[4 * k + 3]);
+        } else {
+            constexpr double qmax = GF == G_FIX16 ? 32767.0 : 2147483647.0;
+            int q[8];
+            for (int k = 0; k < 8; k++) {
+                double v = rint(__dmul_rn(pv[k], k < 2 ? qmax : inv));
+                q[k] = (int)fmin(qmax, fmax(-qmax, v));
+            }
+            if constexpr (GF == G_FIX16) {
+                int4 w;
+                w.x = (int)((q[0] & 0xffff) | ((uint32_t)q[1] << 16));
+                w.y = (int)((q[2] & 0xffff) | ((uint32_t)q[3] << 16));
+                w.z = (int)((q[4] & 0xffff) | ((uint32_t)q[5] << 16));
+                w.w = (int)((q[6] & 0xffff) | ((uint32_t)q[7] << 16));
+                reinterpret_cast<int4 *>(out)[li] = w;
+            } else {
+                reinterpret_cast<int4 *>(out)[li] = make_int4(q[0], q[1], q[2], q[3]);
+                reinterpret_cast<int4 *>(out + pstride)[li] = make_int4(q[4], q[5], q[6], q[7]);
+            }
+        }
+        return;
+    }
     if constexpr (GF == G_F64) {
         for (int k = 0; k < RECON / 2; k++)
             reinterpret_cast<double2 *>(out + k * pstride)[li] = make_double2(src[2 * k], src[2 * k + 1]);
@@ -220,6 +260,101 @@ __global__ void quantise_kernel(Geom g, const double *links, double inv, char *o
             reinterpret_cast<short *>(pp)[li] = (short)rint(t * 32767.0);
         else
             reinterpret_cast<int *>(pp)[li] = (int)rint(t * 2147483647.0);
+    }
+}
+
+// Error of the long links of a field stored with 8 reals, |U_stored - U| per
+// real: the largest (out[0]) and the sum of squares (out[1]).  The stored
+// parameters are decoded and V rebuilt in FP64 (the device rebuilds in the
+// compute precision), so the result is the storage's own error, amplified
+// where the rebuild is ill-conditioned (N = 1 - |V00|^2 or |V20| small).
+// el: the element scale (gmax/qmax or 1), an: the angle scale (1/qmax or 1).
+template <int GF>
+__global__ void r8_check_kernel(Geom g, const double *links, const char *stored, double el, double an, double *out)
+{
+    const int vh = g.vh;
+    const int64_t n = 8LL * vh;
+    const size_t pstride = (size_t)n * 16;
+    double m = 0.0, q = 0.0;
+    for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < n; li += (int64_t)gridDim.x * blockDim.x) {
+        const int cb = (int)(li % vh);
+        const int pm = (int)(li / vh);
+        const int par = pm >> 2, mu = pm & 3;
+        int r = cb / g.xh;
+        const int xh = cb - r * g.xh;
+        const int y = r % g.L[1];
+        r /= g.L[1];
+        const int z = r % g.L[2];
+        const int t = r / g.L[2];
+        const int x = 2 * xh + ((y + z + t + par) & 1);
+        const int lex = 2 * cb + (x & 1);
+        const double *src = links + ((int64_t)mu * 2 * vh + lex) * 18;
+        int ps = 0;
+        const int cc[4] = {x, y, z, t};
+        for (int nu = 0; nu < mu; nu++) ps += cc[nu];
+        double sg = (ps & 1) ? -1.0 : 1.0;
+        if (g.antiperiodic_t && mu == 3 && t + 3 >= g.L[3]) sg = -sg;
+        double p[8];
+        if constexpr (GF == G_F64) {
+            for (int k = 0; k < 4; k++) {
+                const double2 v = reinterpret_cast<const double2 *>(stored + k * pstride)[li];
+                p[2 * k] = v.x;
+                p[2 * k + 1] = v.y;
+            }
+        } else if constexpr (GF == G_F32) {
+            for (int k = 0; k < 2; k++) {
+                const float4 v = reinterpret_cast<const float4 *>(stored + k * pstride)[li];
+                p[4 * k] = v.x; p[4 * k + 1] = v.y; p[4 * k + 2] = v.z; p[4 * k + 3] = v.w;
+            }
+        } else if constexpr (GF == G_FIX16) {
+            const int4 w = reinterpret_cast<const int4 *>(stored)[li];
+            const int ws[4] = {w.x, w.y, w.z, w.w};
+            for (int k = 0; k < 4; k++) {
+                p[2 * k] = (double)(short)(ws[k] & 0xffff);
+                p[2 * k + 1] = (double)(ws[k] >> 16);
+            }
+        } else {
+            const int4 a = reinterpret_cast<const int4 *>(stored)[li], b = reinterpret_cast<const int4 *>(stored + pstride)[li];
+            p[0] = a.x; p[1] = a.y; p[2] = a.z; p[3] = a.w; p[4] = b.x; p[5] = b.y; p[6] = b.z; p[7] = b.w;
+        }
+        const double t1 = p[0] * an, t2 = p[1] * an;
+        const double a2r = p[2] * el, a2i = p[3] * el, a3r = p[4] * el, a3i = p[5] * el, b1r = p[6] * el, b1i = p[7] * el;
+        const double N = a2r * a2r + a2i * a2i + a3r * a3r + a3i * a3i;
+        const double ra = sqrt(fmax(1.0 - N, 0.0)), rc = sqrt(fmax(N - b1r * b1r - b1i * b1i, 0.0));
+        double s1, c1, s2, c2;
+        sincospi(t1, &s1, &c1);
+        sincospi(t2, &s2, &c2);
+        const double a1r = ra * c1, a1i = ra * s1, cr = rc * c2, ci = rc * s2;
+        // b2 = -(conj(a1) a2 b1 + conj(a3) conj(c1)) / N, b3 = (conj(a2) conj(c1) - conj(a1) a3 b1) / N
+        const double a1a2r = a1r * a2r + a1i * a2i, a1a2i = a1r * a2i - a1i * a2r;    // conj(a1) a2
+        const double t3r = a1a2r * b1r - a1a2i * b1i, t3i = a1a2r * b1i + a1a2i * b1r;  // * b1
+        const double t4r = a3r * cr - a3i * ci, t4i = -(a3r * ci + a3i * cr);           // conj(a3) conj(c1)
+        const double b2r = -(t3r + t4r) / N, b2i = -(t3i + t4i) / N;
+        const double t5r = a2r * cr - a2i * ci, t5i = -(a2r * ci + a2i * cr);           // conj(a2) conj(c1)
+        const double a1a3r = a1r * a3r + a1i * a3i, a1a3i = a1r * a3i - a1i * a3r;      // conj(a1) a3
+        const double t6r = a1a3r * b1r - a1a3i * b1i, t6i = a1a3r * b1i + a1a3i * b1r;  // * b1
+        const double b3r = (t5r - t6r) / N, b3i = (t5i - t6i) / N;
+        // c2 = conj(a3 b1 - a1 b3), c3 = conj(a1 b2 - a2 b1)
+        const double c2r = (a3r * b1r - a3i * b1i) - (a1r * b3r - a1i * b3i);
+        const double c2i = -((a3r * b1i + a3i * b1r) - (a1r * b3i + a1i * b3r));
+        const double c3r = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
+        const double c3i = -((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
+        const double V[18] = {a1r, a1i, a2r, a2i, a3r, a3i, b1r, b1i, b2r, b2i, b3r, b3i, cr, ci, c2r, c2i, c3r, c3i};
+        for (int k = 0; k < 18; k++) {
+            const double d = fabs(sg * V[k] - src[k]);
+            m = (d > m || d != d) ? d : m;
+            q += d * d;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, m, off);
+        m = (o > m || o != o) ? o : m;
+        q += __shfl_down_sync(0xffffffffu, q, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(out, m);
+        atomicAdd(out + 1, q);
     }
 }
 
@@ -317,6 +452,18 @@ void launch_absmax(int64_t n, const double *x, double *out, cudaStream_t s)
     absmax_kernel<<<nb, kBlock, 0, s>>>(n, x, out);
 }
 
+void launch_r8_check(const Geom &g, int gf, const double *links, const char *stored, double el, double an,
+                     double *out, cudaStream_t s)
+{
+    const int nb = (int)std::min<int64_t>(nblocks(8LL * g.vh, kBlock), 4096);
+    switch (gf) {
+    case G_F64: r8_check_kernel<G_F64><<<nb, kBlock, 0, s>>>(g, links, stored, el, an, out); break;
+    case G_F32: r8_check_kernel<G_F32><<<nb, kBlock, 0, s>>>(g, links, stored, el, an, out); break;
+    case G_FIX16: r8_check_kernel<G_FIX16><<<nb, kBlock, 0, s>>>(g, links, stored, el, an, out); break;
+    case G_FIX32: r8_check_kernel<G_FIX32><<<nb, kBlock, 0, s>>>(g, links, stored, el, an, out); break;
+    }
+}
+
 void launch_u3_check(const Geom &g, const double *links, double *out, cudaStream_t s)
 {
     const int nb = (int)std::min<int64_t>(nblocks(8LL * g.vh, kBlock), 4096);
@@ -340,6 +487,13 @@ void launch_quantise_links(const Geom &g, int gf, int recon, const double *links
         case G_F32: Q(G_F32, 18); break;
         case G_FIX16: Q(G_FIX16, 18); break;
         case G_FIX32: Q(G_FIX32, 18); break;
+        }
+    } else if (recon == 8) {
+        switch (gf) {
+        case G_F64: Q(G_F64, 8); break;
+        case G_F32: Q(G_F32, 8); break;
+        case G_FIX16: Q(G_FIX16, 8); break;
+        case G_FIX32: Q(G_FIX32, 8); break;
         }
     } else if (recon == 13) {
         switch (gf) {

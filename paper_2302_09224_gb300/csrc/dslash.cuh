@@ -219,6 +219,42 @@ __device__ __forceinline__ void rebuild_row2_r13(real U[18], real scale)
     rebuild_row2_phase(U, scale * cp, scale * sp);
 }
 
+// An 8-real link (arg V00/pi, arg V20/pi, V01, V02, V10 of V = sign U, V in
+// SU(3)) rebuilt in registers from unitarity and det V = 1: N = |V01|^2 +
+// |V02|^2, V00 = sqrt(1 - N) e^{i pi t1}, V20 = sqrt(N - |V10|^2) e^{i pi t2},
+// V11 = -(conj(V00) V01 V10 + conj(V02) conj(V20)) / N, V12 = (conj(V01)
+// conj(V20) - conj(V00) V02 V10) / N, V21 = conj(V02 V10 - V00 V12), V22 =
+// conj(V00 V11 - V01 V10).  U[0..7] holds the stored reals, es and as the
+// element and angle scales (fixed point: the field's scale and 1/qmax); U
+// receives V in true units.
+__device__ __forceinline__ void rebuild_r8(float U[18], float es, float as)
+{
+    const float t1 = U[0] * as, t2 = U[1] * as;
+    const float a2r = U[2] * es, a2i = U[3] * es, a3r = U[4] * es, a3i = U[5] * es, b1r = U[6] * es, b1i = U[7] * es;
+    const float N = a2r * a2r + a2i * a2i + a3r * a3r + a3i * a3i;
+    const float ra = sqrtf(fmaxf(1.0f - N, 0.0f)), rc = sqrtf(fmaxf(N - b1r * b1r - b1i * b1i, 0.0f));
+    float s1, c1, s2, c2;
+    sincospif(t1, &s1, &c1);
+    sincospif(t2, &s2, &c2);
+    const float inv = 1.0f / N;
+    const float a1r = ra * c1, a1i = ra * s1, cr = rc * c2, ci = rc * s2;
+    const float a1a2r = a1r * a2r + a1i * a2i, a1a2i = a1r * a2i - a1i * a2r;     // conj(a1) a2
+    const float t3r = a1a2r * b1r - a1a2i * b1i, t3i = a1a2r * b1i + a1a2i * b1r;  // * b1
+    const float t4r = a3r * cr - a3i * ci, t4i = -(a3r * ci + a3i * cr);            // conj(a3) conj(c1)
+    const float b2r = -(t3r + t4r) * inv, b2i = -(t3i + t4i) * inv;
+    const float t5r = a2r * cr - a2i * ci, t5i = -(a2r * ci + a2i * cr);            // conj(a2) conj(c1)
+    const float a1a3r = a1r * a3r + a1i * a3i, a1a3i = a1r * a3i - a1i * a3r;       // conj(a1) a3
+    const float t6r = a1a3r * b1r - a1a3i * b1i, t6i = a1a3r * b1i + a1a3i * b1r;   // * b1
+    const float b3r = (t5r - t6r) * inv, b3i = (t5i - t6i) * inv;
+    U[0] = a1r; U[1] = a1i; U[2] = a2r; U[3] = a2i; U[4] = a3r; U[5] = a3i;
+    U[6] = b1r; U[7] = b1i; U[8] = b2r; U[9] = b2i; U[10] = b3r; U[11] = b3i;
+    U[12] = cr; U[13] = ci;
+    U[14] = (a3r * b1r - a3i * b1i) - (a1r * b3r - a1i * b3i);
+    U[15] = -((a3r * b1i + a3i * b1r) - (a1r * b3i + a1i * b3r));
+    U[16] = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
+    U[17] = -((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
+}
+
 template <int GF, int SF, typename real, int LREC, bool COH = false, bool KEEP = false>
 __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, int cmu, int c3, int lex, int cb,
                                                   int po, size_t pstride, real lsc, real ratio, int phase_sum,
@@ -252,10 +288,19 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     } else if constexpr (LREC == 13) {
         rebuild_row2_r13(U, lsc);
     }
+    // an 8-real link comes back in true units with its sign removed: the spinor takes the sign and 1/fsc
+    if constexpr (LREC == 8) rebuild_r8(U, lsc, kScaled ? 1.0f / 32767.0f : 1.0f);
     load_neighbour<real, SF, COH>(a.in, vh, np3, s);
-    if constexpr (kScaled)
+    if constexpr (LREC == 8) {
+        const real r8s = kScaled ? ratio / lsc : real(1);
+        const bool flip = g.antiperiodic_t && mu == 3 && c3 + 3 >= L;
+        const real f = ((phase_sum & 1) != flip) ? -r8s : r8s;
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] *= f;
+    } else if constexpr (kScaled) {
 #pragma unroll
         for (int k = 0; k < 6; k++) s[k] *= ratio;
+    }
     acc.add(U, s);
 
     Link<GF, LREC>::template load<real, KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, U);
@@ -265,10 +310,18 @@ __device__ __forceinline__ void stencil_direction(const DslashArgs &a, int mu, i
     } else if constexpr (LREC == 13) {
         rebuild_row2_r13(U, lsc);
     }
+    if constexpr (LREC == 8) rebuild_r8(U, lsc, kScaled ? 1.0f / 32767.0f : 1.0f);
     load_neighbour<real, SF, COH>(a.in, vh, nm3, s);
-    if constexpr (kScaled)
+    if constexpr (LREC == 8) {
+        const real r8s = kScaled ? ratio / lsc : real(1);
+        const bool flip = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
+        const real f = ((phase_sum & 1) != flip) ? -r8s : r8s;
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] *= f;
+    } else if constexpr (kScaled) {
 #pragma unroll
         for (int k = 0; k < 6; k++) s[k] *= ratio;
+    }
     acc.adj_sub(U, s);
 }
 
@@ -576,12 +629,19 @@ void launch_any(int cfg, const DslashArgs &a, cudaStream_t s)
 template <int GF, int SF, typename real>
 bool launch_dslash_t(int long_recon, bool reduce, int cfg, const DslashArgs &a, cudaStream_t s)
 {
-    if (long_recon == 13) {  // FP32 compute with 16-bit or FP32 links
+    if (long_recon == 13 || long_recon == 8) {  // FP32 compute with 16-bit or FP32 links
         if constexpr (std::is_same<real, float>::value && (GF == G_FIX16 || GF == G_F32)) {
-            if (reduce)
-                launch_any<GF, SF, real, 13, true>(cfg, a, s);
-            else
-                launch_any<GF, SF, real, 13, false>(cfg, a, s);
+            if (long_recon == 13) {
+                if (reduce)
+                    launch_any<GF, SF, real, 13, true>(cfg, a, s);
+                else
+                    launch_any<GF, SF, real, 13, false>(cfg, a, s);
+            } else {
+                if (reduce)
+                    launch_any<GF, SF, real, 8, true>(cfg, a, s);
+                else
+                    launch_any<GF, SF, real, 8, false>(cfg, a, s);
+            }
             return true;
         }
         return false;

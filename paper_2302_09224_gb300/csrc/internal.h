@@ -264,6 +264,11 @@ void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out
 // out_max / out_maxdev must be zeroed before the launch (atomic max)
 void launch_absmax(int64_t n, const double *x, double *out_max, cudaStream_t s);
 void launch_r12_check(const Geom &g, const double *links, int k, double *out_maxdev, cudaStream_t s);
+// FP64 rebuild error of a field stored with 8 reals: out[0] the largest
+// element error, out[1] the sum of squared element errors (both zeroed before
+// the launch); el / an: element and angle scales
+void launch_r8_check(const Geom &g, int gf, const double *links, const char *stored, double el, double an,
+                     double *out, cudaStream_t s);
 // max over links of |U U^+ - 1| (out_maxdev zeroed before the launch)
 void launch_u3_check(const Geom &g, const double *links, double *out_maxdev, cudaStream_t s);
 void launch_quantise_links(const Geom &g, int gf, int recon, const double *links, double inv, char *out,

@@ -329,3 +329,90 @@ def test_r13_u3_links_and_refusals(ctx, orc, name):
             hisq.hisq_cg(ctx, g, p, b2, torch.zeros_like(b2))
     finally:
         hisq.hisq_free_gauge(ctx, g)
+
+
+def rotated_long_links(lng):
+    """Long links times one fixed SU(3) matrix on the left whose elements all have |.|^2 = 1/3: still a
+    sign times SU(3), but far from diagonal, where the 8-real rebuild is well conditioned."""
+    w = np.exp(2j * np.pi / 3)
+    f = np.array([[1, 1, 1], [1, w, w * w], [1, w * w, w]]) / np.sqrt(3)
+    f = f / np.linalg.det(f) ** (1.0 / 3.0)
+    u = lng[..., 0] + 1j * lng[..., 1]
+    r = np.einsum("ij,...jk->...ik", f, u)
+    return np.ascontiguousarray(np.stack([r.real, r.imag], axis=-1))
+
+
+def run_fields(ctx, dims, anti, fat, lng, name, recon, parity, a):
+    flags = hisq.HISQ_GAUGE_ANTIPERIODIC_T if anti else 0
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda(), flags)
+    try:
+        full = parity == 2
+        x = synth.spinor(dims, 1000, full=full).numpy()
+        y = synth.spinor(dims, 1001, full=full).numpy()
+        xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        out = torch.empty_like(xd)
+        hisq.hisq_dslash(ctx, g, hisq.prec(name, recon), parity, a, yd if a else None, xd, out, True)
+        torch.cuda.synchronize()
+        return x, y, out.cpu().numpy()
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+
+
+BOUND_EXACT_R8 = {"f32": 2e-6, "half": 1e-3, "int20": 4e-4}
+BOUND_EMUL_R8 = {"f32": 1e-5, "half": 6e-5, "int20": 1e-5}
+
+
+@pytest.mark.parametrize("name", ["f32", "half", "int20"])
+@pytest.mark.parametrize("rotate", [True, False])
+@pytest.mark.parametrize("dims,anti,parity,a", CASES)
+def test_dslash_r8_parity(ctx, orc, name, rotate, dims, anti, parity, a):
+    """8-real long links (Sec. 1: 18 -> 8; V = sign U parametrised by arg V00, arg V20, V01, V02, V10 and
+    rebuilt in registers from unitarity and det V = 1), on the synthetic long links (near the identity) and
+    on the same links rotated far from it: against the oracle's emulation of the same storage within the
+    compute rounding, and against the exact stencil."""
+    fat, lng = lattice(dims, anti)
+    if rotate:
+        lng = rotated_long_links(lng)
+    x, y, out = run_fields(ctx, dims, anti, fat, lng, name, 8, parity, a)
+    exact = oracle_apply(orc, dims, fat, lng, parity, a, x, y)
+    assert rel(out, exact) <= BOUND_EXACT_R8[name], (name, rel(out, exact))
+    fe = orc.gauge_emulate(dims, fat, GAUGE[name], 18, long_link=False, antiperiodic_t=anti)
+    le = orc.gauge_emulate(dims, lng, GAUGE[name], 8, long_link=True, antiperiodic_t=anti)
+    xe = orc.spinor_emulate(x, SPINOR[name]).reshape(x.shape)
+    ye = orc.spinor_emulate(y, SPINOR[name]).reshape(y.shape)
+    emul = oracle_apply(orc, dims, fe, le, parity, a, xe, ye)
+    assert rel(out, emul) <= BOUND_EMUL_R8[name], (name, rel(out, emul))
+
+
+def test_r8_refusals_and_solve(ctx, orc):
+    """8 reals are refused for U(3) long links and for the free field (V00 = 1: N = 0, no rebuild), and on
+    FP64 or 30-bit triplets; a CG solve with 8-real long links meets the oracle's true residual."""
+    dims = (4, 6, 4, 8)
+    fat, lng = lattice(dims, False)
+    x = synth.spinor(dims, 1000)
+    free = synth.gauge_field(dims, "long", seed=0, eps=0.0).numpy()
+    for bad in (u3_long_links(lng, 5), free):
+        g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(bad).cuda())
+        try:
+            out = torch.empty_like(x).cuda()
+            with pytest.raises(hisq.HisqError, match="8-real"):
+                hisq.hisq_dslash(ctx, g, hisq.prec("int20", 8), 0, 0.0, None, x.cuda(), out, True)
+        finally:
+            hisq.hisq_free_gauge(ctx, g)
+    g = hisq.hisq_load_gauge(ctx, dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    try:
+        out = torch.empty_like(x).cuda()
+        for bad in ("f64", "int30"):
+            with pytest.raises(hisq.HisqError, match="EINVAL"):
+                hisq.hisq_dslash(ctx, g, hisq.prec(bad, 8), 0, 0.0, None, x.cuda(), out, True)
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.on_device = 0.05, 1e-10, 1
+        p.sloppy = hisq.prec("int20", 8)
+        b = x.cuda()
+        sol = torch.zeros_like(b)
+        st, info = hisq.hisq_cg(ctx, g, p, b, sol)
+        assert st == hisq.HISQ_OK
+        r = x.numpy() - orc.mee(dims, fat, lng, 0.05, sol.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(x.numpy()) <= 1e-10
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
