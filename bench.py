@@ -883,7 +883,7 @@ def main():
                     help="reference arm: algorithmic bytes of one GPU solve")
     ap.add_argument("--stencil", default=None, help="LX,LY,LZ,LT: only run stencil applications (profiling)")
     ap.add_argument("--prec", default="int20")
-    ap.add_argument("--recon", type=int, default=12, help="long-link storage (12 or 18) of --solve")
+    ap.add_argument("--recon", type=int, default=12, help="long-link storage (18, 13, 12 or 8 reals) of --solve")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--stencil-config", default="",
                     help="force the stencil launch shapes: A (both passes) or A,B (plain, reducing), each 0..4")
