@@ -2,7 +2,8 @@
 // (Sec. 3.1), each a single pass over its vectors in the sloppy storage
 // format with the reduction it needs fused in (deterministic; see reduce_grid
 // for the precision of each stage):
-//   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta)
+//   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta;
+//                 for the 30-bit FP64-class triplet from the stored records)
 //   p_update      p' <- r + beta p       (into the next ring slot)
 //   x_flush       x_hi <- x_hi + sum_j alpha_j p_j   (buffered gradient vectors)
 //   true_residual r_hi <- b - A x_hi (FP64), r <- r_hi (sloppy),
@@ -64,6 +65,29 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
         for (int u = 0; u < U; u++) {
             const int i = i0 + u * blockDim.x;
             if (i >= a.n) continue;
+            if constexpr (SF == S_INT30 && is_ff<real>::value) {
+                // FP64-class: the update in FP32 pairs; |r|^2 and Re<r_new, r_old> exactly in integers
+                // from the stored 30-bit records (products of 30-bit integers, sums below 2^62)
+                int32_t qr[6];
+                const uint32_t Er = Spinor<S_INT30>::raw(cr[u], qr);
+                ff r[6], ap[6], rn[6];
+                Spinor<S_INT30>::decode(cr[u], r);
+                Spinor<S_INT30>::decode(ca[u], ap);
+#pragma unroll
+                for (int k = 0; k < 6; k++) rn[k] = r[k] - alpha * ap[k];
+                uint32_t qn[6], En;
+                if (!Spinor<S_INT30>::store_ff_q(a.v0, a.n, i, rn, qn, En)) atomicExch(a.err, 1);
+                long long n2 = 0, d = 0;
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(n2) : "r"((int)qn[k]));
+                    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(d) : "r"((int)qn[k]), "r"(qr[k]));
+                }
+                // a record's value is q 2^(E-127)
+                v[0] += ff_ldexp(ff_from_ll(n2), 2 * (int)En - 254);
+                v[1] += ff_ldexp(ff_from_ll(d), (int)En + (int)Er - 254);
+                continue;
+            } else {
             real r[6], ap[6], rn[6];
             Spinor<SF>::decode(cr[u], r);
             Spinor<SF>::decode(ca[u], ap);
@@ -77,6 +101,7 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
             v[0] += (red_t<real>)n2;
             v[1] += (red_t<real>)d;
             if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
+            }
         }
     }
     __shared__ double tot[2];

@@ -295,13 +295,19 @@ struct Spinor<S_INT30> {
         const uint2 t = ld_cached(reinterpret_cast<const uint2 *>(b + (size_t)16 * n) + i);
         c[1] = make_uint4(t.x, t.y, 0u, 0u);
     }
+    // the six integers and the exponent field of a gathered record
+    __device__ static uint32_t raw(const uint4 c[chunks], int32_t q[6])
+    {
+        const uint4 a = c[0];
+        q[0] = sext_bits(a.x, 30); q[1] = sext_bits(a.y, 30); q[2] = sext_bits(a.z, 30);
+        q[3] = sext_bits(a.w, 30); q[4] = sext_bits(c[1].x, 30); q[5] = sext_bits(c[1].y, 30);
+        return (a.x >> 30) | ((a.y >> 30) << 2) | ((a.z >> 30) << 4) | ((a.w >> 30) << 6);
+    }
     template <typename real>
     __device__ static void decode(const uint4 c[chunks], real v[6])
     {
-        const uint4 a = c[0];
-        const uint32_t E = (a.x >> 30) | ((a.y >> 30) << 2) | ((a.z >> 30) << 4) | ((a.w >> 30) << 6);
-        const int32_t q[6] = {sext_bits(a.x, 30), sext_bits(a.y, 30), sext_bits(a.z, 30),
-                              sext_bits(a.w, 30), sext_bits(c[1].x, 30), sext_bits(c[1].y, 30)};
+        int32_t q[6];
+        const uint32_t E = raw(c, q);
         if constexpr (is_ff<real>::value) {  // exact: q as an FP32 pair, times a power of two
             const float up = __uint_as_float(E << 23);
 #pragma unroll
@@ -361,6 +367,12 @@ struct Spinor<S_INT30> {
     // (hi' - r) + lo' (TwoSum) rounded the same way in a second stage.
     __device__ static bool store_ff(char *b, int n, int i, const ff v[6])
     {
+        uint32_t u[6], E;
+        return store_ff_q(b, n, i, v, u, E);
+    }
+    // the same, returning the stored integers (signed, in u) and exponent field
+    __device__ static bool store_ff_q(char *b, int n, int i, const ff v[6], uint32_t u[6], uint32_t &E)
+    {
         bool ok = true;
         int km = 0;
 #pragma unroll
@@ -371,8 +383,9 @@ struct Spinor<S_INT30> {
             const float l = copysignf(1.0f, v[k].hi) * v[k].lo, lm = copysignf(1.0f, v[km].hi) * v[km].lo;
             if (a > am || (a == am && l > lm)) km = k;
         }
-        uint32_t E = 1;
-        uint32_t u[6] = {0, 0, 0, 0, 0, 0};
+        E = 1;
+#pragma unroll
+        for (int k = 0; k < 6; k++) u[k] = 0;
         if (ok) {
             const ff m = v[km];
             const uint32_t bits = __float_as_uint(fabsf(m.hi));

@@ -34,7 +34,9 @@ __device__ __forceinline__ int wrap_coord(int c, int L)
     return c;
 }
 
-// acc += U s
+// acc += U s, every product accumulated by one fused multiply-add (four per
+// complex product: on GB300's narrow FP64 pipe a separate multiply and add
+// per pair of products would cost half as many instructions again)
 template <typename real>
 __device__ __forceinline__ void mv_add(real acc[6], const real U[18], const real s[6])
 {
@@ -43,8 +45,10 @@ __device__ __forceinline__ void mv_add(real acc[6], const real U[18], const real
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const real ur = U[2 * (3 * i + j)], ui = U[2 * (3 * i + j) + 1];
-            acc[2 * i] += ur * s[2 * j] - ui * s[2 * j + 1];
-            acc[2 * i + 1] += ur * s[2 * j + 1] + ui * s[2 * j];
+            acc[2 * i] = fma(ur, s[2 * j], acc[2 * i]);
+            acc[2 * i] = fma(-ui, s[2 * j + 1], acc[2 * i]);
+            acc[2 * i + 1] = fma(ur, s[2 * j + 1], acc[2 * i + 1]);
+            acc[2 * i + 1] = fma(ui, s[2 * j], acc[2 * i + 1]);
         }
 }
 
@@ -57,8 +61,10 @@ __device__ __forceinline__ void mv_adj_sub(real acc[6], const real U[18], const 
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             const real ur = U[2 * (3 * j + i)], ui = U[2 * (3 * j + i) + 1];  // conj(U_ji)
-            acc[2 * i] -= ur * s[2 * j] + ui * s[2 * j + 1];
-            acc[2 * i + 1] -= ur * s[2 * j + 1] - ui * s[2 * j];
+            acc[2 * i] = fma(-ur, s[2 * j], acc[2 * i]);
+            acc[2 * i] = fma(-ui, s[2 * j + 1], acc[2 * i]);
+            acc[2 * i + 1] = fma(-ur, s[2 * j + 1], acc[2 * i + 1]);
+            acc[2 * i + 1] = fma(ui, s[2 * j], acc[2 * i + 1]);
         }
 }
 

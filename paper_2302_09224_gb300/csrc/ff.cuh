@@ -80,6 +80,22 @@ __device__ __forceinline__ ff ff_from_int(int q)
 // Scale by a power of two given as a float (exact while the result is normal).
 __device__ __forceinline__ ff ff_scale(ff a, float pow2) { return ff(__fmul_rn(a.hi, pow2), __fmul_rn(a.lo, pow2)); }
 
+// a 2^e for |e| <= 252, in two exact steps of at most 2^126 each
+__device__ __forceinline__ ff ff_ldexp(ff a, int e)
+{
+    const int e1 = e >> 1, e2 = e - e1;
+    return ff_scale(ff_scale(a, __uint_as_float((uint32_t)(e1 + 127) << 23)),
+                    __uint_as_float((uint32_t)(e2 + 127) << 23));
+}
+
+// A 64-bit integer as a pair: hi its FP32 rounding, lo the FP32 rounding of
+// the exact remainder (|s| < 2^62: about 48 significant bits, like any pair).
+__device__ __forceinline__ ff ff_from_ll(long long s)
+{
+    const float hi = __ll2float_rn(s);
+    return ff(hi, __ll2float_rn(s - __float2ll_rn(hi)));
+}
+
 template <typename T>
 struct is_ff {
     static constexpr bool value = false;

@@ -18,12 +18,9 @@
 namespace hisq {
 
 // Type of a thread's sums: the compute type (FP32 pairs stay pairs; their
-// block sums run in pair arithmetic, see below).  Type of the block partials:
-// the compute type, FP64 for pairs (hi + lo is exact in FP64).
+// block sums run in pair arithmetic, see below).
 template <typename real>
 using red_t = real;
-template <typename real>
-using part_t = std::conditional_t<is_ff<real>::value, double, real>;
 
 template <int NR, typename T>
 __device__ __forceinline__ void warp_sum(T v[NR])
@@ -70,6 +67,12 @@ __device__ __forceinline__ FF ff_add(FF a, FF b)
     return {hi, __fadd_rn(e, -__fadd_rn(hi, -s))};
 }
 
+// Type of the block partials: the compute type, an FP32 pair for pairs (the
+// one block that sums them then stays on the FP32 pipe: FP64 adds of several
+// thousand partials on one SM's narrow FP64 pipe took longer than the sum).
+template <typename real>
+using part_t = std::conditional_t<is_ff<real>::value, FF, real>;
+
 template <int NR>
 __device__ __forceinline__ void warp_sum_ff(FF v[NR])
 {
@@ -83,8 +86,8 @@ __device__ __forceinline__ void warp_sum_ff(FF v[NR])
 }
 
 // One block sums the partials of nblocks blocks (in a fixed order) into tot
-// (shared memory), valid in thread 0: FP64 partials in FP64, FP32 partials in
-// the FP32 pair arithmetic.
+// (shared memory), valid in thread 0: FP64 partials in FP64, FP32 partials and
+// FP32-pair partials in the FP32 pair arithmetic.
 template <int NR, typename T>
 __device__ void sum_partials(const RedBuf &rb, unsigned nblocks, double *tot)
 {
@@ -94,7 +97,42 @@ __device__ void sum_partials(const RedBuf &rb, unsigned nblocks, double *tot)
     // flight at once (one L2 round trip per U rows); the order is fixed
     constexpr int U = NR <= 4 ? 8 : NR <= 8 ? 4 : 1;
     const unsigned step = blockDim.x;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, FF>::value) {
+        const float2 *pp = reinterpret_cast<const float2 *>(rb.partials);
+        FF w[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) w[k] = {0.0f, 0.0f};
+        for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * step) {
+            float2 tmp[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const unsigned b = b0 + u * step;
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    tmp[u][k] = b < nblocks ? __ldcg(pp + (size_t)b * NR + k) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int k = 0; k < NR; k++) w[k] = ff_add(w[k], FF{tmp[u][k].x, tmp[u][k].y});
+        }
+        __shared__ FF shp[32][NR];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int nw = (blockDim.x + 31) >> 5;
+        warp_sum_ff<NR>(w);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NR; k++) shp[wid][k] = w[k];
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; k++) w[k] = lane < nw ? shp[lane][k] : FF{0.0f, 0.0f};
+            warp_sum_ff<NR>(w);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < NR; k++) tot[k] = (double)w[k].hi + (double)w[k].lo;
+        }
+    } else if constexpr (sizeof(T) == 8) {
         double w[NR];
 #pragma unroll
         for (int k = 0; k < NR; k++) w[k] = 0.0;
@@ -197,8 +235,8 @@ __device__ bool reduce_grid(const T vin[NR], const RedBuf &rb, double *tot)
 
 // FP32-pair values (the FP64-class kernels): the block sums them in pair
 // arithmetic (TwoSum at every level of the same fixed tree, nothing on the
-// narrow FP64 pipe) and stores one FP64 partial, hi + lo, exact; the last
-// block sums the partials in FP64.
+// narrow FP64 pipe) and stores its pair; the last block sums the pairs in the
+// same arithmetic and returns hi + lo in FP64.
 template <int NR>
 __device__ __forceinline__ void block_sum_pairs(const ff vin[NR], FF v[NR])
 {
@@ -229,9 +267,9 @@ __device__ bool reduce_grid(const ff vin[NR], const RedBuf &rb, double *tot)
     FF v[NR];
     block_sum_pairs<NR>(vin, v);
     if (threadIdx.x == 0) {
-        double *part = reinterpret_cast<double *>(rb.partials);
+        float2 *part = reinterpret_cast<float2 *>(rb.partials);
 #pragma unroll
-        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = (double)v[k].hi + (double)v[k].lo;
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = make_float2(v[k].hi, v[k].lo);
         __threadfence();
         const unsigned prev = atomicAdd(rb.counter, 1u);
         is_last = (prev == nblocks - 1);
@@ -239,7 +277,7 @@ __device__ bool reduce_grid(const ff vin[NR], const RedBuf &rb, double *tot)
     __syncthreads();
     if (!is_last) return false;
     __threadfence();
-    sum_partials<NR, double>(rb, nblocks, tot);
+    sum_partials<NR, FF>(rb, nblocks, tot);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NR; k++) rb.result[k] = tot[k];
@@ -255,10 +293,10 @@ __device__ void store_block_partial(const ff vin[NR], const RedBuf &rb)
     FF v[NR];
     block_sum_pairs<NR>(vin, v);
     if (threadIdx.x == 0) {
-        double *part = reinterpret_cast<double *>(rb.partials);
+        float2 *part = reinterpret_cast<float2 *>(rb.partials);
         const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
-        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = (double)v[k].hi + (double)v[k].lo;
+        for (int k = 0; k < NR; k++) part[(size_t)bid * NR + k] = make_float2(v[k].hi, v[k].lo);
     }
 }
 
