@@ -64,6 +64,8 @@ def _load():
         "or_int20_unpack": (None, [_i64, _p, _p]),
         "or_int30_pack": (_i64, [_i64, _p, _p]),
         "or_int30_unpack": (None, [_i64, _p, _p]),
+        "or_int14_pack": (_i64, [_i64, _p, _p]),
+        "or_int14_unpack": (None, [_i64, _p, _p]),
         "or_absmax": (_d, [_i64, _p]),
         "or_fix_pack": (None, [_i64, _p, _d, _i, _p]),
         "or_fix_unpack": (None, [_i64, _p, _d, _i, _i, _p]),
@@ -164,7 +166,7 @@ def mfull(dims, fat, lng, m: float, x):
 # ---------------------------------------------------------------------------
 # storage formats
 # ---------------------------------------------------------------------------
-SFMT = {"f64": 0, "f32": 1, "half": 2, "int20": 3, "int30": 4}
+SFMT = {"f64": 0, "f32": 1, "half": 2, "int20": 3, "int30": 4, "int14": 5}
 GFMT = {"f64": 0, "f32": 1, "fix16": 2, "fix32": 3}
 
 
@@ -195,6 +197,21 @@ def int20_unpack(w):
     ww = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1, 4)
     out = np.empty((ww.shape[0], 6), dtype=np.float32)
     _load().or_int20_unpack(ww.shape[0], _ptr(ww), _ptr(out))
+    return out
+
+
+def int14_pack(v):
+    """FP32 [n][6] -> (words uint32 [n][3], number of non-finite sites)."""
+    a = _np(v, np.float32).reshape(-1, 6)
+    w = np.zeros((a.shape[0], 3), dtype=np.uint32)
+    bad = _load().or_int14_pack(a.shape[0], _ptr(a), _ptr(w))
+    return w, int(bad)
+
+
+def int14_unpack(w):
+    ww = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1, 3)
+    out = np.empty((ww.shape[0], 6), dtype=np.float32)
+    _load().or_int14_unpack(ww.shape[0], _ptr(ww), _ptr(out))
     return out
 
 
@@ -358,7 +375,8 @@ def multishift_cg(dims, fat, lng, m: float, sigmas, tols, b, maxiter: int = 1000
 
 
 # relative precision of each storage format (a shifted system's freezing floor is 10 times it)
-EPS_FMT = {"f64": 0.0, "f32": 2.0 ** -24, "half": 2.0 ** -15, "int20": 2.0 ** -19, "int30": 2.0 ** -29}
+EPS_FMT = {"f64": 0.0, "f32": 2.0 ** -24, "half": 2.0 ** -15, "int20": 2.0 ** -19, "int30": 2.0 ** -29,
+           "int14": 2.0 ** -13}
 
 
 def mixed_multishift(dims, fat, lng, m: float, sigmas, tols, b, sfmt: str, fat_s=None, lng_s=None,

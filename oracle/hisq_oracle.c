@@ -420,6 +420,65 @@ void or_int30_unpack(int64_t n, const uint32_t *w, double *v)
     }
 }
 
+/* 14-bit shared-exponent format in 12 bytes: a third width of the family the
+ * paper builds its two formats from (Sec. 4: the 20- and 30-bit formats are
+ * two of many possible shared-exponent formats).  Per site: six 14-bit
+ * two's-complement integers and an 8-bit exponent in three 32-bit words of
+ * two 16-bit halves each, half k = 2j + h in word j (h = 0 low, 1 high):
+ *   half k = q_k << 2 | e_k,  e_k = exponent bits 2k..2k+1 for k < 4, 0 else,
+ * components in the order re0, im0, re1, im1, re2, im2.  The exponent rule is
+ * Appendix A's with scale 2^13 - 1 in FP32 arithmetic:
+ *   max = largest |component| (FP32);  t = max / (2^13 - 1) in FP32;
+ *   E = (biased exponent field of t) + 1, so 2^(E-127) is the power of two
+ *       just above t;  q_k = round-to-nearest-even(v_k 2^-(E-127));
+ * decoding multiplies the sign-extended q_k by 2^(E-127).  Non-finite sites
+ * are written as zero with E = 1 and counted (the return value). */
+int64_t or_int14_pack(int64_t n, const float *v, uint32_t *w)
+{
+    int64_t bad = 0;
+    for (int64_t s = 0; s < n; s++) {
+        const float *x = v + 6 * s;
+        float mx = 0.0f;
+        int finite = 1;
+        for (int i = 0; i < 6; i++) {
+            if (!isfinite(x[i])) finite = 0;
+            mx = fmaxf(mx, fabsf(x[i]));
+        }
+        uint32_t q[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t E = 1;
+        if (!finite) {
+            bad++;
+        } else {
+            const float t = mx / 8191.0f;
+            E = ((f2u(t) >> 23) & 0xffu) + 1u;
+            const float down = u2f((254u - E) << 23); /* 2^-(E-127) */
+            for (int i = 0; i < 6; i++) q[i] = (uint32_t)(int32_t)lrintf(x[i] * down);
+        }
+        uint32_t half[6];
+        for (int k = 0; k < 6; k++) {
+            const uint32_t e = k < 4 ? (E >> (2 * k)) & 3u : 0u;
+            half[k] = ((q[k] & 0x3fffu) << 2) | e;
+        }
+        for (int j = 0; j < 3; j++) w[3 * s + j] = half[2 * j] | (half[2 * j + 1] << 16);
+    }
+    return bad;
+}
+
+void or_int14_unpack(int64_t n, const uint32_t *w, float *v)
+{
+    for (int64_t s = 0; s < n; s++) {
+        uint32_t half[6];
+        for (int j = 0; j < 3; j++) {
+            half[2 * j] = w[3 * s + j] & 0xffffu;
+            half[2 * j + 1] = w[3 * s + j] >> 16;
+        }
+        uint32_t E = 0;
+        for (int k = 0; k < 4; k++) E |= (half[k] & 3u) << (2 * k);
+        const float up = u2f(E << 23); /* 2^(E-127) */
+        for (int k = 0; k < 6; k++) v[6 * s + k] = (float)sext(half[k] >> 2, 14) * up;
+    }
+}
+
 /* Fixed-point gauge (Sec. 2 and its footnote on smeared fields; Sec. 4 for the
  * 32-bit variant): one scale per field set by the global max |element|;
  * q = rint(x * (qmax / gmax)) in FP64, clamped to [-qmax, qmax],
@@ -610,7 +669,8 @@ void or_gauge_emulate(const int *L, const double *g, int gfmt, int recon, int k,
     }
 }
 
-/* Spinor format emulation: sfmt 0 FP64, 1 FP32, 2 half, 3 int20, 4 int30. */
+/* Spinor format emulation: sfmt 0 FP64, 1 FP32, 2 half, 3 int20, 4 int30,
+ * 5 int14. */
 void or_spinor_emulate(int64_t nsites, int sfmt, const double *in, double *out)
 {
     const int64_t n = nsites * 6;
@@ -636,6 +696,11 @@ void or_spinor_emulate(int64_t nsites, int sfmt, const double *in, double *out)
         or_half_pack(nsites, f, r);
         or_half_unpack(nsites, r, f);
         free(r);
+    } else if (sfmt == 5) {
+        uint32_t *w = malloc(sizeof(uint32_t) * 3 * nsites);
+        or_int14_pack(nsites, f, w);
+        or_int14_unpack(nsites, w, f);
+        free(w);
     } else {
         uint32_t *w = malloc(sizeof(uint32_t) * 4 * nsites);
         or_int20_pack(nsites, f, w);

@@ -2,7 +2,8 @@
 
 * bit patterns derived by hand from the paper's codec rules
   (``tests/golden/*_vectors.txt``: Appendix A, Listing 4 for 20-bit;
-  Sec. 2, Listing 1 for 16-bit; our stated reading of Listing 3 for 30-bit);
+  Sec. 2, Listing 1 for 16-bit; our stated reading of Listing 3 for 30-bit;
+  the Appendix A rule with scale 2^13-1 for our 12-byte 14-bit width);
 * round-trip error within the format's epsilon (Sec. 2: 2^-15 relative to the
   site maximum for the two's-complement 16-bit format; Sec. 4: about 2^-19
   for 20-bit and 2^-29 for 30-bit);
@@ -42,6 +43,13 @@ def test_int20_golden(orc):
 def test_int30_golden(orc):
     for vals, words in _read("int30_vectors.txt"):
         w, bad = orc.int30_pack(np.array([vals]))
+        assert bad == 0
+        assert [int(x, 16) for x in words] == [int(x) for x in w[0]], vals
+
+
+def test_int14_golden(orc):
+    for vals, words in _read("int14_vectors.txt"):
+        w, bad = orc.int14_pack(np.array([vals], dtype=np.float32))
         assert bad == 0
         assert [int(x, 16) for x in words] == [int(x) for x in w[0]], vals
 
@@ -104,6 +112,49 @@ def test_int20_nonfinite_flagged(orc):
     assert bad == 2
 
 
+def test_int14_roundtrip_bound_and_idempotence(orc):
+    v = _random_sites(20000, 8).astype(np.float32)
+    w, bad = orc.int14_pack(v)
+    assert bad == 0
+    assert np.all((w[:, 2] & 0x00030003) == 0)  # halves 4 and 5 carry no exponent bits
+    u = orc.int14_unpack(w)
+    mx = np.abs(v).max(axis=1, keepdims=True)
+    # step 2^(E-127) <= 2 max/(2^13-1): error <= max/(2^13-1) (+ FP32 rounding of t)
+    assert np.all(np.abs(u - v) <= mx / 8191.0 * (1 + 1e-6))
+    # re-encoding the decoded site gives the same record, except where the
+    # largest integer rounded up to 2^13 - 1: there t = 2^(E-127) exactly and
+    # the rule picks the next exponent
+    w2, _ = orc.int14_pack(u)
+    def expo(ww):
+        return sum(((ww[:, k // 2].astype(np.int64) >> (16 * (k % 2))) & 3) << (2 * k) for k in range(4))
+    E = expo(w)
+    qmax = np.rint(np.abs(u).max(axis=1) / np.ldexp(1.0, E - 127)).astype(np.int64)
+    top = qmax == 8191
+    np.testing.assert_array_equal(w[~top], w2[~top])
+    assert np.all(expo(w2)[top] == E[top] + 1)
+
+
+def test_int14_exact_grid_zero_floor_and_nonfinite(orc):
+    g = np.random.Generator(np.random.Philox(key=9))
+    q = g.integers(-8000, 8001, size=(500, 6))
+    q[:, 1] = 8000  # max |q| in [2^12, 2^13 - 1): the scale is exactly 2^-7
+    v = (q * 2.0 ** -7).astype(np.float32)
+    np.testing.assert_array_equal(orc.int14_unpack(orc.int14_pack(v)[0]), v)
+    w, _ = orc.int14_pack(np.zeros((1, 6), np.float32))
+    assert np.all(orc.int14_unpack(w) == 0)
+    # E = 1 (scale 2^-126) is the floor: FP32 subnormal sites land on that grid
+    v = np.array([[3e-39, -1e-40, 0, 0, 0, 2e-45]], np.float32)
+    w, _ = orc.int14_pack(v)
+    e = sum(((int(w[0, k // 2]) >> (16 * (k % 2))) & 3) << (2 * k) for k in range(4))
+    assert e == 1
+    assert np.all(np.abs(orc.int14_unpack(w) - v) <= 2.0 ** -127)
+    v = np.ones((3, 6), np.float32)
+    v[1, 4] = np.nan
+    v[2, 0] = -np.inf
+    w, bad = orc.int14_pack(v)
+    assert bad == 2 and np.all(orc.int14_unpack(w)[1:] == 0)
+
+
 def test_half_roundtrip_bound_and_idempotence(orc):
     v = _random_sites(20000, 2).astype(np.float32)
     rec, bad = orc.half_pack(v)
@@ -145,14 +196,15 @@ def test_int30_exact_grid(orc):
 
 
 def test_spinor_emulate_orders(orc):
-    """Format error ordering of Sec. 4: int30 << f32 < int20 < half."""
+    """Format error ordering of Sec. 4: int30 << f32 < int20 < half < int14."""
     v = synth.spinor((4, 4, 4, 4), 7).numpy().reshape(-1, 6)
     err = {}
-    for f in ("f32", "half", "int20", "int30"):
+    for f in ("f32", "half", "int20", "int30", "int14"):
         e = orc.spinor_emulate(v, f)
         err[f] = np.linalg.norm(e - v) / np.linalg.norm(v)
     assert err["int30"] < 1e-8 < err["f32"] < 1e-6 < err["int20"] < err["half"] < 1e-4
     assert err["half"] / err["int20"] > 8     # 4 more bits
+    assert 2 < err["int14"] / err["half"] < 8  # 13 bits against the 16-bit format's 15
     np.testing.assert_array_equal(orc.spinor_emulate(v, "f64"), v)
 
 
