@@ -79,7 +79,9 @@ typedef enum {
     HISQ_SPINOR_F32 = 1,    /* 24 B/site */
     HISQ_SPINOR_HALF16 = 2, /* 16 B/site: int16 v[6] + FP32 site max (Sec. 2, Listing 1) */
     HISQ_SPINOR_INT20 = 3,  /* 16 B/site: 6 x int20 + 8-bit exponent (Sec. 4 Listing 2; Appendix A) */
-    HISQ_SPINOR_INT30 = 4   /* 24 B/site: 6 x int30 + 8-bit exponent (Sec. 4, Listing 3) */
+    HISQ_SPINOR_INT30 = 4,  /* 24 B/site: 6 x int30 + 8-bit exponent (Sec. 4, Listing 3) */
+    HISQ_SPINOR_INT14 = 5   /* 12 B/site: 6 x int14 + 8-bit exponent (a third width of the Sec. 4
+                               shared-exponent family; the Appendix A rule with scale 2^13 - 1) */
 } hisq_spinor_fmt;
 
 /* Arithmetic precision (the third member of the triplet, Sec. 4). */
@@ -88,7 +90,7 @@ typedef enum { HISQ_COMPUTE_F32 = 0, HISQ_COMPUTE_F64 = 1 } hisq_compute_fmt;
 /* Precision triplet gauge / fermion / compute plus link compression (Sec. 1:
  * 18 -> 12 reals by SU(3) unitarity).  Supported combinations:
  *   F64/F64/F64, F32/F32/F32, FIX16/HALF16/F32, FIX16/INT20/F32,
- *   FIX32/INT30/F64, FIX32/INT30/F32;
+ *   FIX32/INT30/F64, FIX32/INT30/F32, FIX16/INT14/F32;
  * fat_recon must be 18 (smeared fat links are not unitary); long_recon 18,
  * 12, 13 or 8:
  *   12: rows 0 and 1; needs long links that are a sign times SU(3) (checked
@@ -202,20 +204,21 @@ HISQ_API hisq_status hisq_dslash_noalloc(hisq_ctx *ctx, const hisq_gauge *g, his
 /* Device bytes of one half-lattice (n sites) spinor field in format sfmt, in
  * this library's planar layout: the site record is split into 16-byte planes
  * [plane][site] followed by one narrower tail plane (F32 and INT30: 16 + 8 B;
- * F64: 3 x 16 B; HALF16 and INT20: one 16-B record = the paper's struct). */
+ * F64: 3 x 16 B; HALF16 and INT20: one 16-B record = the paper's struct;
+ * INT14: an 8-B plane (words 0, 1) and a 4-B plane (word 2)). */
 HISQ_API size_t hisq_spinor_bytes(int sfmt, int64_t n);
 
 /* Encode n sites (FP64 [n][6] on the device) into format sfmt (planar layout
  * above) on the device, exactly as every kernel of the library stores a
- * field: HALF16 and INT20 round the input to FP32 first and encode in FP32
- * (Appendix A arithmetic for INT20); INT30 encodes in FP64.  *n_bad receives
+ * field: HALF16, INT20 and INT14 round the input to FP32 first and encode in
+ * FP32 (Appendix A arithmetic for INT20 and INT14); INT30 encodes in FP64.  *n_bad receives
  * the number of sites with a non-finite (or, for INT30, unencodable)
  * component; such sites are stored as zero.  Device pointers only. */
 HISQ_API hisq_status hisq_spinor_pack(hisq_ctx *ctx, int sfmt, int64_t n, const double *in, void *packed,
                              int64_t *n_bad, void *stream);
 
 /* Encode n sites of FP32 [n][6] input (device) into format sfmt (F32, HALF16,
- * INT20 or INT30) exactly as the FP32-compute kernels store a field; for
+ * INT20, INT30 or INT14) exactly as the FP32-compute kernels store a field; for
  * INT30 the bits equal those of hisq_spinor_pack on the same (FP32-exact)
  * values.  *n_bad counts non-finite sites (stored as zero). */
 HISQ_API hisq_status hisq_spinor_pack32(hisq_ctx *ctx, int sfmt, int64_t n, const float *in, void *packed,

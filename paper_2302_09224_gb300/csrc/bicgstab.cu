@@ -392,6 +392,7 @@ dim3 grid2(int vh)
         case S_F32: KERNEL<S_F32, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;      \
         case S_HALF: KERNEL<S_HALF, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;    \
         case S_INT20: KERNEL<S_INT20, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;  \
+        case S_INT14: KERNEL<S_INT14, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;  \
         case S_INT30:                                                                       \
             if (f64_) KERNEL<S_INT30, double><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);        \
             else KERNEL<S_INT30, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);              \

@@ -277,6 +277,7 @@ int nblk(int n) { return (n + kBlock - 1) / kBlock; }
         case S_F32: launch_chained(KERNEL<S_F32, float>, __VA_ARGS__, a); break;            \
         case S_HALF: launch_chained(KERNEL<S_HALF, float>, __VA_ARGS__, a); break;          \
         case S_INT20: launch_chained(KERNEL<S_INT20, float>, __VA_ARGS__, a); break;        \
+        case S_INT14: launch_chained(KERNEL<S_INT14, float>, __VA_ARGS__, a); break;        \
         case S_INT30:                                                                       \
             if (f64_) launch_chained(KERNEL<S_INT30, double>, __VA_ARGS__, a);              \
             else launch_chained(KERNEL<S_INT30, float>, __VA_ARGS__, a);                    \
@@ -303,6 +304,7 @@ void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
     case S_F32: r_update_t<S_F32, float>(a, s); break;
     case S_HALF: r_update_t<S_HALF, float>(a, s); break;
     case S_INT20: r_update_t<S_INT20, float>(a, s); break;
+    case S_INT14: r_update_t<S_INT14, float>(a, s); break;
     case S_INT30:  // FP64-class compute in FP32 pairs (see ff.cuh)
         if (cf == HISQ_COMPUTE_F64)
             r_update_t<S_INT30, ff>(a, s);

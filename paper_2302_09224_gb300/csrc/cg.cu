@@ -449,6 +449,7 @@ double sloppy_eps(const hisq_prec &p)
     if (p.spinor == S_F32) es = 0x1p-24;
     if (p.spinor == S_HALF) es = 0x1p-15;
     if (p.spinor == S_INT20) es = 0x1p-19;
+    if (p.spinor == S_INT14) es = 0x1p-13;
     double eg = 0x1p-31;  // 32-bit fixed point
     if (p.gauge == G_F64) eg = 0x1p-53;
     if (p.gauge == G_F32) eg = 0x1p-24;

@@ -8,6 +8,7 @@
 //   F32    16 + 8 B        (c0, c1) | (c2)
 //   HALF   16 B            int16 q[6] | FP32 site max  (Sec. 2, Listing 1)
 //   INT20  16 B            four words of the Appendix A bitfield layout
+//   INT14  8 + 4 B         three words of 16-bit halves (q << 2 | exponent bits)
 //   INT30  16 + 8 B        words 0..3 | words 4..5 (Sec. 4, Listing 3; our layout)
 // Link formats ([plane][parity][mu][Vh]; reals row-major, first 12 for r12):
 //   F64 16 B = 1 complex, F32 16 B = 2 complex, FIX16 16 B = 8 int16,
@@ -279,6 +280,74 @@ struct Spinor<S_INT20> {
         w.z = (u[3] & 0xffffu) | (((u[4] >> 4) & 0xffffu) << 16);
         w.w = (u[4] & 0xfu) | ((u[5] & 0xfffffu) << 4) | (E << 24);
         reinterpret_cast<uint4 *>(b)[i] = w;
+        return ok;
+    }
+};
+
+// 14-bit shared exponent in 12 bytes (a third width of the Sec. 4 family):
+// three words of two 16-bit halves, half k = q_k << 2 | e_k with e_k the
+// exponent bits 2k..2k+1 (k < 4) and 0 for k = 4, 5; an 8-byte plane (words
+// 0, 1) and a 4-byte plane (word 2).  Encode as the 20-bit format with scale
+// 2^13 - 1.  Decode: masking the exponent bits leaves 4 q_k in each half, which
+// the hardware halfword conversion turns into an exact float; the scale is
+// then 2^(E-129) (a subnormal power of two for E < 3, still exact).
+template <>
+struct Spinor<S_INT14> {
+    static constexpr int chunks = 1;
+    __device__ static void gather(const char *b, int n, int i, uint4 c[chunks])
+    {
+        const uint2 a = ld_cached(reinterpret_cast<const uint2 *>(b) + i);
+        const uint32_t w = ld_cached(reinterpret_cast<const uint32_t *>(b + (size_t)8 * n) + i);
+        c[0] = make_uint4(a.x, a.y, w, 0u);
+    }
+    __device__ static uint32_t exponent(const uint4 &w)
+    {
+        return (w.x & 3u) | ((w.x >> 14) & 0xcu) | ((w.y & 3u) << 4) | ((w.y >> 10) & 0xc0u);
+    }
+    template <typename real>
+    __device__ static void decode(const uint4 c[chunks], real v[6])
+    {
+        const uint4 w = c[0];
+        const uint32_t E = exponent(w);
+        const float up = __uint_as_float(E >= 3u ? (E - 2u) << 23 : E == 2u ? 0x00400000u : 0x00200000u);
+        const uint32_t m0 = w.x & 0xfffcfffcu, m1 = w.y & 0xfffcfffcu, m2 = w.z & 0xfffcfffcu;
+        const float q[6] = {i16lo_to_f(m0), i16hi_to_f(m0), i16lo_to_f(m1),
+                            i16hi_to_f(m1), i16lo_to_f(m2), i16hi_to_f(m2)};
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = (real)fmul(q[k], up);
+    }
+    template <typename real>
+    __device__ static void load(const char *b, int n, int i, real v[6])
+    {
+        uint4 c[chunks];
+        gather(b, n, i, c);
+        decode(c, v);
+    }
+    template <typename real>
+    __device__ static bool store(char *b, int n, int i, const real v[6])
+    {
+        float f[6];
+        float mx = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            f[k] = (float)v[k];
+            ok = ok && isfinite(f[k]);
+            mx = fmaxf(mx, fabsf(f[k]));
+        }
+        uint32_t h[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t E = 1;
+        if (ok) {
+            const float t = __fdiv_rn(mx, 8191.0f);
+            E = ((__float_as_uint(t) >> 23) & 0xffu) + 1u;
+            const float down = __uint_as_float((254u - E) << 23);
+#pragma unroll
+            for (int k = 0; k < 6; k++) h[k] = ((uint32_t)__float2int_rn(fmul(f[k], down)) & 0x3fffu) << 2;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) h[k] |= (E >> (2 * k)) & 3u;
+        reinterpret_cast<uint2 *>(b)[i] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        reinterpret_cast<uint32_t *>(b + (size_t)8 * n)[i] = h[4] | (h[5] << 16);
         return ok;
     }
 };
@@ -555,6 +624,11 @@ struct Spinor<S_FF> {
 template <int SF>
 __device__ __forceinline__ void gather_coherent(const char *b, int n, int i, uint4 c[Spinor<SF>::chunks])
 {
+    if constexpr (SF == S_INT14) {
+        const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(b) + i);
+        c[0] = make_uint4(a.x, a.y, __ldcg(reinterpret_cast<const uint32_t *>(b + (size_t)8 * n) + i), 0u);
+        return;
+    }
     constexpr int n16 = spinor_n16(SF), tail = spinor_tail(SF);
 #pragma unroll
     for (int k = 0; k < n16; k++) c[k] = __ldcg(reinterpret_cast<const uint4 *>(b + (size_t)k * 16 * n) + i);

@@ -226,6 +226,7 @@ hisq_status check_prec(hisq_ctx *c, const hisq_prec &p)
                     (p.gauge == G_F32 && p.spinor == S_F32 && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX16 && p.spinor == S_HALF && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX16 && p.spinor == S_INT20 && p.compute == HISQ_COMPUTE_F32) ||
+                    (p.gauge == G_FIX16 && p.spinor == S_INT14 && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX32 && p.spinor == S_INT30);
     if (!ok)
         return fail(c, HISQ_EINVAL, "unsupported precision triplet gauge=%d spinor=%d compute=%d", p.gauge,
@@ -512,7 +513,7 @@ double hisq_gauge_scale(const hisq_gauge *g, int which)
 
 size_t hisq_spinor_bytes(int sfmt, int64_t n)
 {
-    if (sfmt < 0 || sfmt > 4 || n < 0) return 0;
+    if (sfmt < 0 || sfmt > 5 || n < 0) return 0;
     return spinor_field_bytes(sfmt, n);
 }
 
@@ -533,7 +534,7 @@ static hisq_status grow_scratch(hisq_ctx *c, size_t bytes)
 hisq_status hisq_spinor_pack(hisq_ctx *c, int sfmt, int64_t n, const double *in, void *packed, int64_t *n_bad,
                              void *stream)
 {
-    if (!c || !in || !packed || sfmt < 0 || sfmt > 4 || n < 0 || n > INT32_MAX)
+    if (!c || !in || !packed || sfmt < 0 || sfmt > 5 || n < 0 || n > INT32_MAX)
         return fail(c, HISQ_EINVAL, "hisq_spinor_pack: bad argument");
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);
@@ -554,7 +555,7 @@ hisq_status hisq_spinor_pack(hisq_ctx *c, int sfmt, int64_t n, const double *in,
 hisq_status hisq_spinor_pack32(hisq_ctx *c, int sfmt, int64_t n, const float *in, void *packed, int64_t *n_bad,
                                void *stream)
 {
-    if (!c || !in || !packed || sfmt < 1 || sfmt > 4 || n < 0 || n > INT32_MAX)
+    if (!c || !in || !packed || sfmt < 1 || sfmt > 5 || n < 0 || n > INT32_MAX)
         return fail(c, HISQ_EINVAL, "hisq_spinor_pack32: bad argument");
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);
@@ -596,7 +597,7 @@ hisq_status hisq_spinor_pack_pair_int30(hisq_ctx *c, int64_t n, const float *in,
 hisq_status hisq_spinor_unpack(hisq_ctx *c, int sfmt, int compute, int64_t n, const void *packed, double *out,
                                void *stream)
 {
-    if (!c || !out || !packed || sfmt < 0 || sfmt > 4 || n < 0 || n > INT32_MAX)
+    if (!c || !out || !packed || sfmt < 0 || sfmt > 5 || n < 0 || n > INT32_MAX)
         return fail(c, HISQ_EINVAL, "hisq_spinor_unpack: bad argument");
     cudaSetDevice(c->device);
     cudaStream_t s = pick_stream(c, stream);

@@ -401,6 +401,7 @@ void launch_pack_spinor(int sf, int64_t n, const double *in, char *out, int *bad
     case S_F32: pack_kernel<S_F32><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_HALF: pack_kernel<S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT20: pack_kernel<S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT14: pack_kernel<S_INT14><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT30: pack_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     default: break;
     }
@@ -414,6 +415,7 @@ void launch_pack32_spinor(int sf, int64_t n, const float *in, char *out, int *ba
     case S_F32: pack32_kernel<S_F32><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_HALF: pack32_kernel<S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT20: pack32_kernel<S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
+    case S_INT14: pack32_kernel<S_INT14><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     case S_INT30: pack32_kernel<S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, bad); break;
     default: break;
     }
@@ -438,6 +440,7 @@ void launch_unpack_spinor(int sf, int cf, int64_t n, const char *in, double *out
     case S_F32: unpack_kernel<S_F32, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
     case S_HALF: unpack_kernel<S_HALF, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
     case S_INT20: unpack_kernel<S_INT20, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
+    case S_INT14: unpack_kernel<S_INT14, float><<<nb, kBlock, 0, s>>>(n, in, out); break;
     case S_INT30:
         if (f64) unpack_kernel<S_INT30, double><<<nb, kBlock, 0, s>>>(n, in, out);
         else unpack_kernel<S_INT30, float><<<nb, kBlock, 0, s>>>(n, in, out);

@@ -19,13 +19,15 @@ namespace hisq {
 // formats
 // ---------------------------------------------------------------------------
 enum GaugeFmt { G_F64 = 0, G_F32 = 1, G_FIX16 = 2, G_FIX32 = 3 };
-// S_FF: FP32 pairs (hi, lo) per real, 48 B/site: internal accumulators of the
-// FP64-class kernels only, never a storage format of the ABI.
-enum SpinorFmt { S_F64 = 0, S_F32 = 1, S_HALF = 2, S_INT20 = 3, S_INT30 = 4, S_FF = 5 };
+// S_INT14: 12 B/site, six 14-bit integers and an 8-bit exponent (a third
+// shared-exponent width).  S_FF: FP32 pairs (hi, lo) per real, 48 B/site:
+// internal accumulators of the FP64-class kernels only, never a storage
+// format of the ABI.
+enum SpinorFmt { S_F64 = 0, S_F32 = 1, S_HALF = 2, S_INT20 = 3, S_INT30 = 4, S_INT14 = 5, S_FF = 7 };
 
 __host__ __device__ constexpr int spinor_site_bytes(int sf)
 {
-    return (sf == S_F64 || sf == S_FF) ? 48 : (sf == S_F32 || sf == S_INT30) ? 24 : 16;
+    return (sf == S_F64 || sf == S_FF) ? 48 : (sf == S_F32 || sf == S_INT30) ? 24 : sf == S_INT14 ? 12 : 16;
 }
 __host__ __device__ constexpr int spinor_n16(int sf) { return spinor_site_bytes(sf) / 16; }
 __host__ __device__ constexpr int spinor_tail(int sf) { return spinor_site_bytes(sf) % 16; }

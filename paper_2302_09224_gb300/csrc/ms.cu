@@ -122,6 +122,7 @@ void convert_to(int so, int n, const char *in, char *out, int *err, cudaStream_t
     case S_F32: convert_kernel<SI, S_F32><<<nb, kBlock, 0, s>>>(n, in, out, err); break;
     case S_HALF: convert_kernel<SI, S_HALF><<<nb, kBlock, 0, s>>>(n, in, out, err); break;
     case S_INT20: convert_kernel<SI, S_INT20><<<nb, kBlock, 0, s>>>(n, in, out, err); break;
+    case S_INT14: convert_kernel<SI, S_INT14><<<nb, kBlock, 0, s>>>(n, in, out, err); break;
     case S_INT30: convert_kernel<SI, S_INT30><<<nb, kBlock, 0, s>>>(n, in, out, err); break;
     }
 }
@@ -135,6 +136,7 @@ double format_eps(int sf)
     case S_HALF: return std::ldexp(1.0, -15);  // Sec. 2
     case S_INT20: return std::ldexp(1.0, -19); // Sec. 4
     case S_INT30: return std::ldexp(1.0, -29); // Sec. 4
+    case S_INT14: return std::ldexp(1.0, -13);
     default: return std::ldexp(1.0, -52);
     }
 }
@@ -149,6 +151,7 @@ void launch_convert(int si, int so, int n, const char *in, char *out, int *err, 
     case S_F32: convert_to<S_F32>(so, n, in, out, err, s); break;
     case S_HALF: convert_to<S_HALF>(so, n, in, out, err, s); break;
     case S_INT20: convert_to<S_INT20>(so, n, in, out, err, s); break;
+    case S_INT14: convert_to<S_INT14>(so, n, in, out, err, s); break;
     case S_INT30: convert_to<S_INT30>(so, n, in, out, err, s); break;
     }
 }
@@ -276,6 +279,7 @@ struct MSRun {
             case S_F32: shift_update_kernel<S_F32, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
             case S_HALF: shift_update_kernel<S_HALF, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
             case S_INT20: shift_update_kernel<S_INT20, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
+            case S_INT14: shift_update_kernel<S_INT14, float><<<nblk(vh), kBlock, 0, s>>>(a); break;
             case S_INT30:
                 if (f64)  // FP64-class compute in FP32 pairs, pair accumulators
                     shift_update_kernel<S_INT30, ff><<<nblk(vh), kBlock, 0, s>>>(a);

@@ -23,14 +23,15 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN
                 7: "ETIMEOUT", 8: "ENOTFOUND", 9: "ERANGE"}
 
 HISQ_GAUGE_F64, HISQ_GAUGE_F32, HISQ_GAUGE_FIX16, HISQ_GAUGE_FIX32 = 0, 1, 2, 3
-HISQ_SPINOR_F64, HISQ_SPINOR_F32, HISQ_SPINOR_HALF16, HISQ_SPINOR_INT20, HISQ_SPINOR_INT30 = 0, 1, 2, 3, 4
+HISQ_SPINOR_F64, HISQ_SPINOR_F32, HISQ_SPINOR_HALF16, HISQ_SPINOR_INT20, HISQ_SPINOR_INT30, HISQ_SPINOR_INT14 = \
+    0, 1, 2, 3, 4, 5
 HISQ_COMPUTE_F32, HISQ_COMPUTE_F64 = 0, 1
 HISQ_GAUGE_ANTIPERIODIC_T = 0x1
 HISQ_GAUGE_ON_DEVICE = 0x2
 HISQ_PROF_STENCIL, HISQ_PROF_STENCIL_HI, HISQ_PROF_BLAS, HISQ_PROF_CONVERT = 0, 1, 2, 3
 HISQ_MAX_SHIFTS = 32
 
-SPINOR_FMT = {"f64": 0, "f32": 1, "half": 2, "int20": 3, "int30": 4}
+SPINOR_FMT = {"f64": 0, "f32": 1, "half": 2, "int20": 3, "int30": 4, "int14": 5}
 
 
 class hisq_prec(ctypes.Structure):
@@ -49,6 +50,7 @@ def prec(name: str, long_recon: int = 12) -> hisq_prec:
         "f32": (HISQ_GAUGE_F32, HISQ_SPINOR_F32, HISQ_COMPUTE_F32),
         "half": (HISQ_GAUGE_FIX16, HISQ_SPINOR_HALF16, HISQ_COMPUTE_F32),
         "int20": (HISQ_GAUGE_FIX16, HISQ_SPINOR_INT20, HISQ_COMPUTE_F32),
+        "int14": (HISQ_GAUGE_FIX16, HISQ_SPINOR_INT14, HISQ_COMPUTE_F32),
         "int30": (HISQ_GAUGE_FIX32, HISQ_SPINOR_INT30, HISQ_COMPUTE_F64),
         "int30f32": (HISQ_GAUGE_FIX32, HISQ_SPINOR_INT30, HISQ_COMPUTE_F32),
     }

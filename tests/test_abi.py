@@ -39,6 +39,7 @@ def test_pure_host_calls(lib):
 
     assert hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_HALF16, 10) == 160
     assert hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_INT30, 10) == 240
+    assert hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_INT14, 10) == 120
     assert hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_F64, 3) == 144
     assert hisq.hisq_spinor_bytes(9, 3) == 0
     p = hisq.hisq_default_params()

@@ -62,7 +62,7 @@ def test_vs_dense(ctx, orc, dims):
     assert true_res(orc, dims, fat, lng, m, b, x) <= 1e-11
 
 
-@pytest.mark.parametrize("name", ["f64", "f32", "half", "int20", "int30"])
+@pytest.mark.parametrize("name", ["f64", "f32", "half", "int20", "int30", "int14"])
 @pytest.mark.parametrize("l", [1, 2, 4])
 def test_true_residual(ctx, orc, name, l):
     dims, m = (8, 8, 8, 8), 0.1

@@ -62,6 +62,33 @@ def test_int20_bit_exact(ctx, orc, n):
     np.testing.assert_array_equal(buf.view(np.uint32).reshape(-1, 4), w)
 
 
+def int14_words(buf, n):
+    """The device's two planes (8 + 4 bytes per site) as per-site records of three words."""
+    a = buf[:8 * n].view(np.uint32).reshape(n, 2)
+    b = buf[8 * n:12 * n].view(np.uint32).reshape(n, 1)
+    return np.concatenate([a, b], axis=1)
+
+
+@pytest.mark.parametrize("n", [16, 4096 + 13])
+def test_int14_bit_exact(ctx, orc, n):
+    v = sites(n, 500 + n)
+    v[12] = [1.999755859375, 0, 0, 0, 0, -1.999755859375]   # t = 2^-12 exactly, q = rint(4095.5)
+    buf, bad = device_pack(ctx, hisq.HISQ_SPINOR_INT14, v)
+    w, obad = orc.int14_pack(v.astype(np.float32))
+    assert bad == obad >= 2
+    np.testing.assert_array_equal(int14_words(buf, n), w)
+    # the FP32-input store path, and the decode
+    with np.errstate(over="ignore"):
+        f = v.astype(np.float32)
+    x = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    buf32 = torch.zeros(hisq.hisq_spinor_bytes(hisq.HISQ_SPINOR_INT14, n), dtype=torch.uint8, device="cuda")
+    assert hisq.hisq_spinor_pack32(ctx, hisq.HISQ_SPINOR_INT14, n, x, buf32) == obad
+    np.testing.assert_array_equal(int14_words(buf32.cpu().numpy(), n), w)
+    out = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    hisq.hisq_spinor_unpack(ctx, hisq.HISQ_SPINOR_INT14, 0, n, buf32, out)
+    np.testing.assert_array_equal(out.cpu().numpy(), orc.int14_unpack(w).astype(np.float64))
+
+
 @pytest.mark.parametrize("n", [16, 4096 + 13])
 def test_int30_bit_exact(ctx, orc, n):
     v = sites(n, 200 + n)

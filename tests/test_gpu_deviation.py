@@ -8,7 +8,9 @@ about two orders of magnitude below pure FP32, and the 20-bit fermion below
 the 16-bit one (the gauge field, 16-bit in both, then limits it).  Here the
 50th, 90th and 99th percentiles and the maximum of |y_gpu - y_oracle| over
 every real component must show those orderings, and the 30-bit / FP32-compute
-triplet must sit with pure FP32 (its compute precision limits it).
+triplet must sit with pure FP32 (its compute precision limits it).  The
+12-byte 14-bit fermion (a third shared-exponent width) sits above the 16-bit
+format, by its two fewer bits.
 """
 import numpy as np
 import pytest
@@ -19,7 +21,7 @@ from paper_2302_09224_gb300 import hisq, synth
 pytestmark = pytest.mark.gpu
 
 DIMS = (16, 16, 16, 16)
-NAMES = ("f32", "half", "int20", "int30", "int30f32")
+NAMES = ("f32", "half", "int20", "int30", "int30f32", "int14")
 PCT = (50, 90, 99, 100)
 
 
@@ -67,3 +69,10 @@ def test_reduced_formats_ordered_by_precision(deviations):
     # 16-bit fixed-point links limit both 16-bit-gauge triplets well above FP32
     for k in range(len(PCT)):
         assert deviations["f32"][k] < deviations["int20"][k] < deviations["half"][k]
+
+
+def test_fourteen_bit_above_sixteen_bit(deviations):
+    # the 12-byte format keeps 13 bits against the 16-bit format's 15: its fermion rounding, not the
+    # 16-bit links, dominates
+    for k in range(len(PCT) - 1):
+        assert 1.5 * deviations["half"][k] < deviations["int14"][k] < 8 * deviations["half"][k], PCT[k]

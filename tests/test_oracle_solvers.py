@@ -187,7 +187,7 @@ def test_mixed_cg_reduces_to_textbook_cg(orc):
     assert np.linalg.norm(x - x0) / np.linalg.norm(x0) <= 1e-9
 
 
-@pytest.mark.parametrize("sfmt", ["f32", "half", "int20", "int30"])
+@pytest.mark.parametrize("sfmt", ["f32", "half", "int20", "int30", "int14"])
 def test_mixed_cg_emulated_formats_converge(orc, sfmt):
     dims, m = (8, 8, 8, 8), 0.05
     fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
