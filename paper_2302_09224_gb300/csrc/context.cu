@@ -328,6 +328,7 @@ hisq_status gauge_view_existing(hisq_ctx *c, const hisq_gauge *g, const hisq_pre
     v->lng_scale_d = g->lng_max / qmax;
     v->fat_scale_f = (float)v->fat_scale_d;
     v->lng_scale_f = (float)v->lng_scale_d;
+    set_row2_rescale(v);
     return HISQ_OK;
 }
 
@@ -345,6 +346,7 @@ hisq_status gauge_view_for(hisq_ctx *c, hisq_gauge *g, const hisq_prec &p, Gauge
     v->lng_scale_d = g->lng_max / qmax;
     v->fat_scale_f = (float)v->fat_scale_d;
     v->lng_scale_f = (float)v->lng_scale_d;
+    set_row2_rescale(v);
     return HISQ_OK;
 }
 

@@ -129,60 +129,9 @@ struct SiteAccPacked {
     }
 };
 
-// FP32-pair accumulator (FP64-class compute): each product enters through
-// TwoProd and TwoSum, the error terms of the running sum gathered in lo and
-// folded in once, when the colour vector is read (12 FP32 operations per real
-// multiply-add instead of a normalised pair product and sum).
-struct SiteAccFF {
-    float hi[6], lo[6];
-    __device__ __forceinline__ void zero()
-    {
-#pragma unroll
-        for (int k = 0; k < 6; k++) hi[k] = lo[k] = 0.0f;
-    }
-    // acc_k += a b
-    __device__ __forceinline__ void fma(int k, ff a, ff b)
-    {
-        const float p = __fmul_rn(a.hi, b.hi);
-        const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p)));
-        const float s = __fadd_rn(hi[k], p);
-        const float bb = __fsub_rn(s, hi[k]);
-        const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-        hi[k] = s;
-        lo[k] = __fadd_rn(lo[k], __fadd_rn(e, t));
-    }
-    __device__ __forceinline__ void add(const ff U[18], const ff s[6])
-    {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const ff ur = U[2 * (3 * i + j)], ui = U[2 * (3 * i + j) + 1];
-                fma(2 * i, ur, s[2 * j]);
-                fma(2 * i, -ui, s[2 * j + 1]);
-                fma(2 * i + 1, ur, s[2 * j + 1]);
-                fma(2 * i + 1, ui, s[2 * j]);
-            }
-    }
-    __device__ __forceinline__ void adj_sub(const ff U[18], const ff s[6])
-    {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const ff ur = U[2 * (3 * j + i)], ui = U[2 * (3 * j + i) + 1];  // conj(U_ji)
-                fma(2 * i, -ur, s[2 * j]);
-                fma(2 * i, -ui, s[2 * j + 1]);
-                fma(2 * i + 1, -ur, s[2 * j + 1]);
-                fma(2 * i + 1, ui, s[2 * j]);
-            }
-    }
-    __device__ __forceinline__ ff get(int k) const { return ff_fast_two_sum(hi[k], lo[k]); }
-};
-
+// (FP64-class compute, FP32 pairs, takes the integer-product path below.)
 template <typename real>
-using SiteAcc = std::conditional_t<std::is_same<real, float>::value, SiteAccPacked,
-                                   std::conditional_t<is_ff<real>::value, SiteAccFF, SiteAccScalar<real>>>;
+using SiteAcc = std::conditional_t<std::is_same<real, float>::value, SiteAccPacked, SiteAccScalar<real>>;
 
 // Launch shapes tried by the tuner: threads per block, the minimum number of
 // resident blocks per SM asked of the register allocator (loads in flight per
@@ -435,6 +384,55 @@ __device__ __forceinline__ void load_link_ints(const char *base, size_t pstride,
     u[17] = (int)c[4].y;
 }
 
+// A 12-real long link in integers: rows 0 and 1 as stored (32-bit fixed
+// point, scale s), row 2 = sgn * conj(row0 x row1) rebuilt exactly in 64-bit
+// integers (row 1 halved with rounding first, so that each component, at most
+// 1/(2 s^2) by unitarity, stays below 2^63 for any field whose largest element
+// is at least 1/sqrt(3)) and brought back to the scale s in integers:
+// q = round(P * 2s), 2s = mul * 2^-(32 + shift).  The rounding adds at most one
+// unit of the 32-bit grid to row 2.
+__device__ __forceinline__ int rescale_row2(long long P, int mul, int shift)
+{
+    const int ph = (int)(P >> 32);
+    const unsigned pl = (unsigned)P;
+    long long t = (long long)ph * mul + (long long)__umulhi(pl, (unsigned)mul);  // floor(P mul / 2^32)
+    t = (t + (1LL << (shift - 1))) >> shift;
+    t = t > 2147483647LL ? 2147483647LL : t < -2147483647LL ? -2147483647LL : t;
+    return (int)t;
+}
+
+template <bool KEEP>
+__device__ __forceinline__ void load_link_ints_r12(const char *base, size_t pstride, int li, int u[18], int sgn,
+                                                   int mul, int shift)
+{
+    uint4 c[Link<G_FIX32, 12>::chunks];
+    Link<G_FIX32, 12>::template gather<KEEP>(base, pstride, li, c);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        u[4 * k] = (int)c[k].x; u[4 * k + 1] = (int)c[k].y; u[4 * k + 2] = (int)c[k].z; u[4 * k + 3] = (int)c[k].w;
+    }
+    int b[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) b[k] = (u[6 + k] >> 1) + (u[6 + k] & 1);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;  // (row0 x row1)_j = a_k b_l - a_l b_k
+        const int akr = u[2 * k], aki = u[2 * k + 1], alr = u[2 * l], ali = u[2 * l + 1];
+        const int bkr = b[2 * k], bki = b[2 * k + 1], blr = b[2 * l], bli = b[2 * l + 1];
+        long long pr = 0, pi = 0;
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pr) : "r"(akr), "r"(blr));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pr) : "r"(-aki), "r"(bli));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pr) : "r"(-alr), "r"(bkr));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pr) : "r"(ali), "r"(bki));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pi) : "r"(akr), "r"(bli));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pi) : "r"(aki), "r"(blr));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pi) : "r"(-alr), "r"(bki));
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pi) : "r"(-ali), "r"(bkr));
+        u[12 + 2 * j] = sgn * rescale_row2(pr, mul, shift);
+        u[13 + 2 * j] = -sgn * rescale_row2(pi, mul, shift);
+    }
+}
+
 // A 30-bit record, raw: its six integers and its exponent field.
 template <bool COH>
 __device__ __forceinline__ unsigned load_int30_raw(const char *b, int n, int i, int q[6])
@@ -450,9 +448,9 @@ __device__ __forceinline__ unsigned load_int30_raw(const char *b, int n, int i, 
     return (c[0].x >> 30) | ((c[0].y >> 30) << 2) | ((c[0].z >> 30) << 4) | ((c[0].w >> 30) << 6);
 }
 
-template <bool COH, bool KEEP>
+template <bool COH, bool KEEP, int LREC>
 __device__ __forceinline__ void stencil_direction_i30(const DslashArgs &a, int mu, int cmu, int lex, int cb, int po,
-                                                      size_t pstride, SiteAccI30 &acc)
+                                                      size_t pstride, int phase_sum, SiteAccI30 &acc)
 {
     const Geom &g = a.g;
     const int vh = g.vh, pi = 1 - po;
@@ -468,17 +466,31 @@ __device__ __forceinline__ void stencil_direction_i30(const DslashArgs &a, int m
     load_link_ints<KEEP>(a.gv.fat, pstride, (pi * 4 + mu) * vh + nm1, u);
     E = load_int30_raw<COH>(a.in, vh, nm1, q);
     acc.term<true>(0, u, q, E);
-    load_link_ints<KEEP>(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, u);
-    E = load_int30_raw<COH>(a.in, vh, np3, q);
-    acc.term<false>(1, u, q, E);
-    load_link_ints<KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, u);
+    if constexpr (LREC == 12) {
+        // the sign of a long link: its staggered phase, flipped across an antiperiodic t boundary
+        const int cm3 = wrap_coord(cmu - 3, L);
+        const int eta = (phase_sum & 1) ? -1 : 1;
+        const bool flipf = g.antiperiodic_t && mu == 3 && cmu + 3 >= L;
+        const bool flipb = g.antiperiodic_t && mu == 3 && cm3 + 3 >= L;
+        load_link_ints_r12<KEEP>(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, u, flipf ? -eta : eta,
+                                 a.gv.lng_r2_mul, a.gv.lng_r2_shift);
+        E = load_int30_raw<COH>(a.in, vh, np3, q);
+        acc.term<false>(1, u, q, E);
+        load_link_ints_r12<KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, u, flipb ? -eta : eta,
+                                 a.gv.lng_r2_mul, a.gv.lng_r2_shift);
+    } else {
+        load_link_ints<KEEP>(a.gv.lng, pstride, (po * 4 + mu) * vh + cb, u);
+        E = load_int30_raw<COH>(a.in, vh, np3, q);
+        acc.term<false>(1, u, q, E);
+        load_link_ints<KEEP>(a.gv.lng, pstride, (pi * 4 + mu) * vh + nm3, u);
+    }
     E = load_int30_raw<COH>(a.in, vh, nm3, q);
     acc.term<true>(1, u, q, E);
 }
 
 template <int GF, int SF, typename real, int LREC>
 struct UsesIntPath {
-    static constexpr bool value = GF == G_FIX32 && SF == S_INT30 && is_ff<real>::value && LREC == 18;
+    static constexpr bool value = GF == G_FIX32 && SF == S_INT30 && is_ff<real>::value && (LREC == 18 || LREC == 12);
 };
 
 // One output site cb: the stencil, the optional xpay, the store and, when
@@ -505,13 +517,19 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
         SiteAccI30 acc;
         acc.zero();
         if constexpr (stencil_unrolled(CFG)) {
+            int phase_sum = 0;  // x + y + ... below mu: the staggered phase eta_mu(x)
 #pragma unroll
-            for (int mu = 0; mu < 4; mu++) stencil_direction_i30<COH, KEEP>(a, mu, c[mu], lex, cb, po, pstride, acc);
+            for (int mu = 0; mu < 4; mu++) {
+                stencil_direction_i30<COH, KEEP, LREC>(a, mu, c[mu], lex, cb, po, pstride, phase_sum, acc);
+                phase_sum += c[mu];
+            }
         } else {
+            int phase_sum = 0;
 #pragma unroll 1
             for (int mu = 0; mu < 4; mu++) {
                 const int cmu = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
-                stencil_direction_i30<COH, KEEP>(a, mu, cmu, lex, cb, po, pstride, acc);
+                stencil_direction_i30<COH, KEEP, LREC>(a, mu, cmu, lex, cb, po, pstride, phase_sum, acc);
+                phase_sum += cmu;
             }
         }
         const ff sgn((float)a.sign);

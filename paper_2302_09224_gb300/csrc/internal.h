@@ -2,6 +2,8 @@
 // units (never installed; the public interface is include/hisq.h).
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -175,7 +177,24 @@ struct GaugeView {
     const char *lng;
     float fat_scale_f, lng_scale_f;    // decode scale of fixed point (FP32 compute)
     double fat_scale_d, lng_scale_d;   // decode scale (FP64 compute)
+    // 2 * lng_scale_d = lng_r2_mul * 2^-(32 + lng_r2_shift), lng_r2_mul in [2^30, 2^31): the
+    // integer rescale of a 12-real long link's rebuilt third row (30-bit FP64-class stencil)
+    int lng_r2_mul, lng_r2_shift;
 };
+
+// lng_r2_mul and lng_r2_shift of a view whose lng_scale_d is set
+inline void set_row2_rescale(GaugeView *v)
+{
+    int e = 0;
+    const double f = std::frexp(2.0 * v->lng_scale_d, &e);  // 2s = f 2^e, f in [0.5, 1)
+    long long m = std::llround(std::ldexp(f, 31));
+    if (m >= (1LL << 31)) {
+        m >>= 1;
+        e += 1;
+    }
+    v->lng_r2_mul = (int)m;         // 2s = m 2^(e - 31)
+    v->lng_r2_shift = -1 - e;       // 2^(e - 31) = 2^-(32 + shift)
+}
 
 struct DslashArgs {
     Geom g;
