@@ -97,8 +97,14 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, false, d, s);
     }
     {
+        // the pass alone: its summing launch is a reduction, timed with the BLAS kernels
         LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, true));
+        d2.defer_finish = 1;
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d2, s);
+    }
+    if (fin != FIN_NONE) {
+        LaunchScope ls(c, s, PROF_BLAS, 0.0);
+        launch_dslash_finish(p.gauge, p.spinor, p.compute, p.long_recon, d2, s);
     }
 }
 

@@ -634,8 +634,9 @@ void launch_cfg(const DslashArgs &a, cudaStream_t s)
     const int nb = (a.g.vh + B - 1) / B;
     launch_chained(dslash_kernel<GF, SF, real, LREC, RED, CFG>, dim3(nb), dim3(B), s, a);
     if constexpr (RED)
-        launch_chained(stencil_finish_kernel<real>, dim3(1), dim3(1024), s, a.red, (unsigned)nb, a.fin, a.st, a.slot,
-                       a.active);
+        if (!a.defer_finish)
+            launch_chained(stencil_finish_kernel<real>, dim3(1), dim3(1024), s, a.red, (unsigned)nb, a.fin, a.st,
+                           a.slot, a.active);
 }
 
 template <int GF, int SF, typename real, int LREC, bool RED>

@@ -212,6 +212,7 @@ struct DslashArgs {
     int fin;
     void *st;               // CGState or MSState, per finisher
     int slot;               // ring slot handed to the finisher
+    int defer_finish;       // reducing pass: leave the summing launch to launch_dslash_finish
 };
 
 // The fused M_ee pass (d1: D_oe into tmp; d2: D_eo from tmp with xpay and the
@@ -259,6 +260,8 @@ struct DslashMArgs {
 // no kernel.
 bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const DslashArgs &a,
                    cudaStream_t s);
+// The summing launch of a reducing pass launched with a.defer_finish set.
+bool launch_dslash_finish(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
 // Batched stencil over all right-hand sides in tiles of T (T in {1,2,4,8,16},
 // dividing nrhs), variant 0 (register kernel) or 1 (staged neighbour loads,
 // 16-byte spinor records only); false when the triplet or variant has no
