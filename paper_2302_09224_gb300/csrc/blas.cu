@@ -33,6 +33,35 @@ __device__ __forceinline__ bool nonzero(float v) { return v != 0.0f; }
 __device__ __forceinline__ bool nonzero(double v) { return v != 0.0; }
 __device__ __forceinline__ bool nonzero(ff v) { return v.hi != 0.0f || v.lo != 0.0f; }
 
+// A solver scalar (FP64 in the state) in the compute precision.  For FP32
+// pairs the conversion runs on GB300's narrow FP64 pipe, so one thread of the
+// block converts and the block reads the pair from shared memory.  Every
+// thread of the block calls it, at most once per kernel.
+template <typename real>
+__device__ __forceinline__ real block_scalar(const double *src)
+{
+    if constexpr (is_ff<real>::value) {
+        __shared__ ff sh;
+        if (threadIdx.x == 0) sh = ff(*src);
+        __syncthreads();
+        return sh;
+    } else {
+        return (real)*src;
+    }
+}
+
+// A float as a double, exactly, built from its bits on the integer pipe
+// (zero and normal floats; subnormal, infinite and NaN ones take the
+// conversion instruction).
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (e == 0u || e == 0xffu) return (double)f;
+    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+
 // Sites per thread of the two per-iteration BLAS kernels: every load of a
 // thread's sites is issued before any of them is used (memory-level
 // parallelism for these short, latency-bound kernels).  Four sites a thread
@@ -49,7 +78,7 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
     if (skip(a.active)) return;
     constexpr int U = kRSites, C = Spinor<SF>::chunks;
     red_t<real> v[2] = {0, 0};
-    const real alpha = (real)(a.alpha_src ? *a.alpha_src : a.st->alpha);
+    const real alpha = block_scalar<real>(a.alpha_src ? a.alpha_src : &a.st->alpha);
     // one wave of blocks loops over groups of U sites per thread (see wave_blocks)
     for (int i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < a.n; i0 += gridDim.x * blockDim.x * U) {
         uint4 cr[U][C], ca[U][C];
@@ -132,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
             Spinor<SF>::gather(a.v1, a.n, i, cp[u]);
         }
     }
-    const real beta = (real)a.st->beta;
+    const real beta = block_scalar<real>(&a.st->beta);
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const int i = i0 + u * blockDim.x;
@@ -155,6 +184,9 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
     pdl_launch_dependents();
     if (skip(a.active)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ real al_s[kMaxBuf];  // the step sizes in the compute precision, converted once per block
+    if (threadIdx.x < kMaxBuf) al_s[threadIdx.x] = threadIdx.x < a.nslots ? (real)a.st->alpha_ring[threadIdx.x] : real(0);
+    __syncthreads();
     if (i >= a.n) return;
     constexpr int G = 4, C = Spinor<SF>::chunks;  // slots whose loads are in flight together
     uint4 cx[Spinor<S_F64>::chunks];
@@ -168,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
 #pragma unroll
         for (int g = 0; g < G; g++) {
             const int j = j0 + g;
-            al[g] = j < a.nslots ? (real)a.st->alpha_ring[j] : real(0);
+            al[g] = j < a.nslots ? al_s[j] : real(0);
             if (nonzero(al[g])) Spinor<SF>::gather(a.v0 + (size_t)j * a.slot_bytes, a.n, i, cp[g]);
         }
 #pragma unroll
@@ -183,7 +215,12 @@ __global__ void __launch_bounds__(kBlock) x_flush_kernel(BlasArgs a)
     double x[6];
     Spinor<S_F64>::decode(cx, x);
 #pragma unroll
-    for (int k = 0; k < 6; k++) x[k] += (double)dx[k];
+    for (int k = 0; k < 6; k++) {
+        if constexpr (is_ff<real>::value)  // hi and lo widened on the integer pipe: two FP64 adds per real
+            x[k] += f2d_bits(dx[k].hi) + f2d_bits(dx[k].lo);
+        else
+            x[k] += (double)dx[k];
+    }
     Spinor<S_F64>::store(reinterpret_cast<char *>(a.x64), a.n, i, x);
 }
 

@@ -56,6 +56,15 @@ __global__ void __launch_bounds__(kBlock) shift_update_kernel(MSArgs a)
     constexpr int AF = is_ff<real>::value ? S_FF : sizeof(real) == 8 ? S_F64 : S_F32;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const MSState *m = a.m;
+    // the shifts' step sizes in the compute precision, converted once per block (for FP32 pairs
+    // the conversion runs on the narrow FP64 pipe)
+    __shared__ real cs[3][kMaxShift];
+    if (threadIdx.x < a.nshift) {
+        cs[0][threadIdx.x] = (real)m->alpha_i[threadIdx.x];
+        cs[1][threadIdx.x] = (real)m->zeta[threadIdx.x];
+        cs[2][threadIdx.x] = (real)m->beta_i[threadIdx.x];
+    }
+    __syncthreads();
     if (i < a.n) {
         real r[6];
         Spinor<SF>::load(a.r, a.n, i, r);
@@ -66,7 +75,7 @@ __global__ void __launch_bounds__(kBlock) shift_update_kernel(MSArgs a)
             char *xs = a.acc + (size_t)s * a.acc_bytes;
             Spinor<SF>::load(ps, a.n, i, p);
             Spinor<AF>::load(xs, a.n, i, x);
-            const real al = (real)m->alpha_i[s], z = (real)m->zeta[s], be = (real)m->beta_i[s];
+            const real al = cs[0][s], z = cs[1][s], be = cs[2][s];
 #pragma unroll
             for (int k = 0; k < 6; k++) {
                 x[k] += al * p[k];
