@@ -561,6 +561,32 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
 #pragma unroll
     for (int k = 0; k < 6; k++) o[k] = sf * acc.get(k);
     }
+    if constexpr (RED && UsesIntPath<GF, SF, real, LREC>::value) {
+        // FP64-class: Re<y, out> and |out|^2 exactly in integers from the stored 30-bit records
+        int32_t qy[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t Ey = 0;
+        if (a.xpay) {
+            uint4 cy[Spinor<S_INT30>::chunks];
+            Spinor<S_INT30>::gather(a.y, vh, cb, cy);
+            Ey = Spinor<S_INT30>::raw(cy, qy);
+            real yv[6];
+            Spinor<S_INT30>::decode(cy, yv);
+            const real aa = (real)a.a;
+#pragma unroll
+            for (int k = 0; k < 6; k++) o[k] = aa * yv[k] + o[k];
+        }
+        uint32_t qo[6], Eo;
+        if (!Spinor<S_INT30>::store_ff_q(a.out, vh, cb, o, qo, Eo)) atomicExch(a.err, 1);
+        long long d = 0, n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(d) : "r"(qy[k]), "r"((int)qo[k]));
+            asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(n2) : "r"((int)qo[k]));
+        }
+        if (a.xpay) rv[0] += ff_ldexp(ff_from_ll(d), (int)Ey + (int)Eo - 254);  // a record is q 2^(E-127)
+        rv[1] += ff_ldexp(ff_from_ll(n2), 2 * (int)Eo - 254);
+        return;
+    }
     if (a.xpay) {
         real yv[6];
         Spinor<SF>::load(a.y, vh, cb, yv);
