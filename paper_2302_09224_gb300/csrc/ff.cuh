@@ -88,12 +88,25 @@ __device__ __forceinline__ ff ff_ldexp(ff a, int e)
                     __uint_as_float((uint32_t)(e2 + 127) << 23));
 }
 
-// A 64-bit integer as a pair: hi its FP32 rounding, lo the FP32 rounding of
-// the exact remainder (|s| < 2^62: about 48 significant bits, like any pair).
-__device__ __forceinline__ ff ff_from_ll(long long s)
+// A 64-bit integer as a pair, on the FP32 and integer pipes only (the 64-bit
+// conversion instructions run on GB300's narrow FP64 pipe): P = c2 2^42 +
+// c1 2^21 + c0 with c2 the arithmetic top 22 bits and c1, c0 21-bit fields,
+// each exact in FP32 (the field placed in the mantissa of 2^23, or of 2^23 +
+// 2^22 for the signed one, and the offset subtracted), scaled by exact powers
+// of two; the top two summed error-free, the low one added to the tail (about
+// 45 significant bits or more, like any pair).
+__device__ __forceinline__ ff ff_from_ll(long long P)
 {
-    const float hi = __ll2float_rn(s);
-    return ff(hi, __ll2float_rn(s - __float2ll_rn(hi)));
+    const unsigned lo = (unsigned)P, hi = (unsigned)((unsigned long long)P >> 32);
+    const unsigned c0 = lo & 0x1FFFFFu;
+    const unsigned c1 = __funnelshift_r(lo, hi, 21) & 0x1FFFFFu;
+    const int c2 = (int)hi >> 10;  // bits 42..63 with the sign: |c2| <= 2^21
+    const float f0 = __fsub_rn(__uint_as_float(0x4B000000u | c0), 8388608.0f);
+    const float f1 = __fmul_rn(__fsub_rn(__uint_as_float(0x4B000000u | c1), 8388608.0f), 2097152.0f);
+    const float f2 = __fmul_rn(__fsub_rn(__uint_as_float(0x4B000000u | (unsigned)(c2 + 0x400000)), 12582912.0f),
+                               4398046511104.0f);
+    const ff s = ff_two_sum(f2, f1);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, f0));
 }
 
 template <typename T>
