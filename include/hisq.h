@@ -468,7 +468,11 @@ typedef struct {
  * take requests in arrival order.  CG requests on the same gauge field with
  * the same sloppy triplet (FP32, half or 20-bit) share batch sessions: at
  * every block of iterations finished systems leave and queued ones join
- * (continuous batching); multi-shift requests run one per worker.  A session
+ * (continuous batching).  A multi-shift request runs its multi-shift stage
+ * on a worker; the refinement CG of each shift that has not reached its
+ * target (the shifted system from the stage's solution, in the request's
+ * refine triplet; unlike hisq_multishift_cg, the base system restarts too)
+ * then joins the batch sessions like a CG request.  A session
  * starts only when the context's HBM budget has room for it; otherwise its
  * requests wait.  b and x stay owned by the caller and must stay valid until
  * the request is done; the gauge must not be freed while requests use it.

@@ -65,6 +65,14 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
 hisq_status run_cg(hisq_ctx *c, hisq_gauge *g, const CGConfig &cfg, const double *b64, double *x64, bool x_zero,
                    hisq_solve_info *info, cudaStream_t s);
 
+// The multi-shift stage alone (Sec. 3.2, without the refinement CG): shifts in
+// ascending order, b64 and x64_out[i] device FP64 planar fields (x64_out
+// owned by the caller, 48 Vh bytes each); info->shift_resid[i] is each
+// shift's FP64 true residual over |b| after the stage.
+hisq_status run_multishift_stage(hisq_ctx *c, hisq_gauge *g, const hisq_solver_params &p, int ns, const double *sigma,
+                                 const double *tol, const double *b64, double *const *x64_out, hisq_solve_info *info,
+                                 cudaStream_t s);
+
 hisq_status validate_params(hisq_ctx *c, const hisq_solver_params *p);
 CGConfig config_from(const hisq_solver_params *p, double sigma);
 hisq_status to_planar(hisq_ctx *c, Workspace &ws, const double *user, int on_device, int64_t n, double *planar,

@@ -298,7 +298,8 @@ struct MSRun {
         }
     }
 
-    hisq_status run(const double *b64_, int nshift, const double *sigma, const double *tolv, hisq_solve_info *info)
+    hisq_status run(const double *b64_, int nshift, const double *sigma, const double *tolv, hisq_solve_info *info,
+                    bool refine = true)
     {
         b64 = b64_;
         ns = nshift;
@@ -431,7 +432,11 @@ struct MSRun {
             info->shift_resid_ms[i] = rs[i];
             info->shift_resid[i] = rs[i];
         }
-        if (status == HISQ_EBREAKDOWN) return status;
+        if (status == HISQ_EBREAKDOWN || !refine) {
+            info->matvecs_hi += mv_hi;
+            info->true_residual = info->shift_resid[0];
+            return status;
+        }
         const double rr_base = mh->rr;
         // refinement: the base system keeps its gradient vector, the others restart
         hisq_status worst = status;
@@ -465,6 +470,20 @@ struct MSRun {
 };
 
 }  // namespace
+
+hisq_status run_multishift_stage(hisq_ctx *c, hisq_gauge *g, const hisq_solver_params &p, int ns, const double *sigma,
+                                 const double *tol, const double *b64, double *const *x64_out, hisq_solve_info *info,
+                                 cudaStream_t s)
+{
+    MSRun run(c, g, p, s);
+    const hisq_status st = run.run(b64, ns, sigma, tol, info, false);
+    if (st != HISQ_OK && st != HISQ_ENOTCONV && st != HISQ_EBREAKDOWN) return st;
+    for (int i = 0; i < ns; i++)
+        cudaMemcpyAsync(x64_out[i], run.x64(i), (size_t)48 * g->geom.vh, cudaMemcpyDeviceToDevice, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "multi-shift stage results");
+    return st;
+}
 
 }  // namespace hisq
 

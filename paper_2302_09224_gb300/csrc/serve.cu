@@ -7,8 +7,13 @@
 // finished systems are harvested and refilled from the queue (continuous
 // batching), so a request that arrives while others iterate joins them as
 // soon as a slot frees up.  Sessions are admitted only while the context's
-// HBM budget allows their buffers; otherwise their requests wait.  Multi-shift
-// requests run one at a time per worker.
+// HBM budget allows their buffers; otherwise their requests wait.  A
+// multi-shift request runs its multi-shift stage (all shifts in one fused
+// update per iteration) on a worker; the refinement CG of each shift that has
+// not reached its target then enters the queue as an internal CG request
+// (its shifted diagonal, its target, the stage's solution as initial guess),
+// so the refinements join the batch sessions of their sloppy triplet beside
+// ordinary CG requests; the request is done when its last refinement is.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +23,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <numeric>
 #include <memory>
 #include <set>
 #include <string>
@@ -38,6 +44,8 @@ double now_s()
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+struct MSJob;
+
 struct Req {
     uint64_t ticket = 0;
     hisq_request r{};
@@ -46,6 +54,25 @@ struct Req {
     bool done = false;
     hisq_status status = HISQ_OK;
     hisq_solve_info info{};
+    // a refinement of one shift of a multi-shift request: planar FP64 right-hand
+    // side and initial guess on the device, the shifted diagonal 4m^2 + sigma
+    std::shared_ptr<MSJob> job;
+    int shift = -1;
+    const double *b_planar = nullptr, *x0_planar = nullptr;
+    double diag = 0;
+};
+
+// A multi-shift request between its stage and its last refinement: the device
+// fields the refinements read (freed with the job) and the merged report.
+struct MSJob {
+    std::shared_ptr<Req> parent;
+    std::unique_ptr<Workspace> ws;
+    double *b64 = nullptr;
+    std::vector<double *> x64;
+    std::vector<int> ord;  // sorted shift -> the caller's index
+    int remaining = 0;
+    hisq_solve_info info{};  // per shift in sorted order until the end
+    hisq_status worst = HISQ_OK;
 };
 
 using Key = std::tuple<const hisq_gauge *, int, int, int, int, int, int>;
@@ -89,8 +116,45 @@ struct Server {
         return sizeof(double) * ((size_t)kMaxRedBlocks * kMaxRed + kMaxRed) + 256 + sizeof(unsigned) * kSyncWords;
     }
 
+    // the merged report of a multi-shift request in the caller's shift order
+    static void report_ms(MSJob &j, hisq_solve_info *out)
+    {
+        *out = j.info;
+        const int ns = (int)j.ord.size();
+        for (int i = 0; i < ns; i++) {
+            out->shift_iters[j.ord[i]] = j.info.shift_iters[i];
+            out->shift_resid_ms[j.ord[i]] = j.info.shift_resid_ms[i];
+            out->shift_resid[j.ord[i]] = j.info.shift_resid[i];
+            out->refine_iters[j.ord[i]] = j.info.refine_iters[i];
+        }
+        out->true_residual = j.info.shift_resid[0];
+    }
+
     void finish(const std::shared_ptr<Req> &q, hisq_status st, const hisq_solve_info &info)
     {
+        if (q->job) {  // a refinement: merge into its multi-shift request
+            std::shared_ptr<Req> parent;
+            hisq_solve_info rep{};
+            hisq_status pst = HISQ_OK;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                MSJob &j = *q->job;
+                j.info.refine_iters[q->shift] = info.iters;
+                j.info.shift_resid[q->shift] = info.true_residual;
+                j.info.matvecs += info.matvecs;
+                j.info.matvecs_hi += info.matvecs_hi;
+                j.info.reliable_updates += info.reliable_updates;
+                if (st != HISQ_OK && (j.worst == HISQ_OK || j.worst == HISQ_ENOTCONV)) j.worst = st;
+                if (--j.remaining == 0) {
+                    parent = j.parent;
+                    report_ms(j, &rep);
+                    pst = j.worst;
+                }
+            }
+            q->job.reset();
+            if (parent) finish(parent, pst, rep);
+            return;
+        }
         std::lock_guard<std::mutex> lk(mu);
         q->status = st;
         q->info = info;
@@ -143,17 +207,95 @@ void Server::run_single(const std::shared_ptr<Req> &q, cudaStream_t s)
     p.on_device = q->r.on_device;
     p.stream = s;
     hisq_solve_info info{};
-    hisq_status st;
-    if (q->r.kind == HISQ_REQ_MULTISHIFT) {
-        const int ns = q->r.nshift;
-        std::vector<double *> xs(ns);
-        const size_t f = (size_t)6 * q->r.gauge->geom.vh;
-        for (int i = 0; i < ns; i++) xs[i] = q->r.x + i * f;
-        st = hisq_multishift_cg(c, q->r.gauge, &p, ns, q->sigma.data(), q->tols.data(), q->r.b, xs.data(), &info);
-    } else {
-        st = hisq_cg(c, q->r.gauge, &p, q->r.b, q->r.x, &info);
+    hisq_gauge *g = const_cast<hisq_gauge *>(q->r.gauge);
+    const int64_t vh = g->geom.vh;
+    if (q->job) {  // a refinement whose triplet has no batch session: the single-system CG from its guess
+        CGConfig cfg = config_from(&p, q->diag - 4.0 * p.mass * p.mass);
+        Workspace ws(c, s);
+        double *x64 = nullptr;
+        hisq_status st = ws.alloc((size_t)48 * vh, (void **)&x64);
+        if (!st) {
+            cudaMemcpyAsync(x64, q->x0_planar, (size_t)48 * vh, cudaMemcpyDeviceToDevice, s);
+            st = run_cg(c, g, cfg, q->b_planar, x64, false, &info, s);
+            if (st == HISQ_OK || st == HISQ_ENOTCONV || st == HISQ_EBREAKDOWN) {
+                const hisq_status e = from_planar(c, ws, x64, vh, q->r.x, q->r.on_device, s);
+                if (e) st = e;
+            }
+        }
+        finish(q, st, info);
+        return;
     }
-    finish(q, st, info);
+    if (q->r.kind != HISQ_REQ_MULTISHIFT) {
+        finish(q, hisq_cg(c, q->r.gauge, &p, q->r.b, q->r.x, &info), info);
+        return;
+    }
+    // multi-shift: the stage here, then one refinement request per shift that needs one
+    const int ns = q->r.nshift;
+    auto job = std::make_shared<MSJob>();
+    job->parent = q;
+    job->ws = std::make_unique<Workspace>(c, nullptr);
+    job->ord.resize(ns);
+    std::iota(job->ord.begin(), job->ord.end(), 0);
+    std::stable_sort(job->ord.begin(), job->ord.end(), [&](int a, int b) { return q->sigma[a] < q->sigma[b]; });
+    std::vector<double> ss(ns), tt(ns);
+    for (int i = 0; i < ns; i++) {
+        ss[i] = q->sigma[job->ord[i]];
+        tt[i] = q->tols[job->ord[i]];
+    }
+    hisq_status st = job->ws->alloc((size_t)48 * vh, (void **)&job->b64);
+    job->x64.assign(ns, nullptr);
+    for (int i = 0; i < ns && !st; i++) st = job->ws->alloc((size_t)48 * vh, (void **)&job->x64[i]);
+    if (!st) st = to_planar(c, *job->ws, q->r.b, q->r.on_device, vh, job->b64, s);
+    if (!st) {
+        for (int i = 0; i < ns && !st; i++) {
+            if (4.0 * p.mass * p.mass + ss[i] <= 0.0 || !std::isfinite(ss[i]) || !(tt[i] > 0.0))
+                st = fail(c, HISQ_EINVAL, "shift %d: 4m^2 + sigma must be positive, tol > 0", i);
+        }
+    }
+    if (!st) st = run_multishift_stage(c, g, p, ns, ss.data(), tt.data(), job->b64, job->x64.data(), &job->info, s);
+    if (st != HISQ_OK && st != HISQ_ENOTCONV && st != HISQ_EBREAKDOWN) {
+        hisq_solve_info none{};
+        finish(q, st, none);
+        return;
+    }
+    job->worst = st;
+    const size_t f = (size_t)6 * vh;
+    std::vector<std::shared_ptr<Req>> subs;
+    for (int i = 0; i < ns; i++) {
+        double *xi = q->r.x + job->ord[i] * f;
+        if (st == HISQ_EBREAKDOWN || job->info.shift_resid[i] <= tt[i]) {  // done after the stage
+            const hisq_status e = from_planar(c, *job->ws, job->x64[i], vh, xi, q->r.on_device, s);
+            if (e) {
+                hisq_solve_info none{};
+                finish(q, e, none);
+                return;
+            }
+            continue;
+        }
+        auto r = std::make_shared<Req>();
+        r->r = q->r;
+        r->r.kind = HISQ_REQ_CG;
+        r->r.sloppy = q->r.refine;
+        r->r.tol = tt[i];
+        r->r.x = xi;
+        r->job = job;
+        r->shift = i;
+        r->b_planar = job->b64;
+        r->x0_planar = job->x64[i];
+        r->diag = 4.0 * p.mass * p.mass + ss[i];
+        r->t_submit = now_s();
+        subs.push_back(r);
+    }
+    if (subs.empty()) {
+        hisq_solve_info rep{};
+        report_ms(*job, &rep);
+        finish(q, st, rep);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    job->remaining = (int)subs.size();
+    for (auto it = subs.rbegin(); it != subs.rend(); ++it) pending.push_front(*it);  // ahead of new requests
+    cv_work.notify_all();
 }
 
 void Server::run_batch(const std::shared_ptr<Req> &first, cudaStream_t s)
@@ -202,6 +344,8 @@ void Server::run_batch(const std::shared_ptr<Req> &first, cudaStream_t s)
         return;
     }
     auto load_one = [&](int t, const std::shared_ptr<Req> &q) -> hisq_status {
+        if (q->b_planar)  // a refinement: its fields are already planar on the device
+            return bs.load(t, q->b_planar, q->x0_planar, q->diag, q->r.tol);
         const double *src = q->r.b;
         if (!q->r.on_device) {
             cudaMemcpyAsync(aos, q->r.b, (size_t)48 * vh, cudaMemcpyHostToDevice, s);
