@@ -281,8 +281,9 @@ def run_ours(args):
     shapes = {"plain": hisq.hisq_stencil_config_in_use(g, p.sloppy, False),
               "reducing": hisq.hisq_stencil_config_in_use(g, p.sloppy, True)}
     hisq.hisq_profile_reset(ctx)
-    # the timed solves carry event pairs around the stencil launches only, in one block of iterations
-    # out of PROF_EVERY (each pair costs device time; the other blocks run an identical graph without them)
+    # the timed solves carry event pairs around the stencil launches only (one pair around the two
+    # passes of each M_ee, counted as two launches), in one block of iterations out of PROF_EVERY (each
+    # pair costs device time; the other blocks run an identical graph without them)
     hisq.hisq_profile_select(ctx, 1 << hisq.HISQ_PROF_STENCIL)
     hisq.hisq_profile_sample(ctx, PROF_EVERY)
     torch.cuda.synchronize()
@@ -500,8 +501,8 @@ def run_ours(args):
                      "kernel": ("mee_fused_kernel<FIX16, INT20, float, r12> (M_ee in one pass, links once)"
                                 if args.fused else "dslash_kernel<FIX16, INT20, float, r12> (both passes of M_ee)"),
                      "bytes_per_launch": per_launch_bytes, "launches": stencil.launches,
-                     "sampling": f"event pairs around the stencil launches of one block of iterations in "
-                                 f"{PROF_EVERY} of the timed solves",
+                     "sampling": f"one event pair around the two stencil launches of each M_ee (their mean: half "
+                                 f"the span) in one block of iterations in {PROF_EVERY} of the timed solves",
                      "launch_shapes": shapes,
                      "ms_per_launch": stencil.ms / max(1, stencil.launches)},
         "blas": {"achieved_gbs": blas0.bytes / (blas0.ms / 1e3) / 1e9 if blas0.ms > 0 else 0.0,

@@ -93,12 +93,11 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
         if (launch_mee_fused(p.gauge, p.spinor, p.compute, p.long_recon, m, s)) return;
     }
     {
-        LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, false));
+        // both passes under one event pair, counted as two launches (their average duration is half
+        // the span, and no event node breaks the programmatic dependent launch between them); the
+        // reducing pass's summing launch is a reduction, timed with the BLAS kernels
+        LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, false) + stencil_bytes(p, geom.vh, true), 2);
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, false, d, s);
-    }
-    {
-        // the pass alone: its summing launch is a reduction, timed with the BLAS kernels
-        LaunchScope ls(c, s, kind, stencil_bytes(p, geom.vh, true));
         d2.defer_finish = 1;
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d2, s);
     }

@@ -97,15 +97,15 @@ bool stream_capturing(cudaStream_t s)
     return st != cudaStreamCaptureStatusNone;
 }
 
-LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_)
-    : c(c_), s(s_), kind(kind_), bytes(bytes_), tag(tl_prof_tag)
+LaunchScope::LaunchScope(hisq_ctx *c_, cudaStream_t s_, int kind_, double bytes_, int nl_)
+    : c(c_), s(s_), kind(kind_), bytes(bytes_), tag(tl_prof_tag), nl(nl_)
 {
     const bool sel = c->prof.on && ((c->prof.mask >> kind) & 1u);
     if (thread_capturing()) {  // launches are counted when the graph is replayed
         if (!sel || !tl_graph_rec) return;
         in_graph = true;
     } else {
-        c->launches += 1;
+        c->launches += nl;
         if (!sel || stream_capturing(s)) return;
     }
     std::lock_guard<std::mutex> lk(c->prof_mu);
@@ -132,12 +132,12 @@ LaunchScope::~LaunchScope()
     if (!a) return;
     if (in_graph) {
         cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
-        tl_graph_rec->push_back({a, b, kind, bytes, tag});
+        tl_graph_rec->push_back({a, b, kind, bytes, tag, nl});
         return;
     }
     cudaEventRecord(b, s);
     std::lock_guard<std::mutex> lk(c->prof_mu);
-    c->prof.pending.push_back({a, b, kind, bytes, tag});
+    c->prof.pending.push_back({a, b, kind, bytes, tag, nl});
     if (c->prof.pending.size() > 4096) prof_flush_locked(c);
 }
 
@@ -182,7 +182,7 @@ void prof_graph_account(hisq_ctx *c, const std::vector<Profiler::Rec> &recs, int
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             c->prof.ms[r.kind] += ms;
-            c->prof.launches[r.kind] += 1;
+            c->prof.launches[r.kind] += r.nl;
             c->prof.bytes[r.kind] += r.bytes;
         }
     }
@@ -211,7 +211,7 @@ void prof_flush_locked(hisq_ctx *c)
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             c->prof.ms[r.kind] += ms;
-            c->prof.launches[r.kind] += 1;
+            c->prof.launches[r.kind] += r.nl;
             c->prof.bytes[r.kind] += r.bytes;
         }
         c->prof.pool.push_back(r.a);

@@ -339,6 +339,7 @@ struct Profiler {
         int kind;
         double bytes;
         int tag;  // iteration within a solver's block (-1: always counted), see prof_settle
+        int nl;   // kernel launches between the two events
     };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
@@ -402,9 +403,11 @@ struct LaunchScope {
     int kind;
     double bytes;
     int tag = -1;
+    int nl = 1;
     bool in_graph = false;
     cudaEvent_t a = nullptr, b = nullptr;
-    LaunchScope(hisq_ctx *c, cudaStream_t s, int kind, double bytes);
+    // nl: the launches the scope encloses (counted as nl launches of kind)
+    LaunchScope(hisq_ctx *c, cudaStream_t s, int kind, double bytes, int nl = 1);
     ~LaunchScope();
 };
 void prof_flush(hisq_ctx *c);   // resolve pending event pairs (synchronises on them)
