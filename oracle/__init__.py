@@ -64,6 +64,7 @@ def _load():
         "or_int20_unpack": (None, [_i64, _p, _p]),
         "or_int30_pack": (_i64, [_i64, _p, _p]),
         "or_int30_unpack": (None, [_i64, _p, _p]),
+        "or_ru_trigger_first": (_i, [_i, _p, _p, _d]),
         "or_int14_pack": (_i64, [_i64, _p, _p]),
         "or_int14_unpack": (None, [_i64, _p, _p]),
         "or_absmax": (_d, [_i64, _p]),
@@ -198,6 +199,14 @@ def int20_unpack(w):
     out = np.empty((ww.shape[0], 6), dtype=np.float32)
     _load().or_int20_unpack(ww.shape[0], _ptr(ww), _ptr(out))
     return out
+
+
+def ru_trigger_first(r, alpha_ap, eps: float) -> int:
+    """First step k at which the error-estimate trigger fires on |r_0..r_n| and |alpha_k| |A p_k|."""
+    rr = _np(r).reshape(-1)
+    aa = _np(alpha_ap).reshape(-1)
+    assert len(aa) == len(rr) - 1
+    return int(_load().or_ru_trigger_first(len(aa), _ptr(rr), _ptr(aa), float(eps)))
 
 
 def int14_pack(v):

@@ -23,12 +23,11 @@
  * with links that already carry the staggered phases, M = 2m + D on the full
  * lattice and M_ee = 4m^2 - D_eo D_oe on the even sites.
  *
- * Parity unpinned: the iteration at which or_mixed_cg's error-estimate
- * trigger fires (a heuristic the paper only names): it is checked through its
- * limits (no update as its precision vanishes, more updates the coarser the
- * precision) and through convergence, not against fixed counts.  Every other
- * function is checked against closed forms, invariants, hand-derived bit
- * patterns or a dense direct solve by the tests.
+ * Every function is checked against closed forms, invariants, hand-derived
+ * bit patterns or a dense direct solve by the tests; the error-estimate
+ * trigger's rule (or_ru_trigger_step) against its closed form on geometric
+ * residual sequences, its use inside or_mixed_cg through its limits and
+ * convergence.
  */
 #include <complex.h>
 #include <math.h>
@@ -837,6 +836,32 @@ int or_cg(const int *L, const double *fat, const double *lng, double m, double s
  * the recomputed true residual at the iterations that end with a reliable
  * update (the jumps of Fig. 1).  Returns 0 on convergence, 1 at maxiter, 2
  * on breakdown (p^+ A p <= 0 or non-finite). */
+/* One step of the error-estimate reliable-update trigger (Sec. 3 footnote,
+ * read after van der Vorst and Ye's residual replacement): the drift estimate
+ * grows by the rounding of the step, d_new = d + eps (|r_{k+1}| +
+ * |alpha_k| |A p_k|); an update is due when d crosses sqrt(eps) |r| in this
+ * step (d <= sqrt(eps) |r_k| and d_new > sqrt(eps) |r_{k+1}|) and d_new >
+ * 1.1 d_init.  Returns 1 when due, 0 otherwise; *d_out = d_new. */
+int or_ru_trigger_step(double eps, double d, double d_init, double r_k, double r_k1, double alpha_ap, double *d_out)
+{
+    const double h = sqrt(eps);
+    const double dn = d + eps * (r_k1 + alpha_ap);
+    *d_out = dn;
+    return d <= h * r_k && dn > h * r_k1 && dn > 1.1 * d_init;
+}
+
+/* The first step k (0-based: the step from r_k to r_{k+1}) at which the
+ * trigger fires on the sequences r[0..n] and alpha_ap[0..n-1], starting from
+ * d = d_init = eps r[0]; -1 if it never does. */
+int or_ru_trigger_first(int n, const double *r, const double *alpha_ap, double eps)
+{
+    double d = eps * r[0];
+    const double d_init = d;
+    for (int k = 0; k < n; k++)
+        if (or_ru_trigger_step(eps, d, d_init, r[k], r[k + 1], alpha_ap[k], &d)) return k;
+    return -1;
+}
+
 int or_mixed_cg(const int *L, const double *fat, const double *lng, const double *fat_s,
                 const double *lng_s, double m, int sfmt, const double *b_, double *x_, double tol,
                 double delta, double dyn_eps, int nbuf, int opts, int maxiter, int *iters, int *reliable,
@@ -865,7 +890,6 @@ int or_mixed_cg(const int *L, const double *fat, const double *lng, const double
     STORE(r, rh);
     memcpy(p, r, sizeof(cplx) * n);
     double rr = nrm2(n, r), rmax = sqrt(rr);
-    const double eps_hat = sqrt(dyn_eps > 0.0 ? dyn_eps : 0.0);
     double d = dyn_eps * sqrt(rr), d_init = d;
     int k = 0, ru = 0, status = 1;
     if (hist) hist[0] = sqrt(rr / bb);
@@ -890,9 +914,9 @@ int or_mixed_cg(const int *L, const double *fat, const double *lng, const double
         if (nring == nbuf) FLUSH();
         int trigger = sqrt(rr_new) <= tol * sqrt(bb);
         if (dyn_eps > 0.0) {
-            const double d_new = d + dyn_eps * (sqrt(rr_new) + fabs(alpha) * sqrt(nrm2(n, Ap)));
-            trigger = trigger ||
-                      (d <= eps_hat * sqrt(rr) && d_new > eps_hat * sqrt(rr_new) && d_new > 1.1 * d_init);
+            double d_new = d;
+            trigger = or_ru_trigger_step(dyn_eps, d, d_init, sqrt(rr), sqrt(rr_new),
+                                         fabs(alpha) * sqrt(nrm2(n, Ap)), &d_new) || trigger;
             d = d_new;
         } else {
             trigger = trigger || sqrt(rr_new) < delta * rmax;

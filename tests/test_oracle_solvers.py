@@ -24,6 +24,8 @@
   bit; at a light mass 20-bit storage needs fewer operator applications than
   16-bit storage, the ordering of Table 2.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -318,3 +320,31 @@ def test_mixed_cg_error_estimate_trigger_converges(orc, sfmt, gf, eps):
     assert hist[-1] == pytest.approx(tr, rel=1e-12)
     r = b - orc.mee(dims, fat, lng, m, x)
     assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(tr, rel=1e-6)
+
+
+@pytest.mark.parametrize("rho,c,eps", [(0.9, 0.5, 2.0 ** -15), (0.8, 2.0, 2.0 ** -19), (0.95, 0.1, 2.0 ** -29),
+                                       (0.7, 0.0, 2.0 ** -24)])
+def test_ru_trigger_closed_form(orc, rho, c, eps):
+    """The error-estimate trigger's rule on a geometric sequence |r_k| = rho^k with |alpha_k| |A p_k| =
+    c rho^k: the drift estimate is d_k = eps (1 + A (1 - rho^k)), A = (rho + c) / (1 - rho), which
+    first exceeds sqrt(eps) |r_m| at the smallest m with rho^m < Q = sqrt(eps) (1 + A) / (1 + sqrt(eps) A);
+    the trigger fires in the step that ends there, k = m - 1 (with d_m far above 1.1 d_0)."""
+    A = (rho + c) / (1 - rho)
+    h = math.sqrt(eps)
+    Q = h * (1 + A) / (1 + h * A)
+    t = math.log(Q) / math.log(rho)
+    assert abs(t - round(t)) > 1e-6  # not on the boundary, where rounding would decide
+    m = math.floor(t) + 1
+    n = m + 10
+    r = rho ** np.arange(n + 1, dtype=float)
+    aa = c * rho ** np.arange(n, dtype=float)
+    assert orc.ru_trigger_first(r, aa, eps) == m - 1
+
+
+def test_ru_trigger_guards(orc):
+    """A drift that crosses sqrt(eps) |r| within its first 10 % never fires (it starts above the
+    threshold from then on), and as eps vanishes the estimate never crosses it."""
+    r = 0.01 ** np.arange(6, dtype=float)
+    assert orc.ru_trigger_first(r, np.zeros(5), 0.01) == -1
+    r = 0.9 ** np.arange(101, dtype=float)
+    assert orc.ru_trigger_first(r, 0.5 * r[:-1], 1e-300) == -1
