@@ -97,3 +97,34 @@ def test_graph_matches_direct(ctx):
     _, i2, x2 = run(ctx, dims, fat, lng, m, b, "int20", use_graph=0)
     np.testing.assert_array_equal(x1, x2)
     assert i1.matvecs == i2.matvecs
+
+
+def u3_links(lng, seed):
+    """Long links times a random phase per link: unitary, no longer a sign times SU(3)."""
+    u = lng[..., 0] + 1j * lng[..., 1]
+    g = np.random.Generator(np.random.Philox(key=seed))
+    w = u * np.exp(1j * g.uniform(-np.pi, np.pi, u.shape[:-2]))[..., None, None]
+    return np.ascontiguousarray(np.stack([w.real, w.imag], axis=-1))
+
+
+@pytest.mark.parametrize("name,recon", [("f32", 13), ("half", 13), ("int14", 12)])
+def test_bicgstab_other_formats(ctx, orc, name, recon):
+    """BiCGStab(2) on 2m + D with U(3) long links in 13 reals, and with the 12-byte 14-bit fermion:
+    the FP64 true residual recomputed by the oracle meets the target."""
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = (t.numpy() for t in synth.gauge_pair(dims, seed=0))
+    if recon == 13:
+        lng = u3_links(lng, 11)
+    b = synth.spinor(dims, 1000, full=True).numpy()
+    g = hisq.hisq_load_gauge(ctx, dims, torch.as_tensor(fat).cuda(), torch.as_tensor(lng).cuda())
+    try:
+        p = hisq.hisq_default_params()
+        p.mass, p.tol, p.on_device, p.l = m, 1e-10, 1, 2
+        p.sloppy = hisq.prec(name, recon)
+        bd = torch.as_tensor(b).cuda()
+        x = torch.zeros_like(bd)
+        st, info = hisq.hisq_bicgstabl(ctx, g, p, bd, x)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+    assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+    assert true_res(orc, dims, fat, lng, m, b, x.cpu().numpy()) <= 1e-10

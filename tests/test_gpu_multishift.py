@@ -113,3 +113,39 @@ def test_single_shift_and_invalid(ctx, orc):
         run_ms(ctx, dims, fat, lng, m, b, [0.1] * 33, [1e-8] * 33)
     with pytest.raises(hisq.HisqError, match="EINVAL"):
         run_ms(ctx, dims, fat, lng, m, b, [0.1, -1.0], [1e-8, 1e-8])
+
+
+def rotated(lng):
+    """Long links times a fixed SU(3) matrix with every |element|^2 = 1/3 (far from diagonal)."""
+    w = np.exp(2j * np.pi / 3)
+    f = np.array([[1, 1, 1], [1, w, w * w], [1, w * w, w]]) / np.sqrt(3)
+    f = f / np.linalg.det(f) ** (1.0 / 3.0)
+    u = lng[..., 0] + 1j * lng[..., 1]
+    r = np.einsum("ij,...jk->...ik", f, u)
+    return np.ascontiguousarray(np.stack([r.real, r.imag], axis=-1))
+
+
+@pytest.mark.parametrize("stage,refine", [(("int20", 8), ("int20", 13)), (("int14", 12), ("int14", 12))])
+def test_multishift_other_formats(ctx, orc, stage, refine):
+    """The multi-shift stage and its refinement with 8- and 13-real long links (Sec. 1) and with the
+    12-byte 14-bit fermion: every shift meets its target by the oracle's FP64 residual."""
+    dims, m = (8, 8, 8, 8), 0.02
+    fat, lng = (t.numpy() for t in synth.gauge_pair(dims, seed=0))
+    lng = rotated(lng)
+    b = synth.spinor(dims, 1000).numpy()
+    sig = synth.shifts_logspaced(6)
+    tols = synth.shift_tolerances(6)
+    g = hisq.hisq_load_gauge(ctx, dims, torch.as_tensor(fat).cuda(), torch.as_tensor(lng).cuda())
+    try:
+        p = hisq.hisq_default_params()
+        p.mass, p.on_device = m, 1
+        p.sloppy = hisq.prec(*stage)
+        p.refine = hisq.prec(*refine)
+        bd = torch.as_tensor(b).cuda()
+        xs = [torch.zeros_like(bd) for _ in sig]
+        st, info = hisq.hisq_multishift_cg(ctx, g, p, sig, tols, bd, xs)
+    finally:
+        hisq.hisq_free_gauge(ctx, g)
+    assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+    for i, s in enumerate(sig):
+        assert true_res(orc, dims, fat, lng, m, b, xs[i].cpu().numpy(), s) <= tols[i] * 1.0000001
