@@ -65,6 +65,8 @@ def _load():
         "or_int30_pack": (_i64, [_i64, _p, _p]),
         "or_int30_unpack": (None, [_i64, _p, _p]),
         "or_ru_trigger_first": (_i, [_i, _p, _p, _d]),
+        "or_se15_pack": (_i64, [_i64, _i, _p, _p]),
+        "or_se15_unpack": (None, [_i64, _i, _p, _p]),
         "or_int14_pack": (_i64, [_i64, _p, _p]),
         "or_int14_unpack": (None, [_i64, _p, _p]),
         "or_absmax": (_d, [_i64, _p]),
@@ -168,7 +170,7 @@ def mfull(dims, fat, lng, m: float, x):
 # storage formats
 # ---------------------------------------------------------------------------
 SFMT = {"f64": 0, "f32": 1, "half": 2, "int20": 3, "int30": 4, "int14": 5}
-GFMT = {"f64": 0, "f32": 1, "fix16": 2, "fix32": 3}
+GFMT = {"f64": 0, "f32": 1, "fix16": 2, "fix32": 3, "se15": 4}
 
 
 def half_pack(v):
@@ -207,6 +209,21 @@ def ru_trigger_first(r, alpha_ap, eps: float) -> int:
     aa = _np(alpha_ap).reshape(-1)
     assert len(aa) == len(rr) - 1
     return int(_load().or_ru_trigger_first(len(aa), _ptr(rr), _ptr(aa), float(eps)))
+
+
+def se15_pack(links, nr: int = 18):
+    """Links [n][nr] reals (FP64) -> (halves uint16 [n][nr], number of non-finite links)."""
+    a = _np(links).reshape(-1, nr)
+    h = np.zeros((a.shape[0], nr), dtype=np.uint16)
+    bad = _load().or_se15_pack(a.shape[0], int(nr), _ptr(a), _ptr(h))
+    return h, int(bad)
+
+
+def se15_unpack(h, nr: int = 18):
+    hh = np.ascontiguousarray(h, dtype=np.uint16).reshape(-1, nr)
+    out = np.empty((hh.shape[0], nr), dtype=np.float64)
+    _load().or_se15_unpack(hh.shape[0], int(nr), _ptr(hh), _ptr(out))
+    return out
 
 
 def int14_pack(v):

@@ -517,6 +517,64 @@ void or_fix_unpack(int64_t n, const int32_t *q, double gmax, int bits, int compu
     }
 }
 
+/* Shared-exponent link format (a gauge counterpart of the Sec. 4 fermion
+ * formats, for smeared fat links, whose elements have no common scale across
+ * the lattice): per link, its nr stored reals (18, or 12 for rows 0 and 1) as
+ * 15-bit two's-complement integers sharing one 8-bit exponent.  Exponent rule
+ * of the 30-bit format in FP64 with scale 2^14 - 1: mx = max |x| over the
+ * link's nr reals, t = mx / (2^14 - 1), 2^(E-127) the power of two just above
+ * t (E clamped to [1, 254]), q_k = rint(x_k 2^-(E-127)) (|q_k| <= 2^14 - 1).
+ * Layout: one 16-bit half per real, half k = q_k << 1 | bit k of E for k < 8,
+ * q_k << 1 for k >= 8 (the planar chunks of the 16-bit fixed-point format).
+ * Decoding: q_k 2^(E-127), exact in FP32.  A non-finite link is stored as
+ * zero with E = 1 and counted. */
+int64_t or_se15_pack(int64_t nlinks, int nr, const double *g, uint16_t *h)
+{
+    int64_t bad = 0;
+    for (int64_t l = 0; l < nlinks; l++) {
+        const double *x = g + (int64_t)nr * l;
+        double mx = 0.0;
+        int ok = 1;
+        for (int k = 0; k < nr; k++) {
+            if (!isfinite(x[k])) ok = 0;
+            mx = fmax(mx, fabs(x[k]));
+        }
+        int E = 1;
+        int32_t q[18] = {0};
+        if (ok) {
+            const double t = mx / 16383.0;
+            int ex = 0;
+            if (t > 0.0) frexp(t, &ex); /* t = f 2^ex, f in [0.5, 1) */
+            E = t > 0.0 ? ex + 127 : 1;
+            if (E < 1) E = 1;
+            if (E > 254) ok = 0;
+            if (ok)
+                for (int k = 0; k < nr; k++) q[k] = (int32_t)llrint(ldexp(x[k], -(E - 127)));
+        }
+        if (!ok) {
+            bad++;
+            E = 1;
+            for (int k = 0; k < nr; k++) q[k] = 0;
+        }
+        for (int k = 0; k < nr; k++) {
+            const uint32_t e = k < 8 ? ((uint32_t)E >> k) & 1u : 0u;
+            h[(int64_t)nr * l + k] = (uint16_t)((((uint32_t)q[k] & 0x7fffu) << 1) | e);
+        }
+    }
+    return bad;
+}
+
+void or_se15_unpack(int64_t nlinks, int nr, const uint16_t *h, double *g)
+{
+    for (int64_t l = 0; l < nlinks; l++) {
+        const uint16_t *w = h + (int64_t)nr * l;
+        int E = 0;
+        for (int k = 0; k < 8; k++) E |= (w[k] & 1) << k;
+        for (int k = 0; k < nr; k++)
+            g[(int64_t)nr * l + k] = ldexp((double)sext((uint32_t)w[k] >> 1, 15), E - 127);
+    }
+}
+
 /* Row 2 of a compressed link from rows 0 and 1 (Sec. 1, link compression 18 ->
  * 12): for U = sign * W with W in SU(3), row2(U) = sign * conj(row0 x row1). */
 static void rebuild_row2(cplx *U, double sign)
@@ -609,7 +667,8 @@ void or_link_r8_unpack(int64_t n, const double *p, const double *sign, double *l
 }
 
 /* Format emulation (O4): a link field as the computation sees it after storage
- * in format gfmt (0 FP64, 1 FP32, 2 fixed-16, 3 fixed-32) with recon 18, 12, 13
+ * in format gfmt (0 FP64, 1 FP32, 2 fixed-16, 3 fixed-32, 4 shared-exponent
+ * 15-bit, recon 18 or 12) with recon 18, 12, 13
  * or 8 (the compressions rebuild in FP64 from the rounded stored reals); r12
  * and r8 use the link's sign (long links: k = 3, fat links: k = 1).  gmax is
  * the field's scale (max |element| over all 18 reals of every link). */
@@ -643,6 +702,20 @@ void or_gauge_emulate(const int *L, const double *g, int gfmt, int recon, int k,
         memcpy(out, g, sizeof(double) * n);
     } else if (gfmt == 1) {
         for (int64_t i = 0; i < n; i++) out[i] = (double)(float)g[i];
+    } else if (gfmt == 4) {
+        /* the stored reals of each link (18, or 12 for rows 0 and 1) with its own exponent */
+        const int nr = recon == 12 ? 12 : 18;
+        double *st = malloc(sizeof(double) * 4 * V * nr);
+        uint16_t *h = malloc(sizeof(uint16_t) * 4 * V * nr);
+        for (int64_t i = 0; i < 4 * V; i++)
+            for (int k = 0; k < nr; k++) st[i * nr + k] = g[i * 18 + k];
+        or_se15_pack(4 * V, nr, st, h);
+        or_se15_unpack(4 * V, nr, h, st);
+        memset(out, 0, sizeof(double) * n);
+        for (int64_t i = 0; i < 4 * V; i++)
+            for (int k = 0; k < nr; k++) out[i * 18 + k] = st[i * nr + k];
+        free(st);
+        free(h);
     } else {
         const int bits = gfmt == 2 ? 16 : 32;
         int32_t *q = malloc(sizeof(int32_t) * n);

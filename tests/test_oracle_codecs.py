@@ -3,7 +3,8 @@
 * bit patterns derived by hand from the paper's codec rules
   (``tests/golden/*_vectors.txt``: Appendix A, Listing 4 for 20-bit;
   Sec. 2, Listing 1 for 16-bit; our stated reading of Listing 3 for 30-bit;
-  the Appendix A rule with scale 2^13-1 for our 12-byte 14-bit width);
+  the Appendix A rule with scale 2^13-1 for our 12-byte 14-bit width; the
+  30-bit rule with scale 2^14-1 per link for the shared-exponent link format);
 * round-trip error within the format's epsilon (Sec. 2: 2^-15 relative to the
   site maximum for the two's-complement 16-bit format; Sec. 4: about 2^-19
   for 20-bit and 2^-29 for 30-bit);
@@ -52,6 +53,57 @@ def test_int14_golden(orc):
         w, bad = orc.int14_pack(np.array([vals], dtype=np.float32))
         assert bad == 0
         assert [int(x, 16) for x in words] == [int(x) for x in w[0]], vals
+
+
+def test_se15_golden(orc):
+    for vals, halves in _read("se15_vectors.txt"):
+        h, bad = orc.se15_pack(np.array([vals]), len(vals))
+        assert bad == 0
+        assert [int(x, 16) for x in halves] == [int(x) for x in h[0]], vals
+
+
+@pytest.mark.parametrize("nr", [18, 12])
+def test_se15_roundtrip_bound_exact_grid_and_nonfinite(orc, nr):
+    g = np.random.Generator(np.random.Philox(key=11))
+    # links of very different magnitudes (smeared fat links have no common scale)
+    v = g.standard_normal((5000, nr)) * np.exp(g.uniform(-20, 20, size=(5000, 1)))
+    h, bad = orc.se15_pack(v, nr)
+    assert bad == 0
+    u = orc.se15_unpack(h, nr)
+    mx = np.abs(v).max(axis=1, keepdims=True)
+    # step 2^(E-127) <= 2 mx / (2^14 - 1): every real within half a step
+    assert np.all(np.abs(u - v) <= mx / 16383.0 * (1 + 1e-12))
+    # per-link relative precision, whatever the link's magnitude
+    assert np.all(np.abs(u - v) <= mx * 2.0 ** -14)
+    # values on a link's grid come back exactly; zero links stay zero
+    q = g.integers(-16000, 16001, size=(200, nr))
+    q[:, 0] = 16000  # max |q| in [2^13, 2^14 - 1): the scale is exactly 2^-30
+    w = q * 2.0 ** -30
+    np.testing.assert_array_equal(orc.se15_unpack(orc.se15_pack(w, nr)[0], nr), w)
+    z, _ = orc.se15_pack(np.zeros((1, nr)), nr)
+    assert np.all(orc.se15_unpack(z, nr) == 0)
+    bad_links = np.ones((3, nr))
+    bad_links[1, 3] = np.nan
+    bad_links[2, 0] = np.inf
+    hb, nb = orc.se15_pack(bad_links, nr)
+    assert nb == 2 and np.all(orc.se15_unpack(hb, nr)[1:] == 0)
+
+
+def test_se15_gauge_emulate(orc):
+    """The emulated field keeps each link's relative precision (2^-14 of its own largest element),
+    where 16-bit fixed point with one global scale loses the small links."""
+    dims = (4, 4, 4, 4)
+    fat = synth.gauge_field(dims, "fat", seed=3).numpy()
+    g = np.random.Generator(np.random.Philox(key=12))
+    fat = fat * np.exp(g.uniform(-8, 0, size=fat.shape[:-3]))[..., None, None, None]  # magnitudes over 2^11
+    e = orc.gauge_emulate(dims, fat, "se15", 18, long_link=False)
+    f = orc.gauge_emulate(dims, fat, "fix16", 18, long_link=False)
+    links = fat.reshape(-1, 18)
+    mx = np.abs(links).max(axis=1)
+    err_se = np.abs(e.reshape(-1, 18) - links).max(axis=1) / mx
+    err_fx = np.abs(f.reshape(-1, 18) - links).max(axis=1) / mx
+    assert np.all(err_se <= 2.0 ** -14)
+    assert np.median(err_fx) > 10 * np.median(err_se)
 
 
 def test_half_golden(orc):
