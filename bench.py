@@ -384,7 +384,7 @@ def run_ours(args):
     if not args.no_formats:
         # the FP64-class 30-bit triplet computes in FP32 pairs, where rebuilding the third row of a
         # 12-real link costs more than reading 18 reals: it is timed with 18-real long links
-        for name in ("f32", "half", "int30f32", "int30", "int14"):
+        for name in ("f32", "half", "int30f32", "int30", "int14", "int20se"):
             pf = params(name, DELTA, recon=18 if name == "int30" else None)
             xf = torch.zeros_like(b)
             with torch.cuda.stream(stream):

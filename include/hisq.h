@@ -70,7 +70,9 @@ typedef enum {
     HISQ_GAUGE_F64 = 0,
     HISQ_GAUGE_F32 = 1,
     HISQ_GAUGE_FIX16 = 2, /* 16-bit fixed point, scale = global max (Sec. 2 footnote) */
-    HISQ_GAUGE_FIX32 = 3  /* 32-bit fixed point, scale = global max (Sec. 4) */
+    HISQ_GAUGE_FIX32 = 3, /* 32-bit fixed point, scale = global max (Sec. 4) */
+    HISQ_GAUGE_SE15 = 4   /* per link: 15-bit integers sharing one 8-bit exponent (a shared-exponent
+                             gauge format for smeared fat links; 2 bytes a real) */
 } hisq_gauge_fmt;
 
 /* Storage format of the fermion (spinor) field. */
@@ -90,7 +92,8 @@ typedef enum { HISQ_COMPUTE_F32 = 0, HISQ_COMPUTE_F64 = 1 } hisq_compute_fmt;
 /* Precision triplet gauge / fermion / compute plus link compression (Sec. 1:
  * 18 -> 12 reals by SU(3) unitarity).  Supported combinations:
  *   F64/F64/F64, F32/F32/F32, FIX16/HALF16/F32, FIX16/INT20/F32,
- *   FIX32/INT30/F64, FIX32/INT30/F32, FIX16/INT14/F32;
+ *   FIX32/INT30/F64, FIX32/INT30/F32, and, in the single-right-hand-side
+ *   solvers only, FIX16/INT14/F32 and SE15/INT20/F32;
  * fat_recon must be 18 (smeared fat links are not unitary); long_recon 18,
  * 12, 13 or 8:
  *   12: rows 0 and 1; needs long links that are a sign times SU(3) (checked

@@ -621,7 +621,7 @@ hisq_status run_bcg(hisq_ctx *c, hisq_gauge *g, const BCGConfig &cfg, const doub
                     hisq_solve_info *infos, cudaStream_t s)
 {
     if (cfg.nrhs < 1 || cfg.nrhs > kMaxRHS) return fail(c, HISQ_EINVAL, "nrhs must be in 1..%d", kMaxRHS);
-    if (cfg.sloppy.compute != HISQ_COMPUTE_F32 ||
+    if (cfg.sloppy.compute != HISQ_COMPUTE_F32 || cfg.sloppy.gauge == G_SE15 ||
         !(cfg.sloppy.spinor == S_F32 || cfg.sloppy.spinor == S_HALF || cfg.sloppy.spinor == S_INT20))
         return fail(c, HISQ_EINVAL, "batched solves support the FP32, half and 20-bit sloppy triplets");
     if (cfg.sloppy.long_recon != 12 && cfg.sloppy.long_recon != 18)

@@ -12,7 +12,9 @@
 //   INT30  16 + 8 B        words 0..3 | words 4..5 (Sec. 4, Listing 3; our layout)
 // Link formats ([plane][parity][mu][Vh]; reals row-major, first 12 for r12):
 //   F64 16 B = 1 complex, F32 16 B = 2 complex, FIX16 16 B = 8 int16,
-//   FIX32 16 B = 4 int32; leftover reals go to a 4- or 8-byte tail plane.
+//   FIX32 16 B = 4 int32, SE15 16 B = 8 halves (15-bit q << 1 | one bit of
+//   the link's exponent in halves 0..7); leftover reals go to a 4- or 8-byte
+//   tail plane.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -732,7 +734,7 @@ struct Link {
                 U[4 * n16] = __uint_as_float(c[n16].x);
                 U[4 * n16 + 1] = __uint_as_float(c[n16].y);
             }
-        } else if constexpr (GF == G_FIX16) {
+        } else if constexpr (GF == G_FIX16 || GF == G_SE15) {
             uint32_t w[rows / 2];
 #pragma unroll
             for (int k = 0; k < n16; k++) {
@@ -744,14 +746,29 @@ struct Link {
                 w[4 * n16] = c[n16].x;
                 w[4 * n16 + 1] = c[n16].y;
             }
+            if constexpr (GF == G_SE15) {
+                // exponent bit k in the low bit of half k (k < 8); masked, each half is 2 q_k, exact
+                // in FP32, and the value q_k 2^(E-127) = (2 q_k) 2^(E-128) (subnormal scale for E = 1)
+                const uint32_t E = (w[0] & 1u) | ((w[0] >> 15) & 2u) | ((w[1] & 1u) << 2) | ((w[1] >> 13) & 8u) |
+                                   ((w[2] & 1u) << 4) | ((w[2] >> 11) & 32u) | ((w[3] & 1u) << 6) |
+                                   ((w[3] >> 9) & 128u);
+                const float sc = __uint_as_float(E >= 2u ? (E - 1u) << 23 : E == 1u ? 0x00400000u : 0u);
 #pragma unroll
-            for (int k = 0; k < rows / 2; k++) {
-                if constexpr (sizeof(real) == 8) {
-                    U[2 * k] = (double)(int)(short)(w[k] & 0xffffu);
-                    U[2 * k + 1] = (double)((int)w[k] >> 16);
-                } else {
-                    U[2 * k] = i16lo_to_f(w[k]);
-                    U[2 * k + 1] = i16hi_to_f(w[k]);
+                for (int k = 0; k < rows / 2; k++) {
+                    const uint32_t m = w[k] & 0xfffefffeu;
+                    U[2 * k] = fmul(i16lo_to_f(m), sc);
+                    U[2 * k + 1] = fmul(i16hi_to_f(m), sc);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < rows / 2; k++) {
+                    if constexpr (sizeof(real) == 8) {
+                        U[2 * k] = (double)(int)(short)(w[k] & 0xffffu);
+                        U[2 * k + 1] = (double)((int)w[k] >> 16);
+                    } else {
+                        U[2 * k] = i16lo_to_f(w[k]);
+                        U[2 * k + 1] = i16hi_to_f(w[k]);
+                    }
                 }
             }
         } else {  // G_FIX32

@@ -227,6 +227,7 @@ hisq_status check_prec(hisq_ctx *c, const hisq_prec &p)
                     (p.gauge == G_FIX16 && p.spinor == S_HALF && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX16 && p.spinor == S_INT20 && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX16 && p.spinor == S_INT14 && p.compute == HISQ_COMPUTE_F32) ||
+                    (p.gauge == G_SE15 && p.spinor == S_INT20 && p.compute == HISQ_COMPUTE_F32) ||
                     (p.gauge == G_FIX32 && p.spinor == S_INT30);
     if (!ok)
         return fail(c, HISQ_EINVAL, "unsupported precision triplet gauge=%d spinor=%d compute=%d", p.gauge,

@@ -199,6 +199,37 @@ __global__ void quantise_kernel(Geom g, const double *links, double inv, char *o
         if constexpr (tail == 8)
             reinterpret_cast<float2 *>(out + n16 * pstride)[li] =
                 make_float2((float)src[4 * n16], (float)src[4 * n16 + 1]);
+    } else if constexpr (GF == G_SE15) {
+        // per link: 15-bit integers with one exponent, the 30-bit rule in FP64 with scale 2^14 - 1
+        // (t = max |x| / (2^14 - 1), 2^(E-127) the power of two just above t); half k = q_k << 1 | bit k
+        // of E (k < 8); a link whose exponent does not fit is stored as zero with E = 1
+        double mx = 0.0;
+        bool ok = true;
+        for (int k = 0; k < RECON; k++) {
+            ok = ok && isfinite(src[k]);
+            mx = fmax(mx, fabs(src[k]));
+        }
+        const double tq = mx / 16383.0;
+        int ex = 0;
+        if (tq > 0.0) frexp(tq, &ex);
+        int E = tq > 0.0 ? ex + 127 : 1;
+        if (E < 1) E = 1;
+        if (E > 254) ok = false;
+        if (!ok) E = 1;
+        uint32_t h[RECON];
+        for (int k = 0; k < RECON; k++) {
+            const int q = ok ? (int)rint(ldexp(src[k], -(E - 127))) : 0;
+            h[k] = (((uint32_t)q & 0x7fffu) << 1) | (k < 8 ? ((uint32_t)E >> k) & 1u : 0u);
+        }
+        for (int k = 0; k < n16; k++)
+            reinterpret_cast<uint4 *>(out + k * pstride)[li] =
+                make_uint4(h[8 * k] | (h[8 * k + 1] << 16), h[8 * k + 2] | (h[8 * k + 3] << 16),
+                           h[8 * k + 4] | (h[8 * k + 5] << 16), h[8 * k + 6] | (h[8 * k + 7] << 16));
+        if constexpr (tail == 4)
+            reinterpret_cast<uint32_t *>(out + n16 * pstride)[li] = h[8 * n16] | (h[8 * n16 + 1] << 16);
+        else if constexpr (tail == 8)
+            reinterpret_cast<uint2 *>(out + n16 * pstride)[li] =
+                make_uint2(h[8 * n16] | (h[8 * n16 + 1] << 16), h[8 * n16 + 2] | (h[8 * n16 + 3] << 16));
     } else {
         constexpr double qmax = GF == G_FIX16 ? 32767.0 : 2147483647.0;
         int q[RECON];
@@ -490,6 +521,7 @@ void launch_quantise_links(const Geom &g, int gf, int recon, const double *links
         case G_F32: Q(G_F32, 18); break;
         case G_FIX16: Q(G_FIX16, 18); break;
         case G_FIX32: Q(G_FIX32, 18); break;
+        case G_SE15: Q(G_SE15, 18); break;
         }
     } else if (recon == 8) {
         switch (gf) {
@@ -511,6 +543,7 @@ void launch_quantise_links(const Geom &g, int gf, int recon, const double *links
         case G_F32: Q(G_F32, 12); break;
         case G_FIX16: Q(G_FIX16, 12); break;
         case G_FIX32: Q(G_FIX32, 12); break;
+        case G_SE15: Q(G_SE15, 12); break;
         }
     }
 #undef Q

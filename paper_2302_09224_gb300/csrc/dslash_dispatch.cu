@@ -19,6 +19,7 @@ bool launch_dslash_f32(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_half(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int20(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int14(int, bool, int, const DslashArgs &, cudaStream_t);
+bool launch_dslash_int20se(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int30d(int, bool, int, const DslashArgs &, cudaStream_t);
 bool launch_dslash_int30f(int, bool, int, const DslashArgs &, cudaStream_t);
 
@@ -64,6 +65,7 @@ bool launch_with(int gf, int sf, int cf, int lrec, bool red, int cfg, const Dsla
     if (gf == G_FIX16 && sf == S_HALF && !f64) return launch_dslash_half(lrec, red, cfg, a, s);
     if (gf == G_FIX16 && sf == S_INT20 && !f64) return launch_dslash_int20(lrec, red, cfg, a, s);
     if (gf == G_FIX16 && sf == S_INT14 && !f64) return launch_dslash_int14(lrec, red, cfg, a, s);
+    if (gf == G_SE15 && sf == S_INT20 && !f64) return launch_dslash_int20se(lrec, red, cfg, a, s);
     if (gf == G_FIX32 && sf == S_INT30) {
         if (f64) return launch_dslash_int30d(lrec, red, cfg, a, s);
         return launch_dslash_int30f(lrec, red, cfg, a, s);

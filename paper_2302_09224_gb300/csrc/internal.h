@@ -20,7 +20,8 @@ namespace hisq {
 // ---------------------------------------------------------------------------
 // formats
 // ---------------------------------------------------------------------------
-enum GaugeFmt { G_F64 = 0, G_F32 = 1, G_FIX16 = 2, G_FIX32 = 3 };
+// G_SE15: per link, 15-bit integers sharing one 8-bit exponent (2 bytes a real)
+enum GaugeFmt { G_F64 = 0, G_F32 = 1, G_FIX16 = 2, G_FIX32 = 3, G_SE15 = 4 };
 // S_INT14: 12 B/site, six 14-bit integers and an 8-bit exponent (a third
 // shared-exponent width).  S_FF: FP32 pairs (hi, lo) per real, 48 B/site:
 // internal accumulators of the FP64-class kernels only, never a storage
@@ -36,7 +37,7 @@ __host__ __device__ constexpr int spinor_tail(int sf) { return spinor_site_bytes
 
 __host__ __device__ constexpr int gauge_real_bytes(int gf)
 {
-    return gf == G_F64 ? 8 : gf == G_FIX16 ? 2 : 4;
+    return gf == G_F64 ? 8 : (gf == G_FIX16 || gf == G_SE15) ? 2 : 4;
 }
 // Reals of a link kept in its row planes: 18, 12, and 12 for the 13-real
 // format, whose 13th real (the phase of det U) lives in a plane of its own.

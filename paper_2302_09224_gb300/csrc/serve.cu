@@ -84,7 +84,7 @@ Key key_of(const hisq_request &r)
 
 bool batchable(const hisq_request &r)
 {
-    return r.kind == HISQ_REQ_CG && r.sloppy.compute == HISQ_COMPUTE_F32 &&
+    return r.kind == HISQ_REQ_CG && r.sloppy.compute == HISQ_COMPUTE_F32 && r.sloppy.gauge != G_SE15 &&
            (r.sloppy.spinor == S_F32 || r.sloppy.spinor == S_HALF || r.sloppy.spinor == S_INT20) &&
            r.sloppy.fat_recon == 18 && (r.sloppy.long_recon == 12 || r.sloppy.long_recon == 18);
 }

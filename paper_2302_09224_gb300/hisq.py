@@ -22,7 +22,7 @@ HISQ_ECUDA, HISQ_EBUSY, HISQ_ETIMEOUT, HISQ_ENOTFOUND, HISQ_ERANGE = 5, 6, 7, 8,
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EBREAKDOWN", 5: "ECUDA", 6: "EBUSY",
                 7: "ETIMEOUT", 8: "ENOTFOUND", 9: "ERANGE"}
 
-HISQ_GAUGE_F64, HISQ_GAUGE_F32, HISQ_GAUGE_FIX16, HISQ_GAUGE_FIX32 = 0, 1, 2, 3
+HISQ_GAUGE_F64, HISQ_GAUGE_F32, HISQ_GAUGE_FIX16, HISQ_GAUGE_FIX32, HISQ_GAUGE_SE15 = 0, 1, 2, 3, 4
 HISQ_SPINOR_F64, HISQ_SPINOR_F32, HISQ_SPINOR_HALF16, HISQ_SPINOR_INT20, HISQ_SPINOR_INT30, HISQ_SPINOR_INT14 = \
     0, 1, 2, 3, 4, 5
 HISQ_COMPUTE_F32, HISQ_COMPUTE_F64 = 0, 1
@@ -51,6 +51,7 @@ def prec(name: str, long_recon: int = 12) -> hisq_prec:
         "half": (HISQ_GAUGE_FIX16, HISQ_SPINOR_HALF16, HISQ_COMPUTE_F32),
         "int20": (HISQ_GAUGE_FIX16, HISQ_SPINOR_INT20, HISQ_COMPUTE_F32),
         "int14": (HISQ_GAUGE_FIX16, HISQ_SPINOR_INT14, HISQ_COMPUTE_F32),
+        "int20se": (HISQ_GAUGE_SE15, HISQ_SPINOR_INT20, HISQ_COMPUTE_F32),
         "int30": (HISQ_GAUGE_FIX32, HISQ_SPINOR_INT30, HISQ_COMPUTE_F64),
         "int30f32": (HISQ_GAUGE_FIX32, HISQ_SPINOR_INT30, HISQ_COMPUTE_F32),
     }

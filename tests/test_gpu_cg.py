@@ -68,7 +68,7 @@ def test_cg_vs_dense(ctx, orc, dims, name):
     assert abs(info.true_residual - true_res(orc, dims, fat, lng, m, b, x)) < 1e-12
 
 
-@pytest.mark.parametrize("name", ["f64", "f32", "half", "int20", "int30", "int30f32", "int14"])
+@pytest.mark.parametrize("name", ["f64", "f32", "half", "int20", "int30", "int30f32", "int14", "int20se"])
 def test_cg_true_residual_8x4(ctx, orc, name):
     """The config-1 lattice (8^4, m = 0.1, tol 1e-10) in every sloppy format."""
     dims, m = (8, 8, 8, 8), 0.1

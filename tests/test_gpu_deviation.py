@@ -21,7 +21,7 @@ from paper_2302_09224_gb300 import hisq, synth
 pytestmark = pytest.mark.gpu
 
 DIMS = (16, 16, 16, 16)
-NAMES = ("f32", "half", "int20", "int30", "int30f32", "int14")
+NAMES = ("f32", "half", "int20", "int30", "int30f32", "int14", "int20se")
 PCT = (50, 90, 99, 100)
 
 
@@ -76,3 +76,10 @@ def test_fourteen_bit_above_sixteen_bit(deviations):
     # 16-bit links, dominates
     for k in range(len(PCT) - 1):
         assert 1.5 * deviations["half"][k] < deviations["int14"][k] < 8 * deviations["half"][k], PCT[k]
+
+
+def test_shared_exponent_links_by_their_bits(deviations):
+    # links with 15-bit integers and one exponent each: on these fields (every link of about the same
+    # magnitude) a bit coarser than one global 16-bit scale, so the 20-bit triplet's deviation grows
+    for k in range(len(PCT) - 1):
+        assert deviations["int20"][k] < deviations["int20se"][k] < 4 * deviations["int20"][k], PCT[k]

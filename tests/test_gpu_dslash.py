@@ -25,17 +25,17 @@ pytestmark = pytest.mark.gpu
 
 # relative L2 bounds against the exact FP64 stencil
 BOUND_EXACT = {"f64": 1e-12, "f32": 1e-6, "half": 1e-3, "int20": 3e-4, "int30": 1e-8, "int30f32": 2e-6,
-               "int14": 1e-3}
+               "int14": 1e-3, "int20se": 3e-4}
 # relative L2 bounds against the format emulation (compute + output rounding)
 # (the output is stored in the spinor format: for half and int14 its rounding dominates)
 BOUND_EMUL = {"f64": 1e-13, "f32": 1e-6, "half": 5e-5, "int20": 3e-6, "int30": 3e-9, "int30f32": 1e-6,
-              "int14": 2e-4}
+              "int14": 2e-4, "int20se": 3e-6}
 SPINOR = {"f64": "f64", "f32": "f32", "half": "half", "int20": "int20", "int30": "int30", "int30f32": "int30",
-          "int14": "int14"}
+          "int14": "int14", "int20se": "int20"}
 GAUGE = {"f64": "f64", "f32": "f32", "half": "fix16", "int20": "fix16", "int30": "fix32", "int30f32": "fix32",
-         "int14": "fix16"}
+         "int14": "fix16", "int20se": "se15"}
 COMPUTE_F32 = {"f64": False, "f32": True, "half": True, "int20": True, "int30": False, "int30f32": True,
-               "int14": True}
+               "int14": True, "int20se": True}
 
 
 @pytest.fixture(scope="module")
@@ -245,7 +245,7 @@ def test_launch_shape_controls(ctx):
 # for the FP32-compute triplets (and the FP32-pair arithmetic of 30-bit/FP64),
 # FP64 max for plain FP64
 HUGE = {"f64": 1.7e308, "f32": 3.3e38, "half": 3.3e38, "int20": 3.3e38, "int30": 3.3e38, "int30f32": 3.3e38,
-        "int14": 3.3e38}
+        "int14": 3.3e38, "int20se": 3.3e38}
 
 
 @pytest.mark.parametrize("name", list(BOUND_EXACT))
