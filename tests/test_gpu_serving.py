@@ -187,3 +187,32 @@ def test_admission_by_budget():
             hisq.hisq_destroy(small)
     finally:
         hisq.hisq_destroy(big)
+
+
+def test_multishift_refinement_paths(env, orc):
+    """A multi-shift request's refinements in a triplet with batch sessions (20-bit) and in one without
+    (30-bit, FP64-class: the single-system CG from the stage's solution), both from host and device
+    buffers: every shift meets its target by the oracle's FP64 residual, refinements ran where the
+    stage left a shift above its target, and the report is in the caller's shift order."""
+    ctx, gauges, fields = env
+    d = VOLS[0]
+    fat, lng = fields[d]
+    sig = [0.3, 1e-3, 0.05, 0.01]  # unsorted on purpose
+    tols = [1e-10, 1e-10, 1e-9, 1e-10]
+    for refine, on_device in (("int20", True), ("int30", False)):
+        b = synth.spinor(d, synth.rhs_seed(77))
+        bb = b.numpy()
+        bx = b.cuda() if on_device else bb
+        x = torch.zeros((4,) + tuple(b.shape), dtype=torch.float64, device="cuda") if on_device else \
+            np.zeros((4,) + bb.shape)
+        t = hisq.hisq_submit(ctx, gauges[d], hisq.HISQ_REQ_MULTISHIFT, 0.02, bx, x, on_device, sigma=sig,
+                             shift_tol=tols, sloppy=hisq.prec("half"), refine=hisq.prec(refine, 18 if refine == "int30" else 12))
+        st, info = hisq.hisq_wait(ctx, t, 120.0)
+        assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+        xx = as_np(x)
+        for i, s in enumerate(sig):
+            r = bb - orc.mee(d, fat, lng, 0.02, xx[i], sigma=s)
+            assert np.linalg.norm(r) / np.linalg.norm(bb) <= tols[i], (refine, i)
+            assert info.shift_resid[i] <= tols[i]
+        assert sum(info.refine_iters[i] for i in range(4)) > 0
+        assert info.shift_resid_ms[1] >= info.shift_resid[1]  # the lightest shift was refined
