@@ -20,6 +20,7 @@
 #include "cg.h"
 #include "codecs.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "reduce.cuh"
 
 namespace hisq {
@@ -144,6 +145,8 @@ __device__ __forceinline__ char *half(char *f, size_t hb) { return f + blockIdx.
 // rho_0 <- -omega rho_0 (start of a cycle)
 __global__ void cycle_start_kernel(BState *b, const int *active)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(active)) return;
     const double r = -(b->omega_re * b->rho_re - b->omega_im * b->rho_im);
     const double i = -(b->omega_re * b->rho_im + b->omega_im * b->rho_re);
@@ -155,6 +158,8 @@ __global__ void cycle_start_kernel(BState *b, const int *active)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, const char *y)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     real v[3] = {0, 0, 0};
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
@@ -181,6 +186,8 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, con
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) u_multi_kernel(BArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     const real br = (real)a.b->beta_re, bi = (real)a.b->beta_im;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x)
@@ -203,6 +210,8 @@ __global__ void __launch_bounds__(kBlock) u_multi_kernel(BArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     const real ar = (real)a.b->alpha_re, ai = (real)a.b->alpha_im;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
@@ -239,6 +248,8 @@ __global__ void __launch_bounds__(kBlock) r_multi_kernel(BArgs a)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     real v[3] = {0, 0, 0};
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
@@ -284,6 +295,8 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
 // gamma''_j = gamma_{j+1} + sum_{i=j+1}^{l-1} tau_ji gamma_{i+1}
 __global__ void gamma_kernel(BState *b, const int *active)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(active)) return;
     const int l = b->l;
     b->g_re[l] = b->gp_re[l];
@@ -315,6 +328,8 @@ __global__ void gamma_kernel(BState *b, const int *active)
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     if (skip(a.active)) return;
     const BState *b = a.b;
     const int l = b->l;
@@ -362,6 +377,8 @@ __global__ void __launch_bounds__(kBlock) final_kernel(BArgs a)
 // after a reliable update: rr = |r_hi|^2 (sums[0]) and iterate again
 __global__ void restart_kernel(BState *b, const double *sum)
 {
+    pdl_wait();
+    pdl_launch_dependents();
     b->rr = sum[0];
     b->rr_max = sum[0];
     b->reason = REASON_NONE;
@@ -388,15 +405,15 @@ dim3 grid2(int vh)
     do {                                                                                    \
         const bool f64_ = (CF_) == HISQ_COMPUTE_F64;                                        \
         switch (SF_) {                                                                      \
-        case S_F64: KERNEL<S_F64, double><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;     \
-        case S_F32: KERNEL<S_F32, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;      \
-        case S_HALF: KERNEL<S_HALF, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;    \
-        case S_INT20: KERNEL<S_INT20, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;  \
-        case S_INT14: KERNEL<S_INT14, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); break;  \
-        case S_INT30:                                                                       \
-            if (f64_) KERNEL<S_INT30, double><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);        \
-            else KERNEL<S_INT30, float><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);              \
-            break;                                                                          \
+        case S_F64: launch_chained(KERNEL<S_F64, double>, GRID, dim3(kBlock), st, __VA_ARGS__); break;     \
+        case S_F32: launch_chained(KERNEL<S_F32, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;      \
+        case S_HALF: launch_chained(KERNEL<S_HALF, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;    \
+        case S_INT20: launch_chained(KERNEL<S_INT20, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;  \
+        case S_INT14: launch_chained(KERNEL<S_INT14, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;  \
+        case S_INT30:                                                                                      \
+            if (f64_) launch_chained(KERNEL<S_INT30, double>, GRID, dim3(kBlock), st, __VA_ARGS__);        \
+            else launch_chained(KERNEL<S_INT30, float>, GRID, dim3(kBlock), st, __VA_ARGS__);              \
+            break;                                                                                         \
         }                                                                                   \
     } while (0)
 
@@ -481,7 +498,7 @@ struct BRun {
         const int *act = &b->active;
         {
             LaunchScope ls(c, st, PROF_BLAS, 0.0);
-            cycle_start_kernel<<<1, 1, 0, st>>>(b, act);
+            launch_chained(cycle_start_kernel, dim3(1), dim3(1), st, b, act);
         }
         for (int j = 0; j < l; j++) {
             dot(rt, R + j * fb, OP_RHO, j, 0);
@@ -510,7 +527,7 @@ struct BRun {
             }
         {
             LaunchScope ls(c, st, PROF_BLAS, 0.0);
-            gamma_kernel<<<1, 1, 0, st>>>(b, act);
+            launch_chained(gamma_kernel, dim3(1), dim3(1), st, b, act);
         }
         BArgs a = args();
         a.op = OP_FINAL;
@@ -667,7 +684,7 @@ struct BRun {
                     LaunchScope ls(c, st, PROF_BLAS, 0.0);
                     // total of both halves was assembled on the host; hand it to the device
                     cudaMemcpyAsync(cur_red(c).result, &rr, sizeof rr, cudaMemcpyHostToDevice, st);
-                    restart_kernel<<<1, 1, 0, st>>>(b, cur_red(c).result);
+                    launch_chained(restart_kernel, dim3(1), dim3(1), st, b, (const double *)cur_red(c).result);
                 }
                 e = pull();
                 if (e) break;

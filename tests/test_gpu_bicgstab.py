@@ -128,3 +128,21 @@ def test_bicgstab_other_formats(ctx, orc, name, recon):
         hisq.hisq_free_gauge(ctx, g)
     assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
     assert true_res(orc, dims, fat, lng, m, b, x.cpu().numpy()) <= 1e-10
+
+
+def test_programmatic_launch_same_bits(ctx):
+    """BiCGStab's kernel chain launched with programmatic dependent launch (every kernel waits for its
+    predecessor's results before touching them) gives the same solution, bit for bit, as kernels
+    launched one after another, in graphs and directly."""
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = (t.numpy() for t in synth.gauge_pair(dims, seed=2))
+    b = synth.spinor(dims, 1002, full=True).numpy()
+    prev = hisq.hisq_programmatic_launch(0)
+    try:
+        ref = [run(ctx, dims, fat, lng, m, b, name, l=2, use_graph=g)[2] for name in ("int20", "int30") for g in (0, 1)]
+        hisq.hisq_programmatic_launch(1)
+        got = [run(ctx, dims, fat, lng, m, b, name, l=2, use_graph=g)[2] for name in ("int20", "int30") for g in (0, 1)]
+    finally:
+        hisq.hisq_programmatic_launch(prev)
+    for a, r in zip(got, ref):
+        np.testing.assert_array_equal(a, r)
