@@ -186,7 +186,9 @@ def config_dict(args, world=1):
             "parallelism": "replicas" if world > 1 else "single GPU",
             "m_ee": "one fused pass" if getattr(args, "fused", False) else "two stencil passes",
             "kernel_chain": "sequential launches" if getattr(args, "no_pdl", False)
-            else "programmatic dependent launch"}
+            else "programmatic dependent launch",
+            "cg_scalars": "one-block sums" if getattr(args, "no_split", False)
+            else "summed by every block of the kernel that uses them"}
 
 
 def oracle_sample(fat_h, lng_h, b_h, iters):
@@ -250,6 +252,8 @@ def run_ours(args):
         hisq.hisq_mee_fused(1)
     if args.no_pdl:
         hisq.hisq_programmatic_launch(0)
+    if args.no_split:
+        hisq.hisq_cg_split_scalars(0)
     ctx = hisq.hisq_create(local)
     fat, lng = synth.gauge_pair(DIMS, seed=0, device=dev)
     g = hisq.hisq_load_gauge(ctx, DIMS, fat, lng)
@@ -579,6 +583,8 @@ def run_solve_only(args):
 
     dims = tuple(int(v) for v in args.solve.split(","))
     force_shapes(args)
+    if args.no_split:
+        hisq.hisq_cg_split_scalars(0)
     if args.fused:
         hisq.hisq_mee_fused(1)
     ctx = hisq.hisq_create(0)
@@ -879,6 +885,8 @@ def main():
     ap.add_argument("--fused", action="store_true", help="M_ee as one fused pass (hisq_mee_fused)")
     ap.add_argument("--no-pdl", action="store_true", help="launch the solver kernels without programmatic "
                     "dependent launch (hisq_programmatic_launch(0))")
+    ap.add_argument("--no-split", action="store_true", help="sum the CG iteration's alpha and beta once, in a "
+                    "one-block launch and a last block (hisq_cg_split_scalars(0))")
     ap.add_argument("--solve-iters", type=int, default=2866,
                     help="reference arm: iterations of one GPU solve (extrapolation unit)")
     ap.add_argument("--solve-bytes", type=float, default=3.605e12,

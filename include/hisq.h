@@ -316,6 +316,18 @@ HISQ_API int hisq_stencil_config_reduce(int cfg);
  * Returns the previous setting, or -2 for an invalid value.  For benchmarking;
  * no counterpart in the paper. */
 HISQ_API int hisq_programmatic_launch(int mode);
+/* The scalar steps of the CG iteration (Sec. 3.1: alpha = |r|^2 / p.Ap and
+ * beta): 1 (default) every block of the residual update sums the reducing
+ * stencil pass's per-block partials itself, in one fixed order, and takes
+ * alpha from them, and every block of the gradient update does the same for
+ * beta, so no one-block launch or last-block tail sits between the kernels;
+ * 0 sums them once, in a one-block launch after the stencil pass and in the
+ * last block of the residual update.  The sums are deterministic in both
+ * modes; their rounding differs between the two (other block shapes).  The
+ * FP64 triplet (FP64 sloppy storage) always takes the second form (faster
+ * there).  Returns the previous setting, or -2 for an invalid value.  Read
+ * when a solve starts.  For benchmarking; no counterpart in the paper. */
+HISQ_API int hisq_cg_split_scalars(int mode);
 /* The shape in use for triplet p on gauge g's lattice (plain pass, or the
  * reducing pass if reduce != 0): the forced one, else the tuned one, else -1
  * when that pair has not been tuned yet. */

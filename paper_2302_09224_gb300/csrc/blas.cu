@@ -70,6 +70,68 @@ __device__ __forceinline__ double f2d_bits(float f)
 constexpr int kRSites = 2;
 constexpr int kPSites = 2;
 
+// Loads of r (v0) and Ap (v1) at the U sites i0 + u * blockDim.x.
+template <int SF, int U, int C>
+__device__ __forceinline__ void r_load(const BlasArgs &a, int i0, uint4 (&cr)[U][C], uint4 (&ca)[U][C])
+{
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i < a.n) {
+            Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
+            Spinor<SF>::gather(a.v1, a.n, i, ca[u]);
+        }
+    }
+}
+
+// r <- r - alpha Ap at those sites, stored; |r_new|^2 and Re<r_new, r_old> added to v.
+template <int SF, typename real, int U, int C>
+__device__ __forceinline__ void r_group(const BlasArgs &a, int i0, const uint4 (&cr)[U][C], const uint4 (&ca)[U][C],
+                                        real alpha, red_t<real> v[2])
+{
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= a.n) continue;
+        if constexpr (SF == S_INT30 && is_ff<real>::value) {
+            // FP64-class: the update in FP32 pairs; |r|^2 and Re<r_new, r_old> exactly in integers
+            // from the stored 30-bit records (products of 30-bit integers, sums below 2^62)
+            int32_t qr[6];
+            const uint32_t Er = Spinor<S_INT30>::raw(cr[u], qr);
+            ff r[6], ap[6], rn[6];
+            Spinor<S_INT30>::decode(cr[u], r);
+            Spinor<S_INT30>::decode(ca[u], ap);
+#pragma unroll
+            for (int k = 0; k < 6; k++) rn[k] = r[k] - alpha * ap[k];
+            uint32_t qn[6], En;
+            if (!Spinor<S_INT30>::store_ff_q(a.v0, a.n, i, rn, qn, En)) atomicExch(a.err, 1);
+            long long n2 = 0, d = 0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(n2) : "r"((int)qn[k]));
+                asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(d) : "r"((int)qn[k]), "r"(qr[k]));
+            }
+            // a record's value is q 2^(E-127)
+            v[0] += ff_ldexp(ff_from_ll(n2), 2 * (int)En - 254);
+            v[1] += ff_ldexp(ff_from_ll(d), (int)En + (int)Er - 254);
+        } else {
+            real r[6], ap[6], rn[6];
+            Spinor<SF>::decode(cr[u], r);
+            Spinor<SF>::decode(ca[u], ap);
+            real n2 = real(0), d = real(0);  // in the compute precision; the block sums the threads
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                rn[k] = r[k] - alpha * ap[k];
+                n2 += rn[k] * rn[k];
+                d += rn[k] * r[k];
+            }
+            v[0] += (red_t<real>)n2;
+            v[1] += (red_t<real>)d;
+            if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
+        }
+    }
+}
+
 template <int SF, typename real>
 __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
 {
@@ -82,56 +144,8 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
     // one wave of blocks loops over groups of U sites per thread (see wave_blocks)
     for (int i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < a.n; i0 += gridDim.x * blockDim.x * U) {
         uint4 cr[U][C], ca[U][C];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int i = i0 + u * blockDim.x;
-            if (i < a.n) {
-                Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
-                Spinor<SF>::gather(a.v1, a.n, i, ca[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int i = i0 + u * blockDim.x;
-            if (i >= a.n) continue;
-            if constexpr (SF == S_INT30 && is_ff<real>::value) {
-                // FP64-class: the update in FP32 pairs; |r|^2 and Re<r_new, r_old> exactly in integers
-                // from the stored 30-bit records (products of 30-bit integers, sums below 2^62)
-                int32_t qr[6];
-                const uint32_t Er = Spinor<S_INT30>::raw(cr[u], qr);
-                ff r[6], ap[6], rn[6];
-                Spinor<S_INT30>::decode(cr[u], r);
-                Spinor<S_INT30>::decode(ca[u], ap);
-#pragma unroll
-                for (int k = 0; k < 6; k++) rn[k] = r[k] - alpha * ap[k];
-                uint32_t qn[6], En;
-                if (!Spinor<S_INT30>::store_ff_q(a.v0, a.n, i, rn, qn, En)) atomicExch(a.err, 1);
-                long long n2 = 0, d = 0;
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(n2) : "r"((int)qn[k]));
-                    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(d) : "r"((int)qn[k]), "r"(qr[k]));
-                }
-                // a record's value is q 2^(E-127)
-                v[0] += ff_ldexp(ff_from_ll(n2), 2 * (int)En - 254);
-                v[1] += ff_ldexp(ff_from_ll(d), (int)En + (int)Er - 254);
-                continue;
-            } else {
-            real r[6], ap[6], rn[6];
-            Spinor<SF>::decode(cr[u], r);
-            Spinor<SF>::decode(ca[u], ap);
-            real n2 = real(0), d = real(0);  // in the compute precision; reduce_grid sums the threads
-#pragma unroll
-            for (int k = 0; k < 6; k++) {
-                rn[k] = r[k] - alpha * ap[k];
-                n2 += rn[k] * rn[k];
-                d += rn[k] * r[k];
-            }
-            v[0] += (red_t<real>)n2;
-            v[1] += (red_t<real>)d;
-            if (!Spinor<SF>::store(a.v0, a.n, i, rn)) atomicExch(a.err, 1);
-            }
-        }
+        r_load<SF>(a, i0, cr, ca);
+        r_group<SF, real>(a, i0, cr, ca, alpha, v);
     }
     __shared__ double tot[2];
     if (reduce_grid<2>(v, a.red, tot) && threadIdx.x == 0) {
@@ -139,6 +153,37 @@ __global__ void __launch_bounds__(kBlock) r_update_kernel(BlasArgs a)
             run_finisher(a.fin, tot, a.fst, a.slot);
         else if (a.st)
             run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
+    }
+}
+
+template <int SF, int U, int C>
+__device__ __forceinline__ void p_load(const BlasArgs &a, int i0, uint4 (&cr)[U][C], uint4 (&cp)[U][C])
+{
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i < a.n) {
+            Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
+            Spinor<SF>::gather(a.v1, a.n, i, cp[u]);
+        }
+    }
+}
+
+// p' = r + beta p at those sites, stored into v2.
+template <int SF, typename real, int U, int C>
+__device__ __forceinline__ void p_group(const BlasArgs &a, int i0, const uint4 (&cr)[U][C], const uint4 (&cp)[U][C],
+                                        real beta)
+{
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= a.n) continue;
+        real r[6], p[6];
+        Spinor<SF>::decode(cr[u], r);
+        Spinor<SF>::decode(cp[u], p);
+#pragma unroll
+        for (int k = 0; k < 6; k++) p[k] = r[k] + beta * p[k];
+        if (!Spinor<SF>::store(a.v2, a.n, i, p)) atomicExch(a.err, 1);
     }
 }
 
@@ -153,26 +198,96 @@ __global__ void __launch_bounds__(kBlock) p_update_kernel(BlasArgs a)
     if (a.clear_ring && i0 == 0)
         for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
     uint4 cr[U][C], cp[U][C];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        const int i = i0 + u * blockDim.x;
-        if (i < a.n) {
-            Spinor<SF>::gather(a.v0, a.n, i, cr[u]);
-            Spinor<SF>::gather(a.v1, a.n, i, cp[u]);
-        }
-    }
+    p_load<SF>(a, i0, cr, cp);
     const real beta = block_scalar<real>(&a.st->beta);
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        const int i = i0 + u * blockDim.x;
-        if (i >= a.n) continue;
-        real r[6], p[6];
-        Spinor<SF>::decode(cr[u], r);
-        Spinor<SF>::decode(cp[u], p);
-#pragma unroll
-        for (int k = 0; k < 6; k++) p[k] = r[k] + beta * p[k];
-        if (!Spinor<SF>::store(a.v2, a.n, i, p)) atomicExch(a.err, 1);
+    p_group<SF, real>(a, i0, cr, cp, beta);
+}
+
+// The CG iteration's scalar steps without one-block launches or last-block
+// tails (BlasArgs::split).  Every block of r_update sums the reducing stencil
+// pass's block partials itself, in the one fixed order of sum_partials, and
+// takes alpha = |r|^2 / Re<p, Ap> from them; block 0 also runs the alpha
+// finisher (alpha ring, breakdown) and copies |r|^2 to rr_den.  r_update
+// leaves its own block partials in the second half of the partials buffer;
+// warp 0 of every block of p_update sums those and takes beta with rr_den as
+// denominator, and block 0 runs the beta finisher (reliable-update and
+// convergence decisions, the new |r|^2): no other block reads what it writes.
+// A block that starts after block 0 has stopped the iteration skips its
+// update, which is then partial; the solver never reads that ring slot before
+// rewriting it (the slot's alpha is zero until then).  Each block's first
+// loads are issued before its partial sums, so the sums overlap them.
+inline __device__ RedBuf split_half(RedBuf rb)
+{
+    rb.partials += kSplitHalf;
+    return rb;
+}
+
+template <int SF, typename real, int BS>
+__global__ void __launch_bounds__(BS) r_update_split_kernel(BlasArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    if (skip(a.active)) return;
+    constexpr int U = kRSites, C = Spinor<SF>::chunks;
+    const int step = gridDim.x * BS * U;
+    int i0 = blockIdx.x * BS * U + threadIdx.x;
+    uint4 cr[U][C], ca[U][C];
+    r_load<SF>(a, i0, cr, ca);
+    __shared__ double tot[2];
+    __shared__ real al_sh;
+    __shared__ int ok_sh;
+    sum_partials<2, part_t<real>>(a.red, a.nparts, tot);
+    if (threadIdx.x == 0) {
+        const double al = a.st->rr / tot[0];
+        const bool ok = tot[0] > 0.0 && isfinite(al);  // else the finisher stops the iteration
+        al_sh = ok ? real(al) : real(0);
+        ok_sh = ok;
     }
+    __syncthreads();
+    const bool ok = ok_sh;
+    if (ok) {
+        const real alpha = al_sh;
+        red_t<real> v[2] = {0, 0};
+        for (; i0 < a.n; i0 += step) {
+            r_group<SF, real>(a, i0, cr, ca, alpha, v);
+            r_load<SF>(a, i0 + step, cr, ca);
+        }
+        store_block_partial<2>(v, split_half(a.red));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->rr_den = a.st->rr;
+        run_finisher(FIN_CG_ALPHA, tot, a.st, a.slot);
+    }
+}
+
+template <int SF, typename real>
+__global__ void __launch_bounds__(kBlock) p_update_split_kernel(BlasArgs a)
+{
+    pdl_wait();
+    pdl_launch_dependents();
+    if (skip(a.active)) return;
+    constexpr int U = kPSites, C = Spinor<SF>::chunks;
+    if (a.clear_ring && blockIdx.x == 0 && threadIdx.x == 0)
+        for (int j = 0; j < kMaxBuf; j++) a.st->alpha_ring[j] = 0.0;
+    const int i0 = blockIdx.x * kBlock * U + threadIdx.x;  // one group of U sites a thread (the grid covers all)
+    uint4 cr[U][C], cp[U][C];
+    p_load<SF>(a, i0, cr, cp);
+    __shared__ double tot[2];
+    __shared__ real be_sh;
+    __shared__ int ok_sh;
+    warp0_sum_partials<2, part_t<real>>(split_half(a.red), a.nparts, tot);
+    if (threadIdx.x == 0) {
+        // the beta finisher's arithmetic (Polak-Ribiere or Fletcher-Reeves)
+        const double rr_new = tot[0];
+        const double be = (a.st->pr ? rr_new - tot[1] : rr_new) / a.st->rr_den;
+        const bool ok = isfinite(rr_new) && isfinite(be);  // else the finisher stops the iteration
+        be_sh = ok ? real(be) : real(0);
+        ok_sh = ok;
+    }
+    __syncthreads();
+    if (ok_sh) p_group<SF, real>(a, i0, cr, cp, be_sh);
+    // after the update: the finisher's registers are not live beside the loaded fields
+    if (blockIdx.x == 0 && threadIdx.x == 0) run_finisher(FIN_CG_BETA, tot, a.st, a.slot);
 }
 
 // x_hi += sum_{j < nslots} alpha_j p_j; slots are consecutive fields of
@@ -324,41 +439,76 @@ int nblk(int n) { return (n + kBlock - 1) / kBlock; }
 
 namespace {
 
-template <int SF, typename real>
-void r_update_t(const BlasArgs &a, cudaStream_t s)
+// Block size of the split r_update: 1024 threads (each block sums the
+// stencil pass's partials in one round of loads) where the kernel fits 64
+// registers, 512 for the FP64 and FP32-pair kernels.  One wave of blocks, so
+// p_update sums few partials.
+template <typename real>
+constexpr int split_block()
 {
+    return std::is_same<real, float>::value ? 1024 : 512;
+}
+
+template <int SF, typename real>
+unsigned r_update_t(const BlasArgs &a, cudaStream_t s)
+{
+    if (a.split) {
+        constexpr int BS = split_block<real>();
+        static const int wave = wave_blocks(r_update_split_kernel<SF, real, BS>, BS);
+        const int need = (a.n + BS * kRSites - 1) / (BS * kRSites);
+        const int nb = need < wave ? need : wave;
+        launch_chained(r_update_split_kernel<SF, real, BS>, dim3(nb), dim3(BS), s, a);
+        return (unsigned)nb;
+    }
     static const int wave = wave_blocks(r_update_kernel<SF, real>, kBlock);
     const int need = (a.n + kBlock * kRSites - 1) / (kBlock * kRSites);
     launch_chained(r_update_kernel<SF, real>, dim3(need < wave ? need : wave), dim3(kBlock), s, a);
+    return 0;
+}
+
+template <int SF, typename real>
+void p_update_t(const BlasArgs &a, cudaStream_t s)
+{
+    const int nb = (a.n + kBlock * kPSites - 1) / (kBlock * kPSites);
+    if (a.split) {
+        launch_chained(p_update_split_kernel<SF, real>, dim3(nb), dim3(kBlock), s, a);
+        return;
+    }
+    launch_chained(p_update_kernel<SF, real>, dim3(nb), dim3(kBlock), s, a);
 }
 
 }  // namespace
 
-void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
+unsigned launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
     switch (sf) {
-    case S_F64: r_update_t<S_F64, double>(a, s); break;
-    case S_F32: r_update_t<S_F32, float>(a, s); break;
-    case S_HALF: r_update_t<S_HALF, float>(a, s); break;
-    case S_INT20: r_update_t<S_INT20, float>(a, s); break;
-    case S_INT14: r_update_t<S_INT14, float>(a, s); break;
+    case S_F64: return r_update_t<S_F64, double>(a, s);
+    case S_F32: return r_update_t<S_F32, float>(a, s);
+    case S_HALF: return r_update_t<S_HALF, float>(a, s);
+    case S_INT20: return r_update_t<S_INT20, float>(a, s);
+    case S_INT14: return r_update_t<S_INT14, float>(a, s);
     case S_INT30:  // FP64-class compute in FP32 pairs (see ff.cuh)
-        if (cf == HISQ_COMPUTE_F64)
-            r_update_t<S_INT30, ff>(a, s);
-        else
-            r_update_t<S_INT30, float>(a, s);
-        break;
+        if (cf == HISQ_COMPUTE_F64) return r_update_t<S_INT30, ff>(a, s);
+        return r_update_t<S_INT30, float>(a, s);
     }
+    return 0;
 }
 
 void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s)
 {
-    const int nb = (a.n + kBlock * kPSites - 1) / (kBlock * kPSites);
-    if (sf == S_INT30 && cf == HISQ_COMPUTE_F64) {  // FP64-class compute in FP32 pairs
-        launch_chained(p_update_kernel<S_INT30, ff>, dim3(nb), dim3(kBlock), s, a);
-        return;
+    switch (sf) {
+    case S_F64: p_update_t<S_F64, double>(a, s); break;
+    case S_F32: p_update_t<S_F32, float>(a, s); break;
+    case S_HALF: p_update_t<S_HALF, float>(a, s); break;
+    case S_INT20: p_update_t<S_INT20, float>(a, s); break;
+    case S_INT14: p_update_t<S_INT14, float>(a, s); break;
+    case S_INT30:  // FP64-class compute in FP32 pairs (see ff.cuh)
+        if (cf == HISQ_COMPUTE_F64)
+            p_update_t<S_INT30, ff>(a, s);
+        else
+            p_update_t<S_INT30, float>(a, s);
+        break;
     }
-    HISQ_SF_DISPATCH(sf, cf, p_update_kernel, dim3(nb), dim3(kBlock), s);
 }
 
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s)

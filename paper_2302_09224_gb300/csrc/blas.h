@@ -27,9 +27,13 @@ struct BlasArgs {
     int fin;                 // finisher override (0: the kernel's CG default)
     void *fst;               // state for the override finisher
     const double *alpha_src; // r_update: step size (null: st->alpha)
+    int split;               // CG chain without one-block launches: r_update takes alpha from the
+                             // reducing stencil pass's block partials, p_update beta from r_update's
+    unsigned nparts;         // split: block partials left by the previous kernel
 };
 
-void launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s);
+// Returns the number of block partials a split r_update leaves (0 otherwise).
+unsigned launch_r_update(int sf, int cf, const BlasArgs &a, cudaStream_t s);
 void launch_p_update(int sf, int cf, const BlasArgs &a, cudaStream_t s);
 void launch_x_flush(int sf, int cf, const BlasArgs &a, cudaStream_t s);
 void launch_true_residual(int sf, int cf, const BlasArgs &a, cudaStream_t s);

@@ -60,9 +60,9 @@ hisq_prec prec_f64()
 }
 
 // out_even = diag * in_even - D_eo D_oe in_even, with tmp an odd-parity field.
-void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
-               const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
-               cudaStream_t s)
+unsigned apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
+                   const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
+                   cudaStream_t s, bool leave_partials)
 {
     DslashArgs d{};
     d.g = geom;
@@ -90,7 +90,7 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
         const double links = 8.0 * link_bytes(p.gauge, 18) + 8.0 * link_bytes(p.gauge, p.long_recon);
         LaunchScope ls(c, s, kind, (links + 3.0 * spinor_site_bytes(p.spinor)) * geom.vh);
         MeeArgs m{d, d2};
-        if (launch_mee_fused(p.gauge, p.spinor, p.compute, p.long_recon, m, s)) return;
+        if (launch_mee_fused(p.gauge, p.spinor, p.compute, p.long_recon, m, s)) return 0;
     }
     {
         // both passes under one event pair, counted as two launches (their average duration is half
@@ -101,10 +101,15 @@ void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeVie
         d2.defer_finish = 1;
         launch_dslash(p.gauge, p.spinor, p.compute, p.long_recon, fin != FIN_NONE, d2, s);
     }
-    if (fin != FIN_NONE) {
-        LaunchScope ls(c, s, PROF_BLAS, 0.0);
-        launch_dslash_finish(p.gauge, p.spinor, p.compute, p.long_recon, d2, s);
+    if (fin == FIN_NONE) return 0;
+    if (leave_partials) {
+        // the partials of all blocks must fit the first half of the buffer
+        const unsigned np = dslash_partials(p.gauge, p.spinor, p.compute, p.long_recon, geom);
+        if ((size_t)np * 2 * sizeof(double) <= kSplitHalf * sizeof(double)) return np;
     }
+    LaunchScope ls(c, s, PROF_BLAS, 0.0);
+    launch_dslash_finish(p.gauge, p.spinor, p.compute, p.long_recon, d2, s);
+    return 0;
 }
 
 void tune_stencil(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, char *zero_in, char *out,
@@ -141,6 +146,9 @@ struct CGRun {
     GaugeView gv_s{}, gv_d{};
     double diag = 0;
     int ru = 0, mv_hi = 0;
+    // one mode for the whole solve (its graph is captured once); the FP64 triplet keeps the one-block
+    // sums: its split r_update (82 registers, one 512-thread block a SM) measured 0.2 % slower
+    const bool split = split_mode.load() != 0 && cfg.sloppy.spinor != S_F64;
 
     CGRun(hisq_ctx *c_, hisq_gauge *g_, const CGConfig &cfg_, cudaStream_t s_)
         : c(c_), g(g_), cfg(cfg_), s(s_), ws(c_, s_), vh(g_->geom.vh)
@@ -244,17 +252,21 @@ struct CGRun {
         const int *act = &st->active;
         for (int i = 0; i < N; i++) {
             set_prof_tag(i);
-            apply_mee(c, g->geom, cfg.sloppy, gv_s, diag, slot(i), tmp_s, ap_s, FIN_CG_ALPHA, st, i, act,
-                      PROF_STENCIL, s);
+            const unsigned np = apply_mee(c, g->geom, cfg.sloppy, gv_s, diag, slot(i), tmp_s, ap_s, FIN_CG_ALPHA, st,
+                                          i, act, PROF_STENCIL, s, split);
             BlasArgs a = blas();
             a.active = act;
             a.slot = i;
             a.v0 = r_s;
             a.v1 = ap_s;
+            a.split = np > 0;
+            a.nparts = np;
+            unsigned rp;
             {
                 LaunchScope ls(c, s, PROF_BLAS, 3.0 * spinor_site_bytes(cfg.sloppy.spinor) * vh);
-                launch_r_update(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
+                rp = launch_r_update(cfg.sloppy.spinor, cfg.sloppy.compute, a, s);
             }
+            a.nparts = rp;
             if (i == N - 1) flush(N, act, x64);
             a.v0 = r_s;
             a.v1 = slot(i);

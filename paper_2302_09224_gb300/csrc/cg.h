@@ -56,9 +56,12 @@ void tune_stencil(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const Gauge
                   cudaStream_t s);
 double stencil_bytes(const hisq_prec &p, int vh, bool xpay);
 
-void apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
-               const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
-               cudaStream_t s);
+// Returns the number of block partials left for the next kernel when
+// leave_partials is set and the reducing pass's finisher was not run (the
+// caller's next kernel sums them: the split CG chain), else 0.
+unsigned apply_mee(hisq_ctx *c, const Geom &geom, const hisq_prec &p, const GaugeView &gv, double diag,
+                   const char *in, char *tmp, char *out, int fin, void *st, int slot, const int *active, int kind,
+                   cudaStream_t s, bool leave_partials = false);
 
 // Mixed-precision CG on (M_ee + sigma) x = b; b64 / x64 are FP64 planar device
 // fields (x64 holds the initial guess unless x_zero).

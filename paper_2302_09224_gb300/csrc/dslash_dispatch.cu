@@ -247,6 +247,16 @@ extern "C" int hisq_programmatic_launch(int mode)
     return hisq::pdl_mode.exchange(mode);
 }
 
+namespace hisq {
+std::atomic<int> split_mode{1};
+}
+
+extern "C" int hisq_cg_split_scalars(int mode)
+{
+    if (mode < 0 || mode > 1) return -2;
+    return hisq::split_mode.exchange(mode);
+}
+
 extern "C" int hisq_stencil_config(int cfg)
 {
     if (cfg < -1 || cfg >= hisq::kNumStencilConfigs) return -2;

@@ -85,6 +85,10 @@ struct RedBuf {
                              // slice t (kMaxFusedLt slices); zero between launches
 };
 constexpr int kMaxFusedLt = 4096;
+// Offset (in doubles) of the partials' second half: the split CG chain's
+// r_update leaves its block partials there while it reads the stencil pass's
+// from the first half (see blas.cu).
+constexpr size_t kSplitHalf = (size_t)kMaxRedBlocks * kMaxRed / 2;
 constexpr size_t kSyncWords = 32 + kMaxFusedLt;
 
 // Whether a reducing launch over n sites (blocks of `block` threads, gy grid
@@ -107,6 +111,8 @@ constexpr int kMaxBuf = 16;
 struct CGState {
     double rr;          // |r_k|^2 of the iterated residual
     double rr_prev;     // |r_{k-1}|^2
+    double rr_den;      // split CG chain: |r_k|^2 as r_update read it (beta's denominator, kept
+                        // apart from rr, which p_update's block 0 rewrites while its other blocks run)
     double rr_max;      // max |r|^2 since the last reliable update
     double pAp;
     double alpha;
@@ -263,6 +269,11 @@ bool launch_dslash(int gf, int sf, int cf, int long_recon, bool reduce, const Ds
                    cudaStream_t s);
 // The summing launch of a reducing pass launched with a.defer_finish set.
 bool launch_dslash_finish(int gf, int sf, int cf, int long_recon, const DslashArgs &a, cudaStream_t s);
+// Block partials the reducing pass leaves in a.red.partials (its block count).
+unsigned dslash_partials(int gf, int sf, int cf, int long_recon, const Geom &g);
+// 1: the CG iteration's alpha and beta are summed by every block of the kernel
+// that uses them (hisq_cg_split_scalars)
+extern std::atomic<int> split_mode;
 // Batched stencil over all right-hand sides in tiles of T (T in {1,2,4,8,16},
 // dividing nrhs), variant 0 (register kernel) or 1 (staged neighbour loads,
 // 16-byte spinor records only); false when the triplet or variant has no

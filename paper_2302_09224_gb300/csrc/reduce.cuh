@@ -189,6 +189,74 @@ __device__ void sum_partials(const RedBuf &rb, unsigned nblocks, double *tot)
     }
 }
 
+// Warp 0 alone sums the partials of nblocks blocks (few: a wave of blocks) in
+// the FP32 pair arithmetic (FP64 partials in FP64), in a fixed order (lane l
+// takes rows l, l + 32, ..., then the warp's tree); the totals land in tot
+// (shared memory), valid in thread 0.  The other warps do not take part (no
+// block barrier).
+template <int NR, typename T>
+__device__ void warp0_sum_partials(const RedBuf &rb, unsigned nblocks, double *tot)
+{
+    if (threadIdx.x >= 32) return;
+    constexpr int U = 4;
+    if constexpr (std::is_same<T, double>::value) {  // FP64 partials, summed in FP64
+        double w[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) w[k] = 0.0;
+        for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * 32) {
+            double tmp[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const unsigned b = b0 + u * 32;
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    tmp[u][k] = b < nblocks ? __ldcg(reinterpret_cast<const double *>(rb.partials) + (size_t)b * NR + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int k = 0; k < NR; k++) w[k] += tmp[u][k];
+        }
+        warp_sum<NR, double>(w);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NR; k++) tot[k] = w[k];
+    } else {
+        static_assert(std::is_same<T, FF>::value || std::is_same<T, float>::value, "FP32 or FP32-pair partials");
+        FF w[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++) w[k] = {0.0f, 0.0f};
+        for (unsigned b0 = threadIdx.x; b0 < nblocks; b0 += U * 32) {
+            FF tmp[U][NR];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const unsigned b = b0 + u * 32;
+#pragma unroll
+                for (int k = 0; k < NR; k++) {
+                    if constexpr (std::is_same<T, FF>::value) {
+                        const float2 v = b < nblocks
+                                             ? __ldcg(reinterpret_cast<const float2 *>(rb.partials) + (size_t)b * NR + k)
+                                             : make_float2(0.0f, 0.0f);
+                        tmp[u][k] = FF{v.x, v.y};
+                    } else {
+                        tmp[u][k] = FF{b < nblocks ? __ldcg(reinterpret_cast<const float *>(rb.partials) + (size_t)b * NR + k)
+                                                   : 0.0f,
+                                       0.0f};
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int k = 0; k < NR; k++) w[k] = ff_add(w[k], tmp[u][k]);
+        }
+        warp_sum_ff<NR>(w);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NR; k++) tot[k] = (double)w[k].hi + (double)w[k].lo;
+    }
+}
+
 // Returns true in every thread of the last block, with the grid totals in
 // `tot` (shared memory).  All threads of every block must call it.  Grids may
 // be two-dimensional (blocks are numbered x fastest).

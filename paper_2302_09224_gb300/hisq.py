@@ -137,6 +137,7 @@ _SIGS = {
     "hisq_stencil_config": (_I, [_I]),
     "hisq_stencil_config_reduce": (_I, [_I]),
     "hisq_programmatic_launch": (_I, [_I]),
+    "hisq_cg_split_scalars": (_I, [_I]),
     "hisq_mee_fused": (_I, [_I]),
     "hisq_mee_fused_shape": (None, [_I, _I]),
     "hisq_mee_fused_wait_test": (None, [ctypes.c_uint, _I]),
@@ -342,6 +343,10 @@ def hisq_mee_fused_wait_test(polls: int, unreachable: bool):
 
 def hisq_programmatic_launch(mode: int) -> int:
     return int(lib().hisq_programmatic_launch(int(mode)))
+
+
+def hisq_cg_split_scalars(mode: int) -> int:
+    return int(lib().hisq_cg_split_scalars(int(mode)))
 
 
 def hisq_stencil_config_reduce(cfg: int) -> int:

@@ -181,6 +181,40 @@ def test_maxiter_and_invalid(ctx, orc):
     assert st == hisq.HISQ_OK and not x.any()
 
 
+@pytest.mark.parametrize("name", ["f32", "int20", "half", "int30"])
+def test_split_scalars(ctx, orc, name):
+    """alpha and beta summed from the block partials by every block of the
+    kernel that uses them (the default) or once, by a one-block launch and a
+    last block: both reach the tolerance by the oracle's FP64 residual, with
+    iteration counts within a few percent (they sum in different block shapes,
+    so their rounding differs); the split chain is deterministic (graph and
+    direct launches bitwise equal) and carries the error-estimate trigger,
+    whose finisher reads the alpha record that block 0 writes."""
+    dims, m = (8, 8, 8, 16), 0.01
+    fat, lng = (f.numpy() for f in synth.gauge_pair(dims, seed=0))
+    b = synth.spinor(dims, 1000).numpy()
+    prev = hisq.hisq_cg_split_scalars(0)
+    try:
+        st0, i0, x0 = solve(ctx, dims, fat, lng, m, b, name)
+        assert hisq.hisq_cg_split_scalars(1) == 0
+        st1, i1, x1 = solve(ctx, dims, fat, lng, m, b, name)
+        st2, i2, x2 = solve(ctx, dims, fat, lng, m, b, name, use_graph=0)
+        st3, i3, x3 = solve(ctx, dims, fat, lng, m, b, name, ru_trigger=1)
+    finally:
+        hisq.hisq_cg_split_scalars(prev)
+    # the solver stops on its own FP64 evaluation of |b - M x| / |b| <= 1e-10 and the oracle evaluates
+    # it again in FP64: at m = 0.01 |x| is about 50 |b| per component and each component of M x sums
+    # terms of about 10^3 |b|, so the two roundings may differ by about 1e-13 |b|, 1e-3 of the target
+    for st, x in ((st0, x0), (st1, x1), (st3, x3)):
+        assert st == hisq.HISQ_OK, hisq.STATUS_NAMES[st]
+        assert true_res(orc, dims, fat, lng, m, b, x) <= 1e-10 * (1 + 1e-3)
+    np.testing.assert_array_equal(x1, x2)
+    assert i1.iters == i2.iters and i1.reliable_updates == i2.reliable_updates
+    assert abs(i1.iters - i0.iters) <= 0.03 * i0.iters + 4, (i0.iters, i1.iters)
+    assert i3.reliable_updates >= 2
+    assert hisq.hisq_cg_split_scalars(2) == -2
+
+
 def test_programmatic_launch_same_bits(ctx):
     """Kernels launched with programmatic dependent launch (each waiting for its
     predecessor's results before touching them) give the same solution, bit
