@@ -610,7 +610,8 @@ __device__ __forceinline__ void stencil_site(const DslashArgs &a, int cb, size_t
 }
 
 // One thread per site.  A reducing pass ends each block with its block sum
-// and a partial store; stencil_finish_kernel, launched after it, sums them.
+// and a partial store; stencil_finish_kernel, launched after it, sums them
+// (in the CG the residual update's blocks sum them instead: blas.cu).
 template <int GF, int SF, typename real, int LREC, bool RED, int CFG>
 __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     dslash_kernel(const __grid_constant__ DslashArgs a)
@@ -628,7 +629,7 @@ __global__ void __launch_bounds__(stencil_block(CFG), stencil_minb(CFG))
     real rv[2] = {real(0), real(0)};
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb < vh) stencil_site<GF, SF, real, LREC, RED, CFG>(a, cb, pstride, fsc, lsc, ratio, rv);
-    if constexpr (RED) {  // summed by stencil_finish_kernel
+    if constexpr (RED) {  // summed by stencil_finish_kernel or by the CG's residual update
         const red_t<real> r2[2] = {(red_t<real>)rv[0], (red_t<real>)rv[1]};
         store_block_partial<2>(r2, a.red);
     }
