@@ -576,7 +576,8 @@ def run_stencil_only(args):
 
 
 def run_solve_only(args):
-    """One short mixed-precision CG solve on a small lattice (the small case for ncu captures of the solver's kernels)."""
+    """One short mixed-precision solve (CG, or BiCGStab(4) with --solver bicgstab) on a given lattice: the case for
+    ncu captures of the solver's kernels."""
     import torch
 
     from paper_2302_09224_gb300 import hisq, synth
@@ -591,17 +592,22 @@ def run_solve_only(args):
     fat, lng = synth.gauge_pair(dims, seed=0, device="cuda")
     g = hisq.hisq_load_gauge(ctx, dims, fat, lng)
     del fat, lng
-    b = synth.spinor(dims, synth.rhs_seed(0), device="cuda")
+    bicg = args.solver == "bicgstab"
+    b = synth.spinor(dims, synth.rhs_seed(0), full=bicg, device="cuda")
     x = torch.zeros_like(b)
     p = hisq.hisq_default_params()
     p.mass, p.tol, p.delta, p.on_device = MASS, TOL, DELTA, 1
     p.sloppy = hisq.prec(args.prec, args.recon)
     p.maxiter = args.maxiter
-    st, info = hisq.hisq_cg(ctx, g, p, b, x)
+    if bicg:  # BiCGStab(4) on the full M; maxiter counts operator applications
+        p.l = 4
+        st, info = hisq.hisq_bicgstabl(ctx, g, p, b, x)
+    else:
+        st, info = hisq.hisq_cg(ctx, g, p, b, x)
     torch.cuda.synchronize()
     hisq.hisq_free_gauge(ctx, g)
     hisq.hisq_destroy(ctx)
-    print(json.dumps({"solve": list(dims), "prec": args.prec, "maxiter": args.maxiter,
+    print(json.dumps({"solve": list(dims), "solver": args.solver, "prec": args.prec, "maxiter": args.maxiter,
                       "status": hisq.STATUS_NAMES.get(st, st), "iters": info.iters}))
     return 0
 
@@ -898,6 +904,8 @@ def main():
     ap.add_argument("--stencil-config", default="",
                     help="force the stencil launch shapes: A (both passes) or A,B (plain, reducing), each 0..4")
     ap.add_argument("--solve", default=None, help="LX,LY,LZ,LT: only one short CG solve (profiling)")
+    ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab"],
+                    help="solver of --solve: CG on M_ee, or BiCGStab(4) on the full M")
     ap.add_argument("--workload", default="solve", choices=["solve", "multishift", "batched", "serve"],
                     help="solve: the headline line; the others print their own measurement line")
     ap.add_argument("--formats", default="int20,half", help="sloppy formats for --workload batched")
