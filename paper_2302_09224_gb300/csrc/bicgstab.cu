@@ -386,34 +386,42 @@ __global__ void restart_kernel(BState *b, const double *sum)
     if (!b->active) b->reason = REASON_BREAKDOWN;
 }
 
-// Two rows (parities) of blocks that loop over their parity's sites: at most
-// 4 blocks per SM per row (one wave at the kernels' occupancy), so that the
-// end of a reducing block is paid once per resident block.
+// Two rows (parities) of blocks that loop over their parity's sites: one wave
+// at kernel K's occupancy (at most 4 blocks per SM per row), so that the end
+// of a reducing block is paid once per resident block and no partial second
+// wave trails the first (at 47 registers, five blocks fit a SM, not eight).
+template <auto K>
 dim3 grid2(int vh)
 {
-    static const int sms = [] {
-        int dev = 0, n = 0;
+    static const int per_row = [] {
+        int dev = 0, n = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        return n > 0 ? n : 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, K, kBlock, 0);
+        const int per_sm = occ < 1 ? 1 : occ > 8 ? 8 : occ;
+        const int rows_total = (n > 0 ? n : 1) * per_sm;
+        return rows_total / 2 > 0 ? rows_total / 2 : 1;
     }();
     const int need = (vh + kBlock - 1) / kBlock;
-    return dim3(need < 4 * sms ? need : 4 * sms, 2);
+    return dim3(need < per_row ? need : per_row, 2);
 }
 
-#define B_DISPATCH(SF_, CF_, KERNEL, GRID, ...)                                              \
+// KERNEL<spinor format, compute type> over both parities of vh sites each.
+#define B_LAUNCH(KERNEL, SF, REAL, VH, ...) \
+    launch_chained(KERNEL<SF, REAL>, grid2<&KERNEL<SF, REAL>>(VH), dim3(kBlock), st, __VA_ARGS__)
+#define B_DISPATCH(SF_, CF_, KERNEL, VH, ...)                                               \
     do {                                                                                    \
         const bool f64_ = (CF_) == HISQ_COMPUTE_F64;                                        \
         switch (SF_) {                                                                      \
-        case S_F64: launch_chained(KERNEL<S_F64, double>, GRID, dim3(kBlock), st, __VA_ARGS__); break;     \
-        case S_F32: launch_chained(KERNEL<S_F32, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;      \
-        case S_HALF: launch_chained(KERNEL<S_HALF, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;    \
-        case S_INT20: launch_chained(KERNEL<S_INT20, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;  \
-        case S_INT14: launch_chained(KERNEL<S_INT14, float>, GRID, dim3(kBlock), st, __VA_ARGS__); break;  \
-        case S_INT30:                                                                                      \
-            if (f64_) launch_chained(KERNEL<S_INT30, double>, GRID, dim3(kBlock), st, __VA_ARGS__);        \
-            else launch_chained(KERNEL<S_INT30, float>, GRID, dim3(kBlock), st, __VA_ARGS__);              \
-            break;                                                                                         \
+        case S_F64: B_LAUNCH(KERNEL, S_F64, double, VH, __VA_ARGS__); break;                \
+        case S_F32: B_LAUNCH(KERNEL, S_F32, float, VH, __VA_ARGS__); break;                 \
+        case S_HALF: B_LAUNCH(KERNEL, S_HALF, float, VH, __VA_ARGS__); break;               \
+        case S_INT20: B_LAUNCH(KERNEL, S_INT20, float, VH, __VA_ARGS__); break;             \
+        case S_INT14: B_LAUNCH(KERNEL, S_INT14, float, VH, __VA_ARGS__); break;             \
+        case S_INT30:                                                                       \
+            if (f64_) B_LAUNCH(KERNEL, S_INT30, double, VH, __VA_ARGS__);                   \
+            else B_LAUNCH(KERNEL, S_INT30, float, VH, __VA_ARGS__);                         \
+            break;                                                                          \
         }                                                                                   \
     } while (0)
 
@@ -490,7 +498,7 @@ struct BRun {
         a.j = j;
         a.i = i;
         LaunchScope ls(c, st, PROF_BLAS, 2.0 * sbytes());
-        B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, dot_kernel, grid2(vh), a, x, y);
+        B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, dot_kernel, vh, a, x, y);
     }
 
     void cycle()
@@ -506,13 +514,13 @@ struct BRun {
             a.j = j;
             {
                 LaunchScope ls(c, st, PROF_BLAS, 3.0 * (j + 1) * sbytes());
-                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, u_multi_kernel, grid2(vh), a);
+                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, u_multi_kernel, vh, a);
             }
             mfull(p.sloppy, gv_s, U + j * fb, U + (j + 1) * fb, hb, act, PROF_STENCIL);
             dot(rt, U + (j + 1) * fb, OP_GAMMA, j, 0);
             {
                 LaunchScope ls(c, st, PROF_BLAS, (3.0 * (j + 1) + 1) * sbytes() + 96.0 * 2 * vh);
-                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, r_multi_kernel, grid2(vh), a);
+                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, r_multi_kernel, vh, a);
             }
             mfull(p.sloppy, gv_s, R + j * fb, R + (j + 1) * fb, hb, act, PROF_STENCIL);
         }
@@ -523,7 +531,7 @@ struct BRun {
                 a.i = i;
                 a.op = i < j ? OP_TAU : OP_SIGMA;
                 LaunchScope ls(c, st, PROF_BLAS, (i >= 2 ? 4.0 : 2.0) * sbytes());
-                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, mgs_kernel, grid2(vh), a);
+                B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, mgs_kernel, vh, a);
             }
         {
             LaunchScope ls(c, st, PROF_BLAS, 0.0);
@@ -532,7 +540,7 @@ struct BRun {
         BArgs a = args();
         a.op = OP_FINAL;
         LaunchScope ls(c, st, PROF_BLAS, (2.0 * l + 4.0) * sbytes() + 96.0 * 2 * vh);
-        B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, final_kernel, grid2(vh), a);
+        B_DISPATCH(p.sloppy.spinor, p.sloppy.compute, final_kernel, vh, a);
     }
 
     hisq_status pull()
