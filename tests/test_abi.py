@@ -80,6 +80,14 @@ def test_host_controls_and_refusals(lib):
         assert hisq.hisq_mee_fused(old) == 0
     finally:
         hisq.hisq_mee_fused(old)
+    for control in (hisq.hisq_programmatic_launch, hisq.hisq_cg_split_scalars):
+        old = control(0)
+        try:
+            assert old in (0, 1)
+            assert control(2) == -2 and control(-1) == -2
+            assert control(1) == 0  # the refused calls left 0 in place
+        finally:
+            control(old)
     assert hisq.hisq_mem_used(None) == 0 and hisq.hisq_launch_count(None) == 0
     assert hisq.hisq_last_error(None) == "null context"
     with pytest.raises(hisq.HisqError, match="EINVAL"):
