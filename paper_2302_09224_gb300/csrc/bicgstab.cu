@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kMaxL = 8;
 constexpr int kBlock = 256;
+constexpr int kBSites = 2;  // sites a thread of the reductions loads before using any (in flight together)
 
 struct BState {
     double rho_re, rho_im;         // rho_0
@@ -161,22 +162,37 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(BArgs a, const char *x, con
     pdl_wait();
     pdl_launch_dependents();
     if (skip(a.active)) return;
+    constexpr int U = kBSites, C = Spinor<SF>::chunks;
+    const char *xf = half(x, a.hb), *yf = half(y, a.hb);
     real v[3] = {0, 0, 0};
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
-        real xv[6], yv[6];
-        Spinor<SF>::load(half(x, a.hb), a.vh, s, xv);
-        Spinor<SF>::load(half(y, a.hb), a.vh, s, yv);
-        real d0 = 0, d1 = 0, d2 = 0;  // one site in the compute precision (see reduce_grid)
+    for (int s0 = blockIdx.x * blockDim.x * U + threadIdx.x; s0 < a.vh; s0 += gridDim.x * blockDim.x * U) {
+        uint4 cx[U][C], cy[U][C];
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const real xr = xv[2 * c], xi = xv[2 * c + 1], yr = yv[2 * c], yi = yv[2 * c + 1];
-            d0 += xr * yr + xi * yi;
-            d1 += xr * yi - xi * yr;
-            d2 += yr * yr + yi * yi;
+        for (int u = 0; u < U; u++) {
+            const int s = s0 + u * blockDim.x;
+            if (s < a.vh) {
+                Spinor<SF>::gather(xf, a.vh, s, cx[u]);
+                Spinor<SF>::gather(yf, a.vh, s, cy[u]);
+            }
         }
-        v[0] += d0;
-        v[1] += d1;
-        v[2] += d2;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (s0 + u * (int)blockDim.x >= a.vh) continue;
+            real xv[6], yv[6];
+            Spinor<SF>::decode(cx[u], xv);
+            Spinor<SF>::decode(cy[u], yv);
+            real d0 = 0, d1 = 0, d2 = 0;  // one site in the compute precision (see reduce_grid)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const real xr = xv[2 * c], xi = xv[2 * c + 1], yr = yv[2 * c], yi = yv[2 * c + 1];
+                d0 += xr * yr + xi * yi;
+                d1 += xr * yi - xi * yr;
+                d2 += yr * yr + yi * yi;
+            }
+            v[0] += d0;
+            v[1] += d1;
+            v[2] += d2;
+        }
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
@@ -251,15 +267,34 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
     pdl_wait();
     pdl_launch_dependents();
     if (skip(a.active)) return;
+    constexpr int U = kBSites, C = Spinor<SF>::chunks;
+    char *rjf = half(a.R + a.j * a.fb, a.hb);
+    const char *rpf = half(a.R + (a.i >= 2 ? a.i - 1 : 0) * a.fb, a.hb);
+    const int other = a.i < a.j ? a.i : 0;  // <r_i, r_j>, or <r_j, r_0> at i == j
+    const char *rof = half(a.R + other * a.fb, a.hb);  // never r_j or r_{i-1}: read before r_j is stored
+    const real tr = a.i >= 2 ? (real)a.b->tau_re[a.i - 1][a.j] : real(0);
+    const real ti = a.i >= 2 ? (real)a.b->tau_im[a.i - 1][a.j] : real(0);
     real v[3] = {0, 0, 0};
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.vh; s += gridDim.x * blockDim.x) {
+    for (int s0 = blockIdx.x * blockDim.x * U + threadIdx.x; s0 < a.vh; s0 += gridDim.x * blockDim.x * U) {
+        uint4 cj[U][C], cp[U][C], co[U][C];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int s = s0 + u * blockDim.x;
+            if (s < a.vh) {
+                Spinor<SF>::gather(rjf, a.vh, s, cj[u]);
+                if (a.i >= 2) Spinor<SF>::gather(rpf, a.vh, s, cp[u]);
+                Spinor<SF>::gather(rof, a.vh, s, co[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+        const int s = s0 + u * blockDim.x;
+        if (s >= a.vh) continue;
         real rj[6], ri[6];
-        char *rjf = half(a.R + a.j * a.fb, a.hb);
-        Spinor<SF>::load(rjf, a.vh, s, rj);
+        Spinor<SF>::decode(cj[u], rj);
         if (a.i >= 2) {
             real rp[6];
-            Spinor<SF>::load(half(a.R + (a.i - 1) * a.fb, a.hb), a.vh, s, rp);
-            const real tr = (real)a.b->tau_re[a.i - 1][a.j], ti = (real)a.b->tau_im[a.i - 1][a.j];
+            Spinor<SF>::decode(cp[u], rp);
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const real pr = rp[2 * c], pi = rp[2 * c + 1];
@@ -268,8 +303,7 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
             }
             if (!Spinor<SF>::store(rjf, a.vh, s, rj)) atomicExch(a.err, 1);
         }
-        const int other = a.i < a.j ? a.i : 0;  // <r_i, r_j>, or <r_j, r_0> at i == j
-        Spinor<SF>::load(half(a.R + other * a.fb, a.hb), a.vh, s, ri);
+        Spinor<SF>::decode(co[u], ri);
         real d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -286,6 +320,7 @@ __global__ void __launch_bounds__(kBlock) mgs_kernel(BArgs a)
         v[0] += d0;
         v[1] += d1;
         v[2] += d2;
+        }
     }
     __shared__ double tot[3];
     if (reduce_grid<3>(v, a.red, tot) && threadIdx.x == 0) b_finish(a, tot);
