@@ -5,6 +5,8 @@
 //   r_update      r <- r - alpha Ap,     |r|^2 and Re<r_new, r_old>  (PR beta;
 //                 for the 30-bit FP64-class triplet from the stored records)
 //   p_update      p' <- r + beta p       (into the next ring slot)
+//                 (both also in a split form for the CG, below: alpha and beta
+//                 summed by every block from the previous kernel's partials)
 //   x_flush       x_hi <- x_hi + sum_j alpha_j p_j   (buffered gradient vectors)
 //   true_residual r_hi <- b - A x_hi (FP64), r <- r_hi (sloppy),
 //                 |r_hi|^2 and <r_hi, p> for the re-projection of p
